@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
+    config.addinivalue_line("markers", "slow: longer CPU case")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    import oracle
+    from oracle.build import build_oracle
+
+    build_oracle()
+    return oracle
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
