@@ -1,0 +1,216 @@
+/*
+ * fdtd.h -- C ABI of the GB300 imaginary-time FDTD solver for the 3-D
+ * Schroedinger equation (Strickland & Yager-Elorriaga, "A Parallel Algorithm
+ * for Solving the 3d Schroedinger Equation", arXiv:0904.0939).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Units: hbar = 1; the mass m is a lattice parameter (Sec. II).
+ * - Lattice: N sites per axis, spacing a = L / N (Sec. III), site (i, j, k),
+ *   1 <= i, j, k <= N, at x = (i - (N+1)/2) a (likewise y, z), so the box is
+ *   centred on the origin and r is measured from its centre (Sec. VII).
+ *   Dirichlet boundary: psi = 0 outside the N^3 sites (Sec. III, Sec. V).
+ * - Field layout across the ABI: dense N^3 arrays, x fastest, then y, then z
+ *   (element (i, j, k) at offset ((k-1) N + (j-1)) N + (i-1)).  No padding.
+ * - Memory: every pointer argument is paired with a mem_kind (FDTD_MEM_HOST
+ *   or FDTD_MEM_DEVICE).  Inputs are borrowed for the duration of the call
+ *   only: the library copies them into its own layout.  Outputs are written
+ *   into caller-owned buffers.
+ * - Ownership: the caller allocates ONE device workspace of at least
+ *   fdtd_workspace_size() bytes (256-byte aligned) and keeps it alive until
+ *   fdtd_destroy(); the library never allocates device memory itself.  The
+ *   host-side context is allocated by fdtd_create and freed by fdtd_destroy.
+ * - Streams: all device work of a handle is issued on the cudaStream_t given
+ *   to fdtd_create (passed as void*; NULL = legacy default stream).  Calls
+ *   that return results to host memory synchronise that stream.
+ * - Errors: every call returns an int status (FDTD_OK = 0; negative = error;
+ *   FDTD_NOT_CONVERGED is a positive, soft status).  Nothing aborts, exits or
+ *   throws across the ABI.  fdtd_last_error() gives a message for the last
+ *   failure on a handle.
+ * - Threads: a handle must not be used by two host threads at once.
+ */
+#ifndef FDTD_H_
+#define FDTD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FDTD_API __attribute__((visibility("default")))
+#else
+#define FDTD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define FDTD_OK 0
+#define FDTD_NOT_CONVERGED 1       /* soft: max_steps reached with tol > 0 */
+#define FDTD_ERR_INVALID_ARG (-1)  /* bad pointer, size, enum or index */
+#define FDTD_ERR_UNSTABLE_DT (-2)  /* dtau >= m a^2 / 3, or 1 + dtau V / 2 <= 0 */
+#define FDTD_ERR_NONFINITE (-3)    /* NaN/Inf in an input or in the norm */
+#define FDTD_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define FDTD_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define FDTD_ERR_SHAPE (-6)        /* lattice sizes or boxes do not match */
+#define FDTD_ERR_WORKSPACE (-7)    /* workspace missing, misaligned or too small */
+#define FDTD_ERR_STATE (-8)        /* call out of order (e.g. evolve before set_potential) */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define FDTD_F64 0   /* psi and V in FP64 ("plain FP64 form") */
+#define FDTD_F32 1   /* psi and V in FP32, sums in FP64 / compensated FP32 */
+#define FDTD_BF16 2  /* psi stored as BF16, V and arithmetic in FP32 (coarse levels) */
+
+#define FDTD_MEM_HOST 0
+#define FDTD_MEM_DEVICE 1
+
+#define FDTD_DIST_UNIFORM 0   /* U[-1, 1) */
+#define FDTD_DIST_GAUSSIAN 1  /* N(0, 1), Box-Muller (Sec. III) */
+
+/* Symmetry mask for fdtd_init_symmetric (Sec. IV): two bits per axis,
+ * x in bits 0-1, y in bits 2-3, z in bits 4-5; per axis 0 = none,
+ * 1 = S_i (copy), 2 = A_i (copy with sign flip). */
+#define FDTD_PARITY_NONE 0
+#define FDTD_PARITY_S 1
+#define FDTD_PARITY_A 2
+#define FDTD_PARITY_MASK(px, py, pz) ((px) | ((py) << 2) | ((pz) << 4))
+
+/* ---- descriptors ------------------------------------------------------------ */
+typedef struct {
+  int32_t n;          /* sites per axis, 1 <= n <= 2048 */
+  int32_t precision;  /* FDTD_F64 / FDTD_F32 / FDTD_BF16 */
+  double length;      /* box length L = n a (> 0) */
+  double mass;        /* particle mass m (> 0) */
+  double dtau;        /* imaginary time step; 0 selects a^2 / 4 (Sec. VII) */
+  double v_inf;       /* V at infinity for the binding energy (Eq. bindingenergy) */
+} fdtd_lattice_desc;
+
+typedef struct {
+  int32_t check_every;    /* steps between checks (Sec. V; default 100) */
+  int32_t tol_relative;   /* 1: converged when |dE_b| <= tol |E_b|; 0: |dE_b| <= tol */
+  double tol;             /* convergence tolerance; <= 0 never converges */
+  int32_t temporal_depth; /* FP32/BF16 steps fused per stencil launch; 0 = auto */
+  int32_t backward_steps; /* largest T that fdtd_backward may be asked for; 0 = none */
+  int32_t batched;        /* 1: all lattices of the handle advance in one persistent launch */
+  int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
+  int32_t reserved[4];
+} fdtd_options;
+
+typedef struct {
+  double energy;          /* E = sum psi H psi / sum psi^2 (Eq. energysum, sign of Sec. II's H) */
+  double binding_energy;  /* E - v_inf (Eq. bindingenergy) */
+  double norm;            /* sum psi^2 a^3 of the field the sums were taken on */
+  double r2;              /* <r^2> = sum r^2 psi^2 / sum psi^2 */
+  double r_rms;           /* sqrt(<r^2>) */
+  double v_expect;        /* <V> = sum V psi^2 / sum psi^2 */
+  double delta_e;         /* |E_b - E_b(previous check)|, -1 if none */
+  double reserved;
+  int64_t steps;          /* steps taken by the last fdtd_evolve on this lattice */
+  int32_t converged;      /* 1 if the last fdtd_evolve met the tolerance */
+  int32_t checks;         /* checks made by the last fdtd_evolve */
+} fdtd_obs;
+
+typedef struct {
+  int64_t launches;       /* kernels launched by this handle since creation/reset */
+  int64_t stencil_launches;
+  double stencil_ms;      /* summed device time of stencil launches (profiling on) */
+  int64_t stencil_site_updates;
+  double stencil_bytes;   /* algorithmic HBM bytes of those launches */
+} fdtd_stats;
+
+typedef struct fdtd_context* fdtd_handle;
+
+/* ---- calls ------------------------------------------------------------------ */
+
+/* Fill *o with the defaults: check_every 100, tol 1e-6 relative, auto depth,
+ * no backward storage, not batched, parity re-imposed at every check. */
+FDTD_API int fdtd_default_options(fdtd_options* o);
+
+/* Bytes of device workspace that fdtd_create needs for `count` lattices.
+ * o may be NULL (defaults). */
+FDTD_API int fdtd_workspace_size(const fdtd_lattice_desc* d, int count, const fdtd_options* o, size_t* bytes);
+
+/* Create a handle for `count` lattices on the current CUDA device.
+ * Validates every descriptor: n, L, m > 0; the von Neumann bound
+ * dtau < m a^2 / 3 (Sec. III) else FDTD_ERR_UNSTABLE_DT.  ws must be a
+ * device pointer, 256-byte aligned, of ws_bytes >= fdtd_workspace_size().
+ * stream is a cudaStream_t (or NULL).  On success *out owns no device memory. */
+FDTD_API int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, void* ws, size_t ws_bytes,
+                void* stream, fdtd_handle* out);
+
+/* Release the host-side context (the caller frees the workspace). */
+FDTD_API int fdtd_destroy(fdtd_handle h);
+
+/* Message for the last error on h (or on handle creation when h is NULL). */
+FDTD_API const char* fdtd_last_error(fdtd_handle h);
+
+/* Load V (n^3 values, dense x-fastest, dtype FDTD_F64 or FDTD_F32) for
+ * lattice `lat` (Sec. II: static real potential).  The coefficients
+ * A = (1 - dtau V/2)/(1 + dtau V/2) and B = 1/(1 + dtau V/2) of
+ * Eq. updateeq are derived from it on the device.  Returns
+ * FDTD_ERR_NONFINITE for NaN/Inf and FDTD_ERR_UNSTABLE_DT where
+ * 1 + dtau V/2 <= 0 (the update would divide by zero or flip sign). */
+FDTD_API int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind);
+
+/* Random initial wavefunction (Sec. III) followed by the symmetry mask
+ * (Sec. IV).  Site value = draw number lat_id * 2^42 + n (uniform) or
+ * draws 2n, 2n+1 (Gaussian) of the SplitMix64 stream seeded with `seed`,
+ * n = dense site index.  The mask is remembered and re-imposed at every
+ * check of fdtd_evolve.  The field becomes the start of fdtd_backward. */
+FDTD_API int fdtd_init_symmetric(fdtd_handle h, int lat, uint64_t seed, int parity_mask, int dist);
+
+/* Replace / read psi (n^3 values, dense x-fastest, dtype FDTD_F64/F32) --
+ * the save/restore of Sec. VII.G.  set_psi also records the field as the
+ * start of fdtd_backward and sets the symmetry mask to `parity_mask`. */
+FDTD_API int fdtd_set_psi(fdtd_handle h, int lat, const void* psi, int dtype, int mem_kind, int parity_mask);
+FDTD_API int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_kind);
+
+/* Imaginary-time evolution of every lattice of the handle (Eq. updateeq),
+ * with a check at step t = 0, check_every, 2 check_every, ... and at
+ * t = max_steps: the sums of Eq. energysum on psi_t, renormalisation to
+ * sum psi^2 a^3 = 1 (Sec. III), re-imposition of the symmetry mask
+ * (Sec. IV), and the convergence test on the binding energy (Sec. V).
+ * A lattice stops at the first check whose |dE_b| meets the tolerance.
+ * *steps_done (may be NULL) receives the largest step count over lattices.
+ * Returns FDTD_OK, FDTD_NOT_CONVERGED (tol > 0 and some lattice reached
+ * max_steps), FDTD_ERR_NONFINITE, FDTD_ERR_TIMEOUT or another error. */
+FDTD_API int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done);
+
+/* Observables recorded at the last check of the last fdtd_evolve. */
+FDTD_API int fdtd_last_check(fdtd_handle h, int lat, fdtd_obs* out);
+
+/* Observables of the current psi (Eq. energysum, <r^2>, <V>, norm);
+ * the field is not modified.  steps/converged/checks echo the last evolve. */
+FDTD_API int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out);
+
+/* Multi-resolution transfer (Sec. VI, Sec. VII.G): psi of (dst, lat_dst)
+ * becomes the trilinear interpolation of psi of (src, lat_src), then is
+ * renormalised and given the source's symmetry mask.  Requires
+ * n_dst = 2 n_src and equal box lengths (else FDTD_ERR_SHAPE).  Storage
+ * precisions may differ (e.g. BF16 coarse -> FP32 fine).  Both handles must
+ * use the same device; the work runs on dst's stream after src's work. */
+FDTD_API int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst);
+
+/* Gradient of  w_e E[psi_T] + w_r <r^2>[psi_T]  with respect to V at every
+ * site, through T unrolled update steps started from the recorded initial
+ * field (the last init_symmetric / set_psi), with the same checks as
+ * fdtd_evolve with tol = 0 (renormalisation factors held constant; the
+ * symmetry projection differentiated exactly).  sqrt(T) checkpointing:
+ * the forward pass stores psi every ceil(sqrt T) steps and recomputes each
+ * segment.  Needs T <= options.backward_steps.  gv receives n^3 values of
+ * dtype FDTD_F64 or FDTD_F32.  obs (may be NULL) receives E, <r^2> at T.
+ * Leaves psi of the lattice equal to psi_T. */
+FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, void* gv, int dtype,
+                  int mem_kind, fdtd_obs* obs);
+
+/* Launch counters and (when profiling is on) summed stencil device time. */
+FDTD_API int fdtd_get_stats(fdtd_handle h, fdtd_stats* out);
+FDTD_API int fdtd_reset_stats(fdtd_handle h);
+/* on = 1: bracket every stencil launch with CUDA events on the handle's stream. */
+FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_H_ */

@@ -1,0 +1,342 @@
+"""GB300 imaginary-time FDTD solver for the 3-D Schroedinger equation.
+
+Python binding of the C ABI in ``include/fdtd.h`` (library ``libfdtd.so``,
+hand-written sm_103a CUDA).  This module only marshals arguments: every step
+of the method runs in the library's kernels.  PyTorch supplies the device
+workspace and the CUDA stream.  Importing the package raises if the CUDA
+library has not been built; there is no CPU fallback.
+
+Method (Strickland & Yager-Elorriaga, arXiv:0904.0939):
+  * Eq. updateeq -- imaginary-time update psi <- A psi + (B dtau / 2m) sum D.PsiHat
+  * Eq. energysum -- energy functional, <r^2>, binding energy (Eq. bindingenergy)
+  * Sec. IV -- symmetric / antisymmetric initial conditions (S_i, A_i)
+  * Sec. VI -- multi-resolution bootstrap (trilinear transfer to 2N)
+  * gradients of E and <r^2> w.r.t. V through the unrolled evolution
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdtd.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_UNSTABLE_DT, ERR_NONFINITE, ERR_CUDA = -1, -2, -3, -4
+ERR_TIMEOUT, ERR_SHAPE, ERR_WORKSPACE, ERR_STATE = -5, -6, -7, -8
+F64, F32, BF16 = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+DIST_UNIFORM, DIST_GAUSSIAN = 0, 1
+PARITY_NONE, PARITY_S, PARITY_A = 0, 1, 2
+
+
+def parity_mask(px: int = 0, py: int = 0, pz: int = 0) -> int:
+    """Two bits per axis: 0 none, 1 S_i, 2 A_i (Sec. IV)."""
+    return px | (py << 2) | (pz << 4)
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fdtd error {code}: {msg}")
+        self.code = code
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("precision", ctypes.c_int32), ("length", ctypes.c_double),
+                ("mass", ctypes.c_double), ("dtau", ctypes.c_double), ("v_inf", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("check_every", ctypes.c_int32), ("tol_relative", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("binding_energy", ctypes.c_double), ("norm", ctypes.c_double),
+                ("r2", ctypes.c_double), ("r_rms", ctypes.c_double), ("v_expect", ctypes.c_double),
+                ("delta_e", ctypes.c_double), ("reserved", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("converged", ctypes.c_int32), ("checks", ctypes.c_int32)]
+
+    def to_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("stencil_launches", ctypes.c_int64),
+                ("stencil_ms", ctypes.c_double), ("stencil_site_updates", ctypes.c_int64),
+                ("stencil_bytes", ctypes.c_double)]
+
+
+EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",
+            "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
+            "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
+            "fdtd_reset_stats", "fdtd_set_profiling"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "fdtd_default_options": [P(Options)],
+        "fdtd_workspace_size": [P(LatticeDesc), i32, P(Options), P(ctypes.c_size_t)],
+        "fdtd_create": [P(LatticeDesc), i32, P(Options), vp, ctypes.c_size_t, vp, P(vp)],
+        "fdtd_destroy": [vp],
+        "fdtd_set_potential": [vp, i32, vp, i32, i32],
+        "fdtd_init_symmetric": [vp, i32, u64, i32, i32],
+        "fdtd_set_psi": [vp, i32, vp, i32, i32, i32],
+        "fdtd_get_psi": [vp, i32, vp, i32, i32],
+        "fdtd_evolve": [vp, i64, P(i64)],
+        "fdtd_last_check": [vp, i32, P(Obs)],
+        "fdtd_observables": [vp, i32, P(Obs)],
+        "fdtd_upsample": [vp, i32, vp, i32],
+        "fdtd_backward": [vp, i32, i64, d, d, vp, i32, i32, P(Obs)],
+        "fdtd_get_stats": [vp, P(Stats)],
+        "fdtd_reset_stats": [vp],
+        "fdtd_set_profiling": [vp, i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fdtd_last_error.argtypes = [vp]
+    lib.fdtd_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib.fdtd_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Lattice:
+    """One lattice: n sites per axis, box length, storage precision."""
+    n: int
+    length: float
+    precision: int = F32
+    mass: float = 1.0
+    dtau: float = 0.0
+    v_inf: float = 0.0
+
+    def desc(self) -> LatticeDesc:
+        return LatticeDesc(self.n, self.precision, self.length, self.mass, self.dtau, self.v_inf)
+
+    @property
+    def a(self) -> float:
+        return self.length / self.n
+
+    @property
+    def tau_step(self) -> float:
+        return self.dtau if self.dtau > 0 else self.a * self.a / 4.0
+
+
+def _check(rc: int, handle=None, allow_soft: bool = False) -> int:
+    if rc < 0 or (rc > 0 and not allow_soft):
+        msg = lib.fdtd_last_error(handle)
+        raise FdtdError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _buffer(arr, want_dtype=None):
+    """(pointer, dtype code, mem kind, keepalive) for a numpy array or torch tensor."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(arr, torch.Tensor):
+        t = arr.contiguous()
+        if t.dtype not in (torch.float64, torch.float32):
+            t = t.double()
+        code = F64 if t.dtype == torch.float64 else F32
+        return ctypes.c_void_p(t.data_ptr()), code, (MEM_DEVICE if t.is_cuda else MEM_HOST), t
+    a = np.ascontiguousarray(arr)
+    if a.dtype not in (np.float64, np.float32):
+        a = a.astype(np.float64)
+    code = F64 if a.dtype == np.float64 else F32
+    return ctypes.c_void_p(a.ctypes.data), code, MEM_HOST, a
+
+
+class Solver:
+    """A handle on the C library for one or more lattices.
+
+    The workspace is one torch uint8 CUDA tensor of fdtd_workspace_size()
+    bytes; all work runs on `stream` (default: torch's current stream)."""
+
+    def __init__(self, lattices, options: Options | None = None, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise FdtdError(ERR_CUDA, "no CUDA device: the FDTD solver runs on the GPU only")
+        self.lattices = list(lattices) if isinstance(lattices, (list, tuple)) else [lattices]
+        self.options = options if options is not None else default_options()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        arr = (LatticeDesc * len(self.lattices))(*[l.desc() for l in self.lattices])
+        self._descs = arr
+        size = ctypes.c_size_t()
+        _check(lib.fdtd_workspace_size(arr, len(self.lattices), ctypes.byref(self.options), ctypes.byref(size)))
+        self.workspace_bytes = size.value
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            _check(lib.fdtd_create(arr, len(self.lattices), ctypes.byref(self.options),
+                                   ctypes.c_void_p(self.workspace.data_ptr()), size.value,
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fdtd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ctx(self):
+        import torch
+
+        return torch.cuda.device(self.device)
+
+    # --- calls ---------------------------------------------------------------
+    def set_potential(self, v, lat: int = 0):
+        ptr, code, mem, keep = _buffer(v)
+        with self._ctx():
+            _check(lib.fdtd_set_potential(self.handle, lat, ptr, code, mem), self.handle)
+
+    def init_symmetric(self, seed: int, mask: int = 0, lat: int = 0, dist: int = DIST_UNIFORM):
+        with self._ctx():
+            _check(lib.fdtd_init_symmetric(self.handle, lat, seed, mask, dist), self.handle)
+
+    def set_psi(self, psi, lat: int = 0, mask: int = 0):
+        ptr, code, mem, keep = _buffer(psi)
+        with self._ctx():
+            _check(lib.fdtd_set_psi(self.handle, lat, ptr, code, mem, mask), self.handle)
+
+    def get_psi(self, lat: int = 0, dtype=np.float64, out=None):
+        """psi as a dense (n, n, n) array [z][y][x]; `out` may be a CUDA tensor."""
+        n = self.lattices[lat].n
+        if out is None:
+            out = np.empty((n, n, n), dtype=dtype)
+        ptr, code, mem, keep = _buffer(out)
+        with self._ctx():
+            _check(lib.fdtd_get_psi(self.handle, lat, ptr, code, mem), self.handle)
+        return out
+
+    def evolve(self, max_steps: int) -> tuple[int, bool]:
+        """Run until every lattice converges or max_steps; returns (steps, converged)."""
+        done = ctypes.c_int64()
+        with self._ctx():
+            rc = _check(lib.fdtd_evolve(self.handle, max_steps, ctypes.byref(done)), self.handle, allow_soft=True)
+        return done.value, rc == OK
+
+    def last_check(self, lat: int = 0) -> dict:
+        o = Obs()
+        with self._ctx():
+            _check(lib.fdtd_last_check(self.handle, lat, ctypes.byref(o)), self.handle)
+        return o.to_dict()
+
+    def observables(self, lat: int = 0) -> dict:
+        o = Obs()
+        with self._ctx():
+            _check(lib.fdtd_observables(self.handle, lat, ctypes.byref(o)), self.handle)
+        return o.to_dict()
+
+    def upsample_from(self, src: "Solver", lat_src: int = 0, lat: int = 0):
+        with self._ctx():
+            _check(lib.fdtd_upsample(src.handle, lat_src, self.handle, lat), self.handle)
+
+    def backward(self, T: int, w_e: float = 1.0, w_r: float = 0.0, lat: int = 0, out=None):
+        """dL/dV for L = w_e E + w_r <r^2> after T steps; returns (gV, obs)."""
+        n = self.lattices[lat].n
+        if out is None:
+            out = np.empty((n, n, n), dtype=np.float64)
+        ptr, code, mem, keep = _buffer(out)
+        o = Obs()
+        with self._ctx():
+            _check(lib.fdtd_backward(self.handle, lat, T, w_e, w_r, ptr, code, mem, ctypes.byref(o)), self.handle)
+        return out, o.to_dict()
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib.fdtd_get_stats(self.handle, ctypes.byref(s)), self.handle)
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def reset_stats(self):
+        _check(lib.fdtd_reset_stats(self.handle), self.handle)
+
+    def set_profiling(self, on: bool):
+        _check(lib.fdtd_set_profiling(self.handle, int(bool(on))), self.handle)
+
+
+def solve(v, n: int, length: float, precision: int = F32, mask: int = 0, seed: int = 904939,
+          max_steps: int = 1_000_000, options: Options | None = None, v_inf: float = 0.0):
+    """Ground state of one sector from a random start (Secs. III-V)."""
+    s = Solver(Lattice(n, length, precision, v_inf=v_inf), options)
+    s.set_potential(v)
+    s.init_symmetric(seed, mask)
+    steps, conv = s.evolve(max_steps)
+    return s, s.last_check()
+
+
+def multires(levels, potentials, mask: int = 0, seed: int = 904939, options: Options | None = None,
+             max_steps: int = 1_000_000, v_inf=0.0):
+    """Multi-resolution bootstrap (Sec. VI): solve on levels[0] from a random
+    start, then transfer each converged field to the next (2N, same L)
+    lattice and continue.  Returns the list of (solver, last_check)."""
+    out = []
+    prev = None
+    for i, (lat, v) in enumerate(zip(levels, potentials)):
+        s = Solver(lat, options)
+        s.set_potential(v)
+        if prev is None:
+            s.init_symmetric(seed, mask)
+        else:
+            s.upsample_from(prev)
+        s.evolve(max_steps)
+        out.append((s, s.last_check()))
+        prev = s
+    return out
+
+
+def energy_fn():
+    """torch.autograd.Function computing (E, <r^2>) after T unrolled steps
+    from a seeded start, with dV from fdtd_backward (sqrt(T) checkpointing)."""
+    import torch
+
+    class EnergyFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v, solver, T, seed, mask):
+            solver.set_potential(v.detach())
+            solver.init_symmetric(seed, mask)
+            solver.evolve(T)
+            o = solver.last_check()
+            ctx.solver, ctx.T = solver, T
+            ctx.shape, ctx.dtype, ctx.device = v.shape, v.dtype, v.device
+            return (torch.tensor(o["energy"], dtype=torch.float64, device=v.device),
+                    torch.tensor(o["r2"], dtype=torch.float64, device=v.device))
+
+        @staticmethod
+        def backward(ctx, g_e, g_r):
+            out = torch.empty(ctx.shape, dtype=torch.float64, device=ctx.device)
+            ctx.solver.backward(ctx.T, float(g_e), float(g_r), out=out)
+            return out.to(ctx.dtype), None, None, None, None
+
+    return EnergyFn

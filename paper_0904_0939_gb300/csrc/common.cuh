@@ -1,0 +1,107 @@
+// Device-side helpers shared by the FDTD kernels (sm_103a).
+//
+// Field layout in HBM: dense N^3, x fastest, no padding; sites outside
+// [0, N) along any axis read as 0 (Dirichlet wall of Sec. III / Sec. V).
+// Indices in this file are 0-based: site (x, y, z) sits at physical
+// coordinate (x - (N-1)/2) a, the centred convention of Sec. VII.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+// ---------------------------------------------------------------- storage
+template <typename T> struct Store;
+template <> struct Store<double> {
+  using C = double;  // arithmetic type
+  __device__ __forceinline__ static double ld(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static double to(double v) { return v; }
+  __device__ __forceinline__ static double from(double v) { return v; }
+};
+template <> struct Store<float> {
+  using C = float;
+  __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static float to(float v) { return v; }
+  __device__ __forceinline__ static float from(float v) { return v; }
+};
+template <> struct Store<__nv_bfloat16> {
+  using C = float;
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ __forceinline__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------- coefficients
+// Eq. updateeq with h = dtau V / 2:
+//   psi' = A psi + (B dtau / 2m) sum_i (D . PsiHat)_i,
+//   A = (1 - h)/(1 + h),  B = 1/(1 + h),  D = [1, -2, 1] / a^2.
+// With c = dtau / (2 m a^2) and S = sum of the 6 neighbours this is
+//   psi' = B [ (1 - h - 6c) psi + c S ],
+// the form the FP32 kernels evaluate (one reciprocal per site, the rest
+// FMAs).  The neighbour sum is always taken as ((xm + xp) + (ym + yp)) +
+// (zm + zp): commutative pairs keep an odd/even field exactly odd/even.
+struct CoefF {
+  float b;      // 1 / (1 + h)
+  float alpha;  // 1 - h - 6c
+};
+__device__ __forceinline__ CoefF coef_f32(float v, float half_dtau, float one_minus_6c) {
+  float h = half_dtau * v;
+  CoefF k;
+  k.b = __frcp_rn(1.0f + h);
+  k.alpha = one_minus_6c - h;
+  return k;
+}
+__device__ __forceinline__ float nbr_sum(float xm, float xp, float ym, float yp, float zm, float zp) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+}
+__device__ __forceinline__ float update_f32(float c, float s, CoefF k, float cc) {
+  return __fmul_rn(k.b, __fmaf_rn(cc, s, __fmul_rn(k.alpha, c)));
+}
+
+// FP64 ("plain") form: the per-site A and c B are precomputed once from V
+// and stored, psi' = A psi + cB (S - 6 psi).
+__device__ __forceinline__ double nbr_sum(double xm, double xp, double ym, double yp, double zm, double zp) {
+  return __dadd_rn(__dadd_rn(__dadd_rn(xm, xp), __dadd_rn(ym, yp)), __dadd_rn(zm, zp));
+}
+__device__ __forceinline__ double update_f64(double c, double s, double A, double cB) {
+  return __fma_rn(cB, __fma_rn(-6.0, c, s), __dmul_rn(A, c));
+}
+
+// ---------------------------------------------------------------- geometry
+__device__ __forceinline__ float coord_f32(int i, int n, float a) { return ((float)i - 0.5f * (float)(n - 1)) * a; }
+__device__ __forceinline__ double coord_f64(int i, int n, double a) { return ((double)i - 0.5 * (double)(n - 1)) * a; }
+
+// ---------------------------------------------------------------- RNG
+// SplitMix64 (Steele, Lea & Flood 2014): output d of the stream seeded with
+// s is fin(s + (d + 1) * 0x9E3779B97F4A7C15), fin = the 30/27/31 xor-shift
+// multiply finaliser.  Lattice `lat` owns draws lat * 2^42 .. (lat+1) * 2^42 - 1.
+__device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t d) {
+  uint64_t z = seed + (d + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double unit_interval(uint64_t bits) {
+  return (double)(bits >> 11) * 0x1.0p-53;  // [0, 1)
+}
+
+// ---------------------------------------------------------------- misc
+__device__ __forceinline__ size_t site_index(int x, int y, int z, int n) {
+  return ((size_t)z * (size_t)n + (size_t)y) * (size_t)n + (size_t)x;
+}
+
+// Kahan-compensated FP32 accumulator (Kahan 1965): sum - comp carries the
+// running total to ~2^-48 relative, enough to hand over to FP64.
+struct Kahan {
+  float sum = 0.f, comp = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float y = __fsub_rn(v, comp);
+    float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)sum - (double)comp; }
+};
+
+}  // namespace fdtd

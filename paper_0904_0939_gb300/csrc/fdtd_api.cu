@@ -1,0 +1,836 @@
+// C ABI of the FDTD solver (declared in include/fdtd.h): argument checks,
+// workspace carving, and the host-side drivers that enqueue the kernels of
+// k_core.cu / k_tblock.cu / k_adjoint.cu / k_batched.cu on the caller's stream.
+//
+// The library never allocates device memory: every buffer is a slice of the
+// caller's workspace.  Per lattice the workspace holds two psi fields
+// (ping-pong), V (plus A and cB for FP64 lattices), the block partials of
+// the lattice sums, two state records, and -- when backward storage was
+// requested -- the start field, the sqrt(T) checkpoint pool, one segment of
+// recomputed fields, two adjoint fields and the FP64 gradient accumulator.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "fdtd.h"
+#include "kernels.cuh"
+
+using namespace fdtd;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+constexpr size_t kStagingBytes = 8u << 20;
+
+size_t elem_bytes(int prec) { return prec == FDTD_F64 ? 8 : (prec == FDTD_F32 ? 4 : 2); }
+
+struct Lat {
+  fdtd_lattice_desc d{};
+  Params p{};
+  size_t n3 = 0;
+  int es = 0;
+  void* psi[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* v = nullptr;
+  double* coefA = nullptr;
+  double* coefCB = nullptr;
+  double* partials = nullptr;
+  int nparts = 0;
+  LatState* state = nullptr;    // [0] evolve record, [1] scratch
+  int mask = 0;
+  bool has_v = false, has_psi = false, has_psi0 = false;
+  // backward storage
+  void* psi0 = nullptr;
+  int64_t bw_T = 0;
+  int bw_K = 0;
+  int64_t bw_npool = 0;
+  void* pool = nullptr;
+  void* seg = nullptr;
+  void* lam[2] = {nullptr, nullptr};
+  double* gv = nullptr;
+  double* scales = nullptr;
+  // last evolve
+  int64_t last_steps = 0;
+  LatState host_state{};
+};
+
+struct Carve {
+  char* base = nullptr;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+int check_desc(const fdtd_lattice_desc& d, std::string& err) {
+  if (d.n < 1 || d.n > 2048) {
+    err = "lattice n must be in [1, 2048]";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (d.precision != FDTD_F64 && d.precision != FDTD_F32 && d.precision != FDTD_BF16) {
+    err = "unknown precision";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (!(d.length > 0.0) || !std::isfinite(d.length) || !(d.mass > 0.0) || !std::isfinite(d.mass) ||
+      !(d.dtau >= 0.0) || !std::isfinite(d.dtau) || !std::isfinite(d.v_inf)) {
+    err = "length and mass must be positive and finite, dtau >= 0";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  double a = d.length / d.n;
+  double dt = d.dtau > 0.0 ? d.dtau : a * a / 4.0;
+  if (!(dt < d.mass * a * a / 3.0)) {
+    err = "dtau violates the von Neumann bound dtau < m a^2 / 3";
+    return FDTD_ERR_UNSTABLE_DT;
+  }
+  return FDTD_OK;
+}
+
+int check_options(const fdtd_options& o, std::string& err) {
+  if (o.check_every < 1) {
+    err = "check_every must be >= 1";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.temporal_depth < 0 || o.temporal_depth > blocked_max_depth()) {
+    err = "temporal_depth out of range";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.backward_steps < 0 || !std::isfinite(o.tol)) {
+    err = "backward_steps must be >= 0 and tol finite";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  return FDTD_OK;
+}
+
+Params make_params(const fdtd_lattice_desc& d) {
+  Params p{};
+  p.n = d.n;
+  p.a = d.length / d.n;
+  p.dtau = d.dtau > 0.0 ? d.dtau : p.a * p.a / 4.0;
+  p.mass = d.mass;
+  p.c = p.dtau / (2.0 * p.mass * p.a * p.a);
+  p.half_dtau_f = (float)(0.5 * p.dtau);
+  p.c_f = (float)p.c;
+  p.one_m6c_f = (float)(1.0 - 6.0 * p.c);
+  return p;
+}
+
+// Carve (or, with base == nullptr, measure) the workspace of every lattice.
+void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve& cv, std::vector<Lat>* lats,
+            void** staging, int32_t** flags, void** batch_ws, size_t* batch_bytes) {
+  *staging = cv.take(kStagingBytes);
+  *flags = (int32_t*)cv.take(256);
+  for (int l = 0; l < count; ++l) {
+    Lat L;
+    L.d = d[l];
+    L.p = make_params(d[l]);
+    L.n3 = (size_t)d[l].n * d[l].n * d[l].n;
+    L.es = (int)elem_bytes(d[l].precision);
+    L.psi[0] = cv.take(L.n3 * L.es);
+    L.psi[1] = cv.take(L.n3 * L.es);
+    if (d[l].precision == FDTD_F64) {
+      L.v = cv.take(L.n3 * 8);
+      L.coefA = (double*)cv.take(L.n3 * 8);
+      L.coefCB = (double*)cv.take(L.n3 * 8);
+    } else {
+      L.v = cv.take(L.n3 * 4);
+    }
+    L.nparts = sums_blocks(d[l].n);
+    L.partials = (double*)cv.take((size_t)L.nparts * 4 * sizeof(double));
+    L.state = (LatState*)cv.take(2 * sizeof(LatState));
+    if (o.backward_steps > 0 && d[l].precision != FDTD_BF16) {
+      L.bw_T = o.backward_steps;
+      L.bw_K = (int)std::ceil(std::sqrt((double)o.backward_steps));
+      L.bw_npool = (L.bw_T + L.bw_K - 1) / L.bw_K;
+      L.psi0 = cv.take(L.n3 * L.es);
+      L.pool = cv.take((size_t)L.bw_npool * L.n3 * L.es);
+      L.seg = cv.take((size_t)L.bw_K * L.n3 * L.es);
+      L.lam[0] = cv.take(L.n3 * L.es);
+      L.lam[1] = cv.take(L.n3 * L.es);
+      L.gv = (double*)cv.take(L.n3 * 8);
+      L.scales = (double*)cv.take((size_t)(L.bw_T / o.check_every + 2) * sizeof(double));
+    }
+    if (lats) lats->push_back(L);
+  }
+  *batch_bytes = batched_workspace_bytes(d, count);
+  *batch_ws = cv.take(*batch_bytes);
+}
+
+}  // namespace
+
+struct fdtd_context {
+  std::vector<Lat> lats;
+  fdtd_options o{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* staging = nullptr;
+  int32_t* flags = nullptr;
+  void* batch_ws = nullptr;
+  size_t batch_bytes = 0;
+  std::string err;
+  fdtd_stats stats{};
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  int check_seq = 0;
+};
+
+namespace {
+
+int fail(fdtd_context* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(fdtd_context* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return FDTD_OK;
+}
+
+int lat_check(fdtd_context* c, int lat) {
+  if (!c) return FDTD_ERR_INVALID_ARG;
+  if (lat < 0 || lat >= (int)c->lats.size()) return fail(c, FDTD_ERR_INVALID_ARG, "lattice index out of range");
+  return FDTD_OK;
+}
+
+// ---- profiling of the stencil launches --------------------------------------
+void prof_begin(fdtd_context* c) {
+  if (!c->profiling) return;
+  while (c->ev.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev.push_back(e);
+  }
+  cudaEventRecord(c->ev[c->ev_used], c->st);
+}
+void prof_end(fdtd_context* c) {
+  if (!c->profiling) return;
+  cudaEventRecord(c->ev[c->ev_used + 1], c->st);
+  c->ev_used += 2;
+}
+void prof_collect(fdtd_context* c) {  // call after a stream synchronisation
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) c->stats.stencil_ms += ms;
+  }
+  c->ev_used = 0;
+}
+
+// ---- typed dispatch helpers ---------------------------------------------------
+template <typename F>
+void with_type(int prec, F&& f) {
+  if (prec == FDTD_F64)
+    f((double*)nullptr);
+  else if (prec == FDTD_F32)
+    f((float*)nullptr);
+  else
+    f((__nv_bfloat16*)nullptr);
+}
+
+// Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows).
+void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
+  const int prec = L.d.precision;
+  int depth = c->o.temporal_depth;
+  if (depth == 0) depth = auto_depth(L.d.n, prec);
+  while (count > 0) {
+    int k = (int)std::min<int64_t>(count, prec == FDTD_F64 ? 1 : depth);
+    prof_begin(c);
+    if (prec == FDTD_F64) {
+      launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
+    } else if (prec == FDTD_F32) {
+      launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
+                             c->st);
+    } else {
+      launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
+                                     (const float*)L.v, L.p, active, c->st);
+    }
+    prof_end(c);
+    c->stats.launches += 1;
+    c->stats.stencil_launches += 1;
+    c->stats.stencil_site_updates += (int64_t)L.n3 * k;
+    // algorithmic bytes: psi read + psi write + V read once per launch
+    c->stats.stencil_bytes += (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0));
+    L.cur ^= 1;
+    count -= k;
+  }
+}
+
+int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* active) {
+  int np = 0;
+  with_type(L.d.precision, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    np = launch_sums<T>((const T*)psi, L.v, L.p, L.partials, active, c->st);
+  });
+  c->stats.launches += 1;
+  return np;
+}
+
+void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int mask, const LatState* s, int id,
+                      int out_idx, LatState* sw) {
+  with_type(L.d.precision, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    launch_scale_parity<T>((const T*)in, (T*)out, L.d.n, mask, s, id, out_idx, sw, c->st);
+  });
+  c->stats.launches += 1;
+}
+
+// One check of Secs. III-V on psi[cur]: sums, finalize, renormalise + mask.
+void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
+  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st);
+  c->stats.launches += 1;
+  int mask = c->o.reimpose_parity ? L.mask : 0;
+  scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], check_id, 1 - L.cur, &L.state[0]);
+  L.cur ^= 1;
+}
+
+int read_state(fdtd_context* c, Lat& L) {
+  cudaMemcpyAsync(&L.host_state, &L.state[0], sizeof(LatState), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("evolve: ") + cudaGetErrorString(e));
+  prof_collect(c);
+  return FDTD_OK;
+}
+
+int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
+  launch_state_reset(&L.state[0], 0, c->st);
+  c->stats.launches += 1;
+  const int64_t ce = c->o.check_every;
+  int64_t t = 0;
+  int check_id = 0;
+  int groups = 2;
+  bool done = false;
+  while (!done) {
+    for (int g = 0; g < groups && !done; ++g) {
+      enqueue_check(c, L, check_id++, t);
+      if (t >= max_steps) {
+        done = true;
+        break;
+      }
+      int64_t nst = std::min<int64_t>(ce, max_steps - t);
+      run_steps(c, L, nst, &L.state[0].active);
+      t += nst;
+    }
+    int rc = cuda_check(c, "evolve launch");
+    if (rc) return rc;
+    rc = read_state(c, L);
+    if (rc) return rc;
+    if (!L.host_state.active) done = true;
+    groups = std::min(groups * 2, 64);
+  }
+  if (L.host_state.status == STATUS_NONFINITE)
+    return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+  L.cur = L.host_state.cur;
+  L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+  return FDTD_OK;
+}
+
+void fill_obs(const Lat& L, const LatState& s, fdtd_obs* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->energy = s.energy;
+  out->binding_energy = s.ebind;
+  out->norm = s.s0 * L.p.a * L.p.a * L.p.a;
+  out->r2 = s.r2;
+  out->r_rms = std::sqrt(std::max(0.0, s.r2));
+  out->v_expect = s.vexp;
+  out->delta_e = s.delta_e;
+}
+
+// Copy n3 elements of dtype `dt` from user memory into a typed device
+// buffer of lattice precision `prec` (through the staging buffer for host
+// memory).
+int import_field(fdtd_context* c, const void* src, int dt, int mem, void* dst, int prec, size_t n3) {
+  const size_t isz = dt == FDTD_F64 ? 8 : 4;
+  auto convert = [&](const void* s, size_t count, size_t off) {
+    with_type(prec, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      if (dt == FDTD_F64)
+        launch_convert<double, T>((const double*)s, (T*)dst + off, count, c->st);
+      else
+        launch_convert<float, T>((const float*)s, (T*)dst + off, count, c->st);
+    });
+    c->stats.launches += 1;
+  };
+  if (mem == FDTD_MEM_DEVICE) {
+    convert(src, n3, 0);
+  } else {
+    const size_t chunk = kStagingBytes / isz;
+    for (size_t off = 0; off < n3; off += chunk) {
+      size_t cnt = std::min(chunk, n3 - off);
+      cudaMemcpyAsync(c->staging, (const char*)src + off * isz, cnt * isz, cudaMemcpyHostToDevice, c->st);
+      convert(c->staging, cnt, off);
+    }
+  }
+  return cuda_check(c, "import");
+}
+
+int export_field(fdtd_context* c, const void* src, int prec, void* dst, int dt, int mem, size_t n3) {
+  const size_t osz = dt == FDTD_F64 ? 8 : 4;
+  auto convert = [&](void* d, size_t count, size_t off) {
+    with_type(prec, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      if (dt == FDTD_F64)
+        launch_convert<T, double>((const T*)src + off, (double*)d, count, c->st);
+      else
+        launch_convert<T, float>((const T*)src + off, (float*)d, count, c->st);
+    });
+    c->stats.launches += 1;
+  };
+  if (mem == FDTD_MEM_DEVICE) {
+    convert(dst, n3, 0);
+  } else {
+    const size_t chunk = kStagingBytes / osz;
+    for (size_t off = 0; off < n3; off += chunk) {
+      size_t cnt = std::min(chunk, n3 - off);
+      convert(c->staging, cnt, off);
+      cudaMemcpyAsync((char*)dst + off * osz, c->staging, cnt * osz, cudaMemcpyDeviceToHost, c->st);
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+  return cuda_check(c, "export");
+}
+
+int evolve_batched(fdtd_context* c, int64_t) {
+  return fail(c, FDTD_ERR_INVALID_ARG, "evolve: batched mode is not available in this build");
+}
+
+int valid_mask(int mask) {
+  if (mask < 0 || mask >= 64) return 0;
+  for (int ax = 0; ax < 3; ++ax)
+    if (((mask >> (2 * ax)) & 3) == 3) return 0;
+  return 1;
+}
+
+void record_start(fdtd_context* c, Lat& L) {
+  if (L.psi0) {
+    cudaMemcpyAsync(L.psi0, L.psi[L.cur], L.n3 * L.es, cudaMemcpyDeviceToDevice, c->st);
+    L.has_psi0 = true;
+  }
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+int fdtd_default_options(fdtd_options* o) {
+  if (!o) return FDTD_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->check_every = 100;
+  o->tol = 1e-6;
+  o->tol_relative = 1;
+  o->temporal_depth = 0;
+  o->backward_steps = 0;
+  o->batched = 0;
+  o->reimpose_parity = 1;
+  return FDTD_OK;
+}
+
+int fdtd_workspace_size(const fdtd_lattice_desc* d, int count, const fdtd_options* o, size_t* bytes) {
+  if (!d || count < 1 || !bytes) {
+    g_create_err = "workspace_size: null descriptor/out or count < 1";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  fdtd_options oo;
+  if (o)
+    oo = *o;
+  else
+    fdtd_default_options(&oo);
+  std::string err;
+  int rc = check_options(oo, err);
+  for (int l = 0; rc == FDTD_OK && l < count; ++l) rc = check_desc(d[l], err);
+  if (rc) {
+    g_create_err = err;
+    return rc;
+  }
+  Carve cv;
+  void* s;
+  int32_t* f;
+  void* bw;
+  size_t bb;
+  layout(d, count, oo, cv, nullptr, &s, &f, &bw, &bb);
+  *bytes = cv.off + 256;
+  return FDTD_OK;
+}
+
+int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, void* ws, size_t ws_bytes,
+                void* stream, fdtd_handle* out) {
+  if (!out) {
+    g_create_err = "create: null output handle";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  size_t need = 0;
+  int rc = fdtd_workspace_size(d, count, o, &need);
+  if (rc) return rc;
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < need) {
+    g_create_err = "workspace null, not 256-byte aligned, or smaller than fdtd_workspace_size()";
+    return FDTD_ERR_WORKSPACE;
+  }
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ws) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    g_create_err = "workspace is not device memory";
+    return FDTD_ERR_WORKSPACE;
+  }
+  fdtd_context* c = new fdtd_context();
+  if (o)
+    c->o = *o;
+  else
+    fdtd_default_options(&c->o);
+  c->st = (cudaStream_t)stream;
+  c->ws = (char*)ws;
+  c->ws_bytes = ws_bytes;
+  cudaGetDevice(&c->device);
+  Carve cv;
+  cv.base = c->ws;
+  layout(d, count, c->o, cv, &c->lats, &c->staging, &c->flags, &c->batch_ws, &c->batch_bytes);
+  for (auto& L : c->lats) {
+    launch_state_reset(&L.state[0], 1, c->st);
+    launch_state_reset(&L.state[1], 1, c->st);
+    c->stats.launches += 2;
+  }
+  if (cuda_check(c, "create")) {
+    g_create_err = c->err;
+    delete c;
+    return FDTD_ERR_CUDA;
+  }
+  *out = c;
+  return FDTD_OK;
+}
+
+int fdtd_destroy(fdtd_handle h) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->st);
+  for (auto e : h->ev) cudaEventDestroy(e);
+  delete h;
+  return FDTD_OK;
+}
+
+const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!v || (dtype != FDTD_F64 && dtype != FDTD_F32) || (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
+    return fail(h, FDTD_ERR_INVALID_ARG, "set_potential: null pointer, bad dtype or mem_kind");
+  Lat& L = h->lats[lat];
+  cudaMemsetAsync(h->flags, 0, sizeof(int32_t), h->st);
+  const size_t isz = dtype == FDTD_F64 ? 8 : 4;
+  float* vf = L.d.precision == FDTD_F64 ? nullptr : (float*)L.v;
+  double* vd = L.d.precision == FDTD_F64 ? (double*)L.v : nullptr;
+  auto conv = [&](const void* src, size_t cnt, size_t off) {
+    if (dtype == FDTD_F64)
+      launch_set_potential<double>((const double*)src, cnt, off, vf, vd, L.coefA, L.coefCB, L.p, h->flags, h->st);
+    else
+      launch_set_potential<float>((const float*)src, cnt, off, vf, vd, L.coefA, L.coefCB, L.p, h->flags, h->st);
+    h->stats.launches += 1;
+  };
+  if (mem_kind == FDTD_MEM_DEVICE) {
+    conv(v, L.n3, 0);
+  } else {
+    const size_t chunk = kStagingBytes / isz;
+    for (size_t off = 0; off < L.n3; off += chunk) {
+      size_t cnt = std::min(chunk, L.n3 - off);
+      cudaMemcpyAsync(h->staging, (const char*)v + off * isz, cnt * isz, cudaMemcpyHostToDevice, h->st);
+      conv(h->staging, cnt, off);
+    }
+  }
+  int32_t flags = 0;
+  cudaMemcpyAsync(&flags, h->flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("set_potential: ") + cudaGetErrorString(e));
+  if ((rc = cuda_check(h, "set_potential"))) return rc;
+  if (flags & 1) return fail(h, FDTD_ERR_NONFINITE, "set_potential: NaN or Inf in V");
+  if (flags & 2) return fail(h, FDTD_ERR_UNSTABLE_DT, "set_potential: 1 + dtau V / 2 <= 0 at some site");
+  L.has_v = true;
+  return FDTD_OK;
+}
+
+int fdtd_init_symmetric(fdtd_handle h, int lat, uint64_t seed, int parity_mask, int dist) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!valid_mask(parity_mask) || (dist != FDTD_DIST_UNIFORM && dist != FDTD_DIST_GAUSSIAN))
+    return fail(h, FDTD_ERR_INVALID_ARG, "init_symmetric: bad parity mask or distribution");
+  Lat& L = h->lats[lat];
+  with_type(L.d.precision, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    launch_init_random<T>((T*)L.psi[0], L.d.n, seed, (uint64_t)lat, dist, h->st);
+  });
+  h->stats.launches += 1;
+  L.cur = 0;
+  if (parity_mask) {
+    scale_parity_any(h, L, L.psi[0], L.psi[1], parity_mask, nullptr, 0, 1, nullptr);
+    L.cur = 1;
+  }
+  L.mask = parity_mask;
+  L.has_psi = true;
+  record_start(h, L);
+  return cuda_check(h, "init_symmetric");
+}
+
+int fdtd_set_psi(fdtd_handle h, int lat, const void* psi, int dtype, int mem_kind, int parity_mask) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32) ||
+      (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE) || !valid_mask(parity_mask))
+    return fail(h, FDTD_ERR_INVALID_ARG, "set_psi: null pointer, bad dtype, mem_kind or mask");
+  Lat& L = h->lats[lat];
+  if ((rc = import_field(h, psi, dtype, mem_kind, L.psi[L.cur], L.d.precision, L.n3))) return rc;
+  L.mask = parity_mask;
+  L.has_psi = true;
+  record_start(h, L);
+  return cuda_check(h, "set_psi");
+}
+
+int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_kind) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32) || (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
+    return fail(h, FDTD_ERR_INVALID_ARG, "get_psi: null pointer, bad dtype or mem_kind");
+  Lat& L = h->lats[lat];
+  if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "get_psi: no wavefunction yet");
+  return export_field(h, L.psi[L.cur], L.d.precision, psi, dtype, mem_kind, L.n3);
+}
+
+int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (max_steps < 0) return fail(h, FDTD_ERR_INVALID_ARG, "evolve: max_steps < 0");
+  for (auto& L : h->lats)
+    if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "evolve: set_potential and init/set_psi first");
+  int rc = FDTD_OK;
+  if (h->o.batched) {
+    rc = evolve_batched(h, max_steps);
+  } else {
+    for (auto& L : h->lats) {
+      rc = evolve_one(h, L, max_steps);
+      if (rc) return rc;
+    }
+  }
+  if (rc) return rc;
+  int64_t mx = 0;
+  bool all_conv = true;
+  for (auto& L : h->lats) {
+    mx = std::max(mx, L.last_steps);
+    all_conv = all_conv && L.host_state.converged;
+  }
+  if (steps_done) *steps_done = mx;
+  return (h->o.tol > 0.0 && !all_conv) ? FDTD_NOT_CONVERGED : FDTD_OK;
+}
+
+int fdtd_last_check(fdtd_handle h, int lat, fdtd_obs* out) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!out) return fail(h, FDTD_ERR_INVALID_ARG, "last_check: null output");
+  Lat& L = h->lats[lat];
+  cudaMemcpyAsync(&L.host_state, &L.state[0], sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("last_check: ") + cudaGetErrorString(e));
+  fill_obs(L, L.host_state, out);
+  out->steps = L.last_steps;
+  out->converged = L.host_state.converged;
+  out->checks = L.host_state.checks;
+  return FDTD_OK;
+}
+
+int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!out) return fail(h, FDTD_ERR_INVALID_ARG, "observables: null output");
+  Lat& L = h->lats[lat];
+  if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "observables: set_potential and init/set_psi first");
+  int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
+  launch_state_reset(&L.state[1], 0, h->st);
+  launch_finalize(&L.state[1], L.partials, np, 0, 0, L.p, L.d.v_inf, 0.0, 0, 1, h->st);
+  h->stats.launches += 2;
+  LatState s;
+  cudaMemcpyAsync(&s, &L.state[1], sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("observables: ") + cudaGetErrorString(e));
+  if ((rc = cuda_check(h, "observables"))) return rc;
+  if (s.status == STATUS_NONFINITE) return fail(h, FDTD_ERR_NONFINITE, "observables: non-finite or zero norm");
+  fill_obs(L, s, out);
+  out->steps = L.last_steps;
+  out->converged = L.host_state.converged;
+  out->checks = L.host_state.checks;
+  return FDTD_OK;
+}
+
+int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
+  int rc = lat_check(src, lat_src);
+  if (rc) return rc;
+  if ((rc = lat_check(dst, lat_dst))) return rc;
+  Lat& S = src->lats[lat_src];
+  Lat& D = dst->lats[lat_dst];
+  if (D.d.n != 2 * S.d.n || std::fabs(D.d.length - S.d.length) > 1e-12 * S.d.length)
+    return fail(dst, FDTD_ERR_SHAPE, "upsample: need n_dst = 2 n_src and equal box lengths");
+  if (!S.has_psi) return fail(dst, FDTD_ERR_STATE, "upsample: source has no wavefunction");
+  if (!D.has_v) return fail(dst, FDTD_ERR_STATE, "upsample: set the destination potential first");
+  if (src->st != dst->st) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, src->st);
+    cudaStreamWaitEvent(dst->st, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  void* tmp = D.psi[1 - D.cur];
+  with_type(S.d.precision, [&](auto* tin) {
+    using Ti = std::remove_pointer_t<decltype(tin)>;
+    with_type(D.d.precision, [&](auto* tout) {
+      using To = std::remove_pointer_t<decltype(tout)>;
+      launch_upsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, dst->st);
+    });
+  });
+  dst->stats.launches += 1;
+  // renormalise and give the field the source's symmetry (Sec. VI)
+  int id = 1000000 + (dst->check_seq++);
+  int np = launch_sums_any(dst, D, tmp, nullptr);
+  launch_state_reset(&D.state[1], 0, dst->st);
+  launch_finalize(&D.state[1], D.partials, np, id, 0, D.p, D.d.v_inf, 0.0, 0, 0, dst->st);
+  scale_parity_any(dst, D, tmp, D.psi[D.cur], S.mask, &D.state[1], id, D.cur, nullptr);
+  dst->stats.launches += 2;
+  D.mask = S.mask;
+  D.has_psi = true;
+  record_start(dst, D);
+  LatState s;
+  cudaMemcpyAsync(&s, &D.state[1], sizeof(LatState), cudaMemcpyDeviceToHost, dst->st);
+  cudaError_t e = cudaStreamSynchronize(dst->st);
+  if (e != cudaSuccess) return fail(dst, FDTD_ERR_CUDA, std::string("upsample: ") + cudaGetErrorString(e));
+  if (s.status == STATUS_NONFINITE) return fail(dst, FDTD_ERR_NONFINITE, "upsample: non-finite or zero norm");
+  return cuda_check(dst, "upsample");
+}
+
+int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, void* gv_out, int dtype, int mem_kind,
+                  fdtd_obs* obs) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  Lat& L = h->lats[lat];
+  if (!gv_out || (dtype != FDTD_F64 && dtype != FDTD_F32) ||
+      (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE) || T < 1 || !std::isfinite(w_e) ||
+      !std::isfinite(w_r))
+    return fail(h, FDTD_ERR_INVALID_ARG, "backward: bad pointer, dtype, mem_kind, T or weights");
+  if (L.d.precision == FDTD_BF16) return fail(h, FDTD_ERR_INVALID_ARG, "backward: not available for BF16 storage");
+  if (!L.psi0 || T > L.bw_T)
+    return fail(h, FDTD_ERR_WORKSPACE, "backward: T exceeds options.backward_steps given at create");
+  if (!L.has_v || !L.has_psi0) return fail(h, FDTD_ERR_STATE, "backward: set_potential and init/set_psi first");
+  const int64_t ce = h->o.check_every;
+  const int K = L.bw_K;
+  const int mask = h->o.reimpose_parity ? L.mask : 0;
+  const size_t fb = L.n3 * L.es;
+  auto field = [&](void* base, int64_t i) { return (void*)((char*)base + (size_t)i * fb); };
+  LatState* scratch = &L.state[1];
+  launch_state_reset(scratch, 0, h->st);
+  h->stats.launches += 1;
+
+  // forward pass from the recorded start, saving every K-th field
+  L.cur = 0;
+  cudaMemcpyAsync(L.psi[0], L.psi0, fb, cudaMemcpyDeviceToDevice, h->st);
+  for (int64_t t = 0; t < T; ++t) {
+    if (t % ce == 0) {
+      int id = 2000000 + (h->check_seq++);
+      int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
+      launch_finalize(scratch, L.partials, np, id, t, L.p, 0.0, 0.0, 0, 0, h->st);
+      launch_store_scale(scratch, L.scales + t / ce, h->st);
+      scale_parity_any(h, L, L.psi[L.cur], L.psi[1 - L.cur], mask, scratch, id, 1 - L.cur, nullptr);
+      h->stats.launches += 2;
+      L.cur ^= 1;
+    }
+    if (t % K == 0)
+      cudaMemcpyAsync(field(L.pool, t / K), L.psi[L.cur], fb, cudaMemcpyDeviceToDevice, h->st);
+    run_steps(h, L, 1, nullptr);
+  }
+  // seed the adjoint with the derivative of the loss at psi_T
+  int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
+  launch_finalize(scratch, L.partials, np, 0, T, L.p, 0.0, 0.0, 0, 1, h->st);
+  h->stats.launches += 1;
+  int lc = 0;
+  with_type(L.d.precision, [&](auto* tag) {
+    using T_ = std::remove_pointer_t<decltype(tag)>;
+    if constexpr (!std::is_same_v<T_, __nv_bfloat16>)
+      launch_adjoint_seed<T_>((const T_*)L.psi[L.cur], L.v, scratch, w_e, w_r, (T_*)L.lam[0], L.gv, L.p, h->st);
+  });
+  h->stats.launches += 1;
+  void* tmp = L.psi[1 - L.cur];  // psi[cur] keeps psi_T
+  for (int64_t sgi = (T - 1) / K; sgi >= 0; --sgi) {
+    const int64_t t0 = sgi * K, t1 = std::min<int64_t>(t0 + K, T);
+    cudaMemcpyAsync(field(L.seg, 0), field(L.pool, sgi), fb, cudaMemcpyDeviceToDevice, h->st);
+    for (int64_t t = t0; t + 1 < t1; ++t) {
+      with_type(L.d.precision, [&](auto* tag) {
+        using T_ = std::remove_pointer_t<decltype(tag)>;
+        void* nxt = ((t + 1) % ce == 0) ? tmp : field(L.seg, t + 1 - t0);
+        if constexpr (std::is_same_v<T_, double>)
+          launch_step_f64((const double*)field(L.seg, t - t0), (double*)nxt, L.coefA, L.coefCB, L.p, nullptr, h->st);
+        else if constexpr (std::is_same_v<T_, float>)
+          launch_step_f32<float>((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr,
+                                 h->st);
+        if constexpr (!std::is_same_v<T_, __nv_bfloat16>)
+          if ((t + 1) % ce == 0)
+            launch_scale_parity_from<T_>((const T_*)tmp, (T_*)field(L.seg, t + 1 - t0), L.d.n, mask,
+                                         L.scales + (t + 1) / ce, h->st);
+      });
+      h->stats.launches += ((t + 1) % ce == 0) ? 2 : 1;
+    }
+    for (int64_t t = t1; t > t0; --t) {
+      with_type(L.d.precision, [&](auto* tag) {
+        using T_ = std::remove_pointer_t<decltype(tag)>;
+        if constexpr (!std::is_same_v<T_, __nv_bfloat16>) {
+          launch_adjoint_step<T_>((const T_*)L.lam[lc], (T_*)L.lam[1 - lc], (const T_*)field(L.seg, t - 1 - t0), L.v,
+                                  L.coefA, L.coefCB, L.gv, L.p, h->st);
+          if ((t - 1) % ce == 0)
+            launch_parity_adjoint_scale<T_>((T_*)L.lam[1 - lc], L.d.n, mask, L.scales + (t - 1) / ce, h->st);
+        }
+      });
+      h->stats.launches += ((t - 1) % ce == 0) ? 2 : 1;
+      lc ^= 1;
+    }
+  }
+  if ((rc = cuda_check(h, "backward"))) return rc;
+  if (obs) {
+    LatState s;
+    cudaMemcpyAsync(&s, scratch, sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    fill_obs(L, s, obs);
+    obs->steps = T;
+  }
+  return export_field(h, L.gv, FDTD_F64, gv_out, dtype, mem_kind, L.n3);
+}
+
+int fdtd_get_stats(fdtd_handle h, fdtd_stats* out) {
+  if (!h || !out) return FDTD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->st);
+  prof_collect(h);
+  *out = h->stats;
+  return FDTD_OK;
+}
+
+int fdtd_reset_stats(fdtd_handle h) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->st);
+  h->ev_used = 0;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  return FDTD_OK;
+}
+
+int fdtd_set_profiling(fdtd_handle h, int on) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->st);
+  prof_collect(h);
+  h->profiling = on != 0;
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Adjoint kernels for gradients with respect to the potential V through the
+// unrolled update of Eq. updateeq.
+//
+// The step is linear in psi, psi' = M psi with
+//   M = diag(A) + c diag(B) Adj - 6c diag(B),   Adj = sum of the 6 neighbours,
+// and Adj is symmetric under the zero boundary, so
+//   M^T lam = A lam + c [ Adj(B lam) - 6 B lam ].
+// Differentiating (1 + h) psi' = (1 - h) psi + c (Adj - 6) psi, h = dtau V/2,
+// at one site gives  d psi'(s)/d V(s) = -(dtau/2) B(s) (psi'(s) + psi(s)),
+// equivalently  dA/dV psi + dB/dV c (Adj - 6) psi  with dA/dV = -dtau B^2,
+// dB/dV = -(dtau/2) B^2; the kernels use the latter form on psi_t alone.
+//
+// These kernels are one thread per site with cached global loads: the
+// backward pass is a minor share of any run.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fdtd {
+
+static int grid_1d(size_t total) {
+  size_t b = (total + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__device__ __forceinline__ double ldz(const T* p, int x, int y, int z, int n) {
+  if ((unsigned)x < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)z < (unsigned)n)
+    return (double)Store<T>::to(p[site_index(x, y, z, n)]);
+  return 0.0;
+}
+
+// B at a site: FP64 lattices from the stored c B, FP32 from V as the forward does.
+template <typename T>
+__device__ __forceinline__ double b_at(const void* v, const double* coefCB, size_t i, const Params& p) {
+  if constexpr (sizeof(T) == 8) {
+    return coefCB[i] / p.c;
+  } else {
+    return (double)coef_f32(((const float*)v)[i], p.half_dtau_f, p.one_m6c_f).b;
+  }
+}
+
+template <typename T>
+__global__ void k_adjoint_step(const T* __restrict__ lam, T* __restrict__ lam_out, const T* __restrict__ psi,
+                               const void* __restrict__ v, const double* __restrict__ coefA,
+                               const double* __restrict__ coefCB, double* __restrict__ gv, Params p) {
+  const int n = p.n;
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
+    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+    double bl_sum = 0.0, psi_sum = 0.0;
+    for (int q = 0; q < 6; ++q) {
+      int xx = x + dx[q], yy = y + dy[q], zz = z + dz[q];
+      if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n) {
+        size_t j = site_index(xx, yy, zz, n);
+        bl_sum += b_at<T>(v, coefCB, j, p) * (double)Store<T>::to(lam[j]);
+        psi_sum += (double)Store<T>::to(psi[j]);
+      }
+    }
+    double l = (double)Store<T>::to(lam[i]);
+    double ps = (double)Store<T>::to(psi[i]);
+    double b = b_at<T>(v, coefCB, i, p);
+    double A;
+    if constexpr (sizeof(T) == 8) {
+      A = coefA[i];
+    } else {
+      CoefF k = coef_f32(((const float*)v)[i], p.half_dtau_f, p.one_m6c_f);
+      A = (double)k.b * ((double)k.alpha + 6.0 * (double)p.c_f);
+    }
+    double cc = (sizeof(T) == 8) ? p.c : (double)p.c_f;
+    double out = A * l + cc * (bl_sum - 6.0 * b * l);
+    double lap = psi_sum - 6.0 * ps;
+    gv[i] += l * (-p.dtau * b * b * ps - 0.5 * p.dtau * b * b * cc * lap);
+    if constexpr (sizeof(T) == 8)
+      lam_out[i] = out;
+    else
+      lam_out[i] = Store<T>::from((float)out);
+  }
+}
+
+template <typename T>
+void launch_adjoint_step(const T* lam_in, T* lam_out, const T* psi_prev, const void* v, const double* coefA,
+                         const double* coefCB, double* gv, const Params& p, cudaStream_t st) {
+  size_t total = (size_t)p.n * p.n * p.n;
+  k_adjoint_step<T><<<grid_1d(total), 256, 0, st>>>(lam_in, lam_out, psi_prev, v, coefA, coefCB, gv, p);
+}
+template void launch_adjoint_step<double>(const double*, double*, const double*, const void*, const double*,
+                                          const double*, double*, const Params&, cudaStream_t);
+template void launch_adjoint_step<float>(const float*, float*, const float*, const void*, const double*,
+                                         const double*, double*, const Params&, cudaStream_t);
+
+// Seed at T:  lam = w_e 2 (H psi - E psi) / S0 + w_r 2 (r^2 - <r^2>) psi / S0,
+// and the direct term gv = w_e psi^2 / S0 (E depends on V explicitly).
+template <typename T>
+__global__ void k_adjoint_seed(const T* __restrict__ psi, const void* __restrict__ v, const LatState* __restrict__ s,
+                               double w_e, double w_r, T* __restrict__ lam, double* __restrict__ gv, Params p) {
+  const int n = p.n;
+  const size_t total = (size_t)n * n * n;
+  const double s0 = s->s0, e = s->energy, r2m = s->r2;
+  const double kfac = 1.0 / (2.0 * p.mass * p.a * p.a);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
+    double c = (double)Store<T>::to(psi[i]);
+    double nb = ldz(psi, x - 1, y, z, n) + ldz(psi, x + 1, y, z, n) + ldz(psi, x, y - 1, z, n) +
+                ldz(psi, x, y + 1, z, n) + ldz(psi, x, y, z - 1, n) + ldz(psi, x, y, z + 1, n);
+    double vv = (sizeof(T) == 8) ? ((const double*)v)[i] : (double)((const float*)v)[i];
+    double hpsi = -kfac * (nb - 6.0 * c) + vv * c;
+    double px = coord_f64(x, n, p.a), py = coord_f64(y, n, p.a), pz = coord_f64(z, n, p.a);
+    double r2 = px * px + py * py + pz * pz;
+    double l = w_e * 2.0 * (hpsi - e * c) / s0 + w_r * 2.0 * (r2 - r2m) * c / s0;
+    gv[i] = w_e * c * c / s0;
+    if constexpr (sizeof(T) == 8)
+      lam[i] = l;
+    else
+      lam[i] = Store<T>::from((float)l);
+  }
+}
+template <typename T>
+void launch_adjoint_seed(const T* psi, const void* v, const LatState* s, double w_e, double w_r, T* lam, double* gv,
+                         const Params& p, cudaStream_t st) {
+  size_t total = (size_t)p.n * p.n * p.n;
+  k_adjoint_seed<T><<<grid_1d(total), 256, 0, st>>>(psi, v, s, w_e, w_r, lam, gv, p);
+}
+template void launch_adjoint_seed<double>(const double*, const void*, const LatState*, double, double, double*,
+                                          double*, const Params&, cudaStream_t);
+template void launch_adjoint_seed<float>(const float*, const void*, const LatState*, double, double, float*,
+                                         double*, const Params&, cudaStream_t);
+
+// Transpose of the check  psi <- P(s psi):  lam <- s P^T lam.
+// P sends the value at a source site q (lower half along every masked axis,
+// or the central plane of an S_i axis) to q and to each of its mirror images
+// o with sign sg(o); P^T gathers sum_o sg(o) lam(o) back onto q and leaves 0
+// on every non-source site.  In place: every site is read only by the
+// thread of its own source.
+template <typename T>
+__global__ void k_parity_adjoint_scale(T* __restrict__ lam, int n, int mask, const double* __restrict__ scale) {
+  const double s = scale ? *scale : 1.0;
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / ((size_t)n * n))};
+    bool source = true;
+    int img_axes = 0;  // axes along which q has a distinct mirror image
+    double sgn_ax[3] = {1.0, 1.0, 1.0};
+    for (int ax = 0; ax < 3; ++ax) {
+      int mode = (mask >> (2 * ax)) & 3;
+      if (mode == 0) continue;
+      int mm = n - 1 - c[ax];
+      if (c[ax] > mm || (c[ax] == mm && mode == 2)) source = false;
+      if (c[ax] < mm) img_axes |= 1 << ax;
+      sgn_ax[ax] = (mode == 2) ? -1.0 : 1.0;
+    }
+    if (!source) continue;  // zeroed below by its own source thread
+    double acc = 0.0;
+    for (int sub = 0; sub < 8; ++sub) {
+      if (sub & ~img_axes) continue;
+      int o[3] = {c[0], c[1], c[2]};
+      double sg = 1.0;
+      for (int ax = 0; ax < 3; ++ax)
+        if (sub & (1 << ax)) {
+          o[ax] = n - 1 - c[ax];
+          sg *= sgn_ax[ax];
+        }
+      size_t j = site_index(o[0], o[1], o[2], n);
+      acc += sg * (double)Store<T>::to(lam[j]);
+      if (sub) lam[j] = Store<T>::from(0.0f);
+    }
+    // non-source sites that are not a mirror image of any source (central
+    // planes of A_i axes) are zeroed here as well
+    double val = s * acc;
+    if constexpr (sizeof(T) == 8)
+      lam[i] = val;
+    else
+      lam[i] = Store<T>::from((float)val);
+  }
+}
+
+template <typename T>
+__global__ void k_zero_central_planes(T* __restrict__ lam, int n, int mask) {
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / ((size_t)n * n))};
+    for (int ax = 0; ax < 3; ++ax) {
+      int mode = (mask >> (2 * ax)) & 3;
+      if (mode == 2 && c[ax] == n - 1 - c[ax]) lam[i] = Store<T>::from(0.0f);
+    }
+  }
+}
+
+template <typename T>
+void launch_parity_adjoint_scale(T* lam, int n, int mask, const double* scale, cudaStream_t st) {
+  size_t total = (size_t)n * n * n;
+  if (mask && (n & 1)) k_zero_central_planes<T><<<grid_1d(total), 256, 0, st>>>(lam, n, mask);
+  k_parity_adjoint_scale<T><<<grid_1d(total), 256, 0, st>>>(lam, n, mask, scale);
+}
+template void launch_parity_adjoint_scale<double>(double*, int, int, const double*, cudaStream_t);
+template void launch_parity_adjoint_scale<float>(float*, int, int, const double*, cudaStream_t);
+
+__global__ void k_store_scale(const LatState* s, double* dst) { *dst = s->scale; }
+void launch_store_scale(const LatState* s, double* dst, cudaStream_t st) { k_store_scale<<<1, 1, 0, st>>>(s, dst); }
+
+// Recompute pass of the checkpointed forward: out = P(scale * in) with the
+// factor saved by the first forward pass.
+template <typename T>
+__global__ void k_scale_parity_from(const T* __restrict__ in, T* __restrict__ out, int n, int mask,
+                                    const double* __restrict__ scale) {
+  const double s = *scale;
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / ((size_t)n * n))};
+    double sign = 1.0;
+    bool zero = false;
+    for (int ax = 0; ax < 3; ++ax) {
+      int mode = (mask >> (2 * ax)) & 3;
+      if (mode == 0) continue;
+      int mm = n - 1 - c[ax];
+      if (c[ax] > mm) {
+        c[ax] = mm;
+        if (mode == 2) sign = -sign;
+      } else if (c[ax] == mm && mode == 2) {
+        zero = true;
+      }
+    }
+    double val = zero ? 0.0 : sign * ((double)Store<T>::to(in[site_index(c[0], c[1], c[2], n)]) * s);
+    if constexpr (sizeof(T) == 8)
+      out[i] = val;
+    else
+      out[i] = Store<T>::from((float)val);
+  }
+}
+template <typename T>
+void launch_scale_parity_from(const T* in, T* out, int n, int mask, const double* scale, cudaStream_t st) {
+  size_t total = (size_t)n * n * n;
+  k_scale_parity_from<T><<<grid_1d(total), 256, 0, st>>>(in, out, n, mask, scale);
+}
+template void launch_scale_parity_from<double>(const double*, double*, int, int, const double*, cudaStream_t);
+template void launch_scale_parity_from<float>(const float*, float*, int, int, const double*, cudaStream_t);
+
+}  // namespace fdtd

@@ -1,0 +1,520 @@
+// Core FDTD kernels for sm_103a: the one-step 7-point update (Eq. updateeq),
+// the fused lattice sums of Eq. energysum, the check finaliser, the
+// renormalisation + symmetry pass (Secs. III-IV), the random start, the
+// multi-resolution transfer (Sec. VI) and the potential loader.
+//
+// The stencil and the sums share one traversal: a block of 32 x 8 threads
+// owns a 32 x 8 column of sites and walks `zc` consecutive z-planes.  Each
+// thread keeps psi(z-1), psi(z), psi(z+1) of its own column in registers
+// (the z-neighbours), exchanges x-neighbours by warp shuffles (a warp is one
+// x-row of the tile) and reads y-neighbours from a double-buffered shared
+// row tile; only the tile's rim is loaded twice.  Loads for plane z+1 are
+// issued one iteration ahead.  HBM traffic is the ideal one-read-one-write
+// of psi plus one read of V per site.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fdtd {
+
+constexpr int TX = 32, TY = 8;
+
+Tiling tiling_for(int n, int min_blocks) {
+  Tiling t;
+  int bx = (n + TX - 1) / TX, by = (n + TY - 1) / TY;
+  int zc = n;
+  while (zc > 8 && (long long)bx * by * ((n + zc - 1) / zc) < min_blocks) zc = (zc + 1) / 2;
+  t.zc = zc;
+  t.grid = dim3(bx, by, (n + zc - 1) / zc);
+  return t;
+}
+
+template <typename C>
+struct RowTile {
+  C r[2][TY + 2][TX];
+};
+
+template <typename T, typename Body>
+__device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, RowTile<typename Store<T>::C>& tile,
+                                       Body&& body) {
+  using C = typename Store<T>::C;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, n);
+  const bool act = (x < n) && (y < n);
+  auto ld = [&](int xx, int yy, int zz) -> C {
+    if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n)
+      return Store<T>::ld(in + site_index(xx, yy, zz, n));
+    return C(0);
+  };
+  const bool hy_lo = (ty == 0), hy_hi = (ty == TY - 1), hx_lo = (tx == 0), hx_hi = (tx == TX - 1);
+  const int hy = hy_lo ? y - 1 : y + 1;
+  C zm = ld(x, y, z0 - 1), c = ld(x, y, z0), zp = ld(x, y, z0 + 1);
+  C hyv = (hy_lo || hy_hi) ? ld(x, hy, z0) : C(0);
+  C hxm = hx_lo ? ld(x - 1, y, z0) : C(0);
+  C hxp = hx_hi ? ld(x + 1, y, z0) : C(0);
+  for (int z = z0; z < z1; ++z) {
+    C zpp = ld(x, y, z + 2);
+    C hyv_n = (hy_lo || hy_hi) ? ld(x, hy, z + 1) : C(0);
+    C hxm_n = hx_lo ? ld(x - 1, y, z + 1) : C(0);
+    C hxp_n = hx_hi ? ld(x + 1, y, z + 1) : C(0);
+    const int b = (z - z0) & 1;
+    tile.r[b][ty + 1][tx] = c;
+    if (hy_lo) tile.r[b][0][tx] = hyv;
+    if (hy_hi) tile.r[b][TY + 1][tx] = hyv;
+    C xm = __shfl_up_sync(0xffffffffu, c, 1);
+    C xp = __shfl_down_sync(0xffffffffu, c, 1);
+    if (hx_lo) xm = hxm;
+    if (hx_hi) xp = hxp;
+    __syncthreads();
+    C ym = tile.r[b][ty][tx], yp = tile.r[b][ty + 2][tx];
+    body(x, y, z, act, c, xm, xp, ym, yp, zm, zp);
+    zm = c;
+    c = zp;
+    zp = zpp;
+    hyv = hyv_n;
+    hxm = hxm_n;
+    hxp = hxp_n;
+  }
+}
+
+// ------------------------------------------------------------------ update
+__global__ void __launch_bounds__(TX* TY) k_step_f64(const double* __restrict__ in, double* __restrict__ out,
+                                                     const double* __restrict__ coefA,
+                                                     const double* __restrict__ coefCB, int n, int zc,
+                                                     const int32_t* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ RowTile<double> tile;
+  zmarch<double>(in, n, zc, tile,
+                 [&](int x, int y, int z, bool act, double c, double xm, double xp, double ym, double yp, double zm,
+                     double zp) {
+                   if (!act) return;
+                   size_t i = site_index(x, y, z, n);
+                   double s = nbr_sum(xm, xp, ym, yp, zm, zp);
+                   out[i] = update_f64(c, s, __ldg(coefA + i), __ldg(coefCB + i));
+                 });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T* __restrict__ out,
+                                                     const float* __restrict__ v, int n, int zc, float half_dtau,
+                                                     float one_m6c, float cc, const int32_t* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ RowTile<float> tile;
+  zmarch<T>(in, n, zc, tile,
+            [&](int x, int y, int z, bool act, float c, float xm, float xp, float ym, float yp, float zm, float zp) {
+              if (!act) return;
+              size_t i = site_index(x, y, z, n);
+              CoefF k = coef_f32(__ldg(v + i), half_dtau, one_m6c);
+              float s = nbr_sum(xm, xp, ym, yp, zm, zp);
+              out[i] = Store<T>::from(update_f32(c, s, k, cc));
+            });
+}
+
+void launch_step_f64(const double* in, double* out, const double* coefA, const double* coefCB, const Params& p,
+                     const int32_t* active, cudaStream_t st) {
+  Tiling t = tiling_for(p.n, 1216);
+  k_step_f64<<<t.grid, dim3(TX, TY), 0, st>>>(in, out, coefA, coefCB, p.n, t.zc, active);
+}
+
+template <typename T>
+void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st) {
+  Tiling t = tiling_for(p.n, 1216);
+  k_step_f32<T><<<t.grid, dim3(TX, TY), 0, st>>>(in, out, v, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
+}
+template void launch_step_f32<float>(const float*, float*, const float*, const Params&, const int32_t*, cudaStream_t);
+template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
+                                             const int32_t*, cudaStream_t);
+
+// ------------------------------------------------------------------ sums
+__device__ __forceinline__ void block_sum4_store(double v0, double v1, double v2, double v3, double* dst) {
+  __shared__ double red[TY][4];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, off);
+    v1 += __shfl_down_sync(0xffffffffu, v1, off);
+    v2 += __shfl_down_sync(0xffffffffu, v2, off);
+    v3 += __shfl_down_sync(0xffffffffu, v3, off);
+  }
+  if (threadIdx.x == 0) {
+    red[threadIdx.y][0] = v0;
+    red[threadIdx.y][1] = v1;
+    red[threadIdx.y][2] = v2;
+    red[threadIdx.y][3] = v3;
+  }
+  __syncthreads();
+  if (threadIdx.y == 0 && threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < TY; ++w) s += red[w][threadIdx.x];
+    size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    dst[b * 4 + threadIdx.x] = s;
+  }
+}
+
+// FP64: every term and sum in FP64.
+__global__ void __launch_bounds__(TX* TY) k_sums_f64(const double* __restrict__ psi, const double* __restrict__ v,
+                                                     int n, int zc, double a, double kfac, double* partials,
+                                                     const int32_t* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ RowTile<double> tile;
+  double s0 = 0, sh = 0, sr = 0, sv = 0;
+  zmarch<double>(psi, n, zc, tile,
+                 [&](int x, int y, int z, bool act, double c, double xm, double xp, double ym, double yp, double zm,
+                     double zp) {
+                   if (!act) return;
+                   size_t i = site_index(x, y, z, n);
+                   double vv = __ldg(v + i);
+                   double lap = __fma_rn(-6.0, c, nbr_sum(xm, xp, ym, yp, zm, zp));
+                   double px = coord_f64(x, n, a), py = coord_f64(y, n, a), pz = coord_f64(z, n, a);
+                   double c2 = c * c;
+                   s0 += c2;
+                   sh += c * (-kfac * lap + vv * c);
+                   sr += (px * px + py * py + pz * pz) * c2;
+                   sv += vv * c2;
+                 });
+  block_sum4_store(s0, sh, sr, sv, partials);
+}
+
+// FP32 / BF16 storage: per-site terms in FP32, Kahan-compensated FP32 runs
+// per thread, FP64 across threads and blocks.
+template <typename T>
+__global__ void __launch_bounds__(TX* TY) k_sums_f32(const T* __restrict__ psi, const float* __restrict__ v, int n,
+                                                     int zc, float a, float kfac, double* partials,
+                                                     const int32_t* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ RowTile<float> tile;
+  Kahan s0, sh, sr, sv;
+  zmarch<T>(psi, n, zc, tile,
+            [&](int x, int y, int z, bool act, float c, float xm, float xp, float ym, float yp, float zm, float zp) {
+              if (!act) return;
+              size_t i = site_index(x, y, z, n);
+              float vv = __ldg(v + i);
+              float lap = __fmaf_rn(-6.0f, c, nbr_sum(xm, xp, ym, yp, zm, zp));
+              float px = coord_f32(x, n, a), py = coord_f32(y, n, a), pz = coord_f32(z, n, a);
+              float c2 = c * c;
+              s0.add(c2);
+              sh.add(c * (-kfac * lap + vv * c));
+              sr.add((px * px + py * py + pz * pz) * c2);
+              sv.add(vv * c2);
+            });
+  block_sum4_store(s0.value(), sh.value(), sr.value(), sv.value(), partials);
+}
+
+static Tiling sums_tiling(int n) { return tiling_for(n, 1216); }
+int sums_blocks(int n) {
+  Tiling t = sums_tiling(n);
+  return (int)(t.grid.x * t.grid.y * t.grid.z);
+}
+
+template <>
+int launch_sums<double>(const double* psi, const void* v, const Params& p, double* partials, const int32_t* active,
+                        cudaStream_t st) {
+  Tiling t = sums_tiling(p.n);
+  k_sums_f64<<<t.grid, dim3(TX, TY), 0, st>>>(psi, (const double*)v, p.n, t.zc, p.a,
+                                               1.0 / (2.0 * p.mass * p.a * p.a), partials, active);
+  return (int)(t.grid.x * t.grid.y * t.grid.z);
+}
+template <typename T>
+int launch_sums(const T* psi, const void* v, const Params& p, double* partials, const int32_t* active,
+                cudaStream_t st) {
+  Tiling t = sums_tiling(p.n);
+  k_sums_f32<T><<<t.grid, dim3(TX, TY), 0, st>>>(psi, (const float*)v, p.n, t.zc, (float)p.a,
+                                                  (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active);
+  return (int)(t.grid.x * t.grid.y * t.grid.z);
+}
+template int launch_sums<float>(const float*, const void*, const Params&, double*, const int32_t*, cudaStream_t);
+template int launch_sums<__nv_bfloat16>(const __nv_bfloat16*, const void*, const Params&, double*, const int32_t*,
+                                        cudaStream_t);
+
+// ------------------------------------------------------------------ check
+// One block: deterministic reduction of the partials, then the check of
+// Secs. III-V on thread 0.
+__global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __restrict__ parts, int np, int check_id,
+                                                  int64_t t, double a3, double v_inf, double tol, int tol_rel,
+                                                  int record) {
+  if (record && s->active == 0) return;
+  __shared__ double sm[4][256];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < np; i += 256)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += parts[(size_t)i * 4 + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double s0 = sm[0][0], sh = sm[1][0], sr = sm[2][0], sv = sm[3][0];
+  if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(sh) || !isfinite(sr) || !isfinite(sv)) {
+    s->status = STATUS_NONFINITE;
+    s->active = 0;
+    s->scale_seq = -1;
+    return;
+  }
+  s->scale = 1.0 / sqrt(s0 * a3);
+  s->scale_seq = check_id;
+  if (!record) return;
+  double e = sh / s0, eb = e - v_inf;
+  s->s0 = s0;
+  s->sh = sh;
+  s->sr = sr;
+  s->sv = sv;
+  s->energy = e;
+  s->ebind = eb;
+  s->r2 = sr / s0;
+  s->vexp = sv / s0;
+  s->step = t;
+  s->checks += 1;
+  double d = -1.0;
+  if (s->has_prev) {
+    d = fabs(eb - s->e_prev);
+    double thr = tol * (tol_rel ? fabs(eb) : 1.0);
+    if (tol > 0.0 && d <= thr) {
+      s->converged = 1;
+      s->active = 0;
+    }
+  }
+  s->delta_e = d;
+  s->e_prev = eb;
+  s->has_prev = 1;
+}
+
+void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
+                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st) {
+  k_finalize<<<1, 256, 0, st>>>(s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol, tol_rel, record);
+}
+
+__global__ void k_state_reset(LatState* s, int mode) {
+  if (mode == 1) {
+    *s = LatState{};
+    s->scale_seq = -1;
+    s->delta_e = -1.0;
+    return;
+  }
+  s->has_prev = 0;
+  s->active = 1;
+  s->converged = 0;
+  s->status = STATUS_OK;
+  s->checks = 0;
+  s->scale_seq = -1;
+  s->step = 0;
+  s->delta_e = -1.0;
+}
+void launch_state_reset(LatState* s, int mode, cudaStream_t st) { k_state_reset<<<1, 1, 0, st>>>(s, mode); }
+
+// ------------------------------------------------------------------ renormalise + symmetry
+// out(site) = sign * scale * in(source): for each masked axis the upper half
+// (index above its mirror n-1-index) takes the mirrored lower-half value
+// (sign -1 for A_i), the central plane of odd n is zeroed by A_i, the rest is
+// scaled in place of itself (Sec. IV; renormalisation of Sec. III).
+template <typename T>
+__device__ __forceinline__ void parity_source(int& x, int& y, int& z, int n, int mask, double& sign, bool& zero) {
+  int* cs[3] = {&x, &y, &z};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int mode = (mask >> (2 * ax)) & 3;
+    if (mode == 0) continue;
+    int m = *cs[ax], mm = n - 1 - m;
+    if (m > mm) {
+      *cs[ax] = mm;
+      if (mode == 2) sign = -sign;
+    } else if (m == mm && mode == 2) {
+      zero = true;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale_parity(const T* __restrict__ in, T* __restrict__ out, int n, int mask,
+                               const LatState* __restrict__ s, int check_id, int out_idx, LatState* sw) {
+  double scale = 1.0;
+  if (s) {
+    if (s->scale_seq != check_id) return;
+    scale = s->scale;
+  }
+  if (sw && blockIdx.x == 0 && threadIdx.x == 0) sw->cur = out_idx;
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
+    double sign = 1.0;
+    bool zero = false;
+    if (mask) parity_source<T>(x, y, z, n, mask, sign, zero);
+    double val = zero ? 0.0 : sign * ((double)Store<T>::to(in[site_index(x, y, z, n)]) * scale);
+    if constexpr (sizeof(T) == 8)
+      out[i] = val;
+    else
+      out[i] = Store<T>::from((float)val);
+  }
+}
+
+static int grid_for(size_t total, int threads) {
+  size_t b = (total + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+void launch_scale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
+                         LatState* s_w, cudaStream_t st) {
+  size_t total = (size_t)n * n * n;
+  k_scale_parity<T><<<grid_for(total, 256), 256, 0, st>>>(in, out, n, mask, s, check_id, out_idx, s_w);
+}
+template void launch_scale_parity<double>(const double*, double*, int, int, const LatState*, int, int, LatState*,
+                                          cudaStream_t);
+template void launch_scale_parity<float>(const float*, float*, int, int, const LatState*, int, int, LatState*,
+                                         cudaStream_t);
+template void launch_scale_parity<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, int, int, const LatState*,
+                                                 int, int, LatState*, cudaStream_t);
+
+// ------------------------------------------------------------------ random start
+template <typename T>
+__global__ void k_init_random(T* __restrict__ out, int n, uint64_t seed, uint64_t lat, int dist) {
+  const size_t total = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    double val;
+    if (dist == 1) {
+      uint64_t d = (lat << 42) + 2ull * i;
+      double u1 = unit_interval(sm64(seed, d)), u2 = unit_interval(sm64(seed, d + 1));
+      val = sqrt(-2.0 * log(1.0 - u1)) * cos(2.0 * 3.14159265358979323846 * u2);  // Box-Muller
+    } else {
+      val = 2.0 * unit_interval(sm64(seed, (lat << 42) + i)) - 1.0;
+    }
+    if constexpr (sizeof(T) == 8)
+      out[i] = val;
+    else
+      out[i] = Store<T>::from((float)val);
+  }
+}
+template <typename T>
+void launch_init_random(T* out, int n, uint64_t seed, uint64_t lat, int dist, cudaStream_t st) {
+  size_t total = (size_t)n * n * n;
+  k_init_random<T><<<grid_for(total, 256), 256, 0, st>>>(out, n, seed, lat, dist);
+}
+template void launch_init_random<double>(double*, int, uint64_t, uint64_t, int, cudaStream_t);
+template void launch_init_random<float>(float*, int, uint64_t, uint64_t, int, cudaStream_t);
+template void launch_init_random<__nv_bfloat16>(__nv_bfloat16*, int, uint64_t, uint64_t, int, cudaStream_t);
+
+// ------------------------------------------------------------------ multi-resolution transfer
+// Fine site x (0-based) of a 2 nc lattice lies at coarse index position
+// x/2 - 1/4 (0-based, cell-centred boxes of equal length): between coarse
+// sites x/2 - 1 (weight 1/4) and x/2 (3/4) for even x, (x-1)/2 (3/4) and
+// (x+1)/2 (1/4) for odd x; coarse sites outside the box hold 0.
+__device__ __forceinline__ void interp_axis(int x, int& lo, double& wlo, double& whi) {
+  if (x & 1) {
+    lo = (x - 1) >> 1;
+    wlo = 0.75;
+    whi = 0.25;
+  } else {
+    lo = (x >> 1) - 1;
+    wlo = 0.25;
+    whi = 0.75;
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ out) {
+  const int nf = 2 * nc;
+  const size_t total = (size_t)nf * nf * nf;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % nf), y = (int)((i / nf) % nf), z = (int)(i / ((size_t)nf * nf));
+    int lx, ly, lz;
+    double wx[2], wy[2], wz[2];
+    interp_axis(x, lx, wx[0], wx[1]);
+    interp_axis(y, ly, wy[0], wy[1]);
+    interp_axis(z, lz, wz[0], wz[1]);
+    double acc = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          int cx = lx + dx, cy = ly + dy, cz = lz + dz;
+          double val = 0.0;
+          if ((unsigned)cx < (unsigned)nc && (unsigned)cy < (unsigned)nc && (unsigned)cz < (unsigned)nc)
+            val = (double)Store<Ti>::to(in[site_index(cx, cy, cz, nc)]);
+          acc += (wx[dx] * wy[dy] * wz[dz]) * val;
+        }
+    if constexpr (sizeof(To) == 8)
+      out[i] = acc;
+    else
+      out[i] = Store<To>::from((float)acc);
+  }
+}
+template <typename Ti, typename To>
+void launch_upsample(const Ti* in, int nc, To* out, cudaStream_t st) {
+  size_t total = (size_t)8 * nc * nc * nc;
+  k_upsample<Ti, To><<<grid_for(total, 256), 256, 0, st>>>(in, nc, out);
+}
+#define INST_UP(Ti, To) template void launch_upsample<Ti, To>(const Ti*, int, To*, cudaStream_t);
+INST_UP(double, double)
+INST_UP(double, float)
+INST_UP(double, __nv_bfloat16)
+INST_UP(float, double)
+INST_UP(float, float)
+INST_UP(float, __nv_bfloat16)
+INST_UP(__nv_bfloat16, double)
+INST_UP(__nv_bfloat16, float)
+INST_UP(__nv_bfloat16, __nv_bfloat16)
+
+// ------------------------------------------------------------------ conversions
+template <typename Ti, typename To>
+__global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    double val = (double)Store<Ti>::to(in[i]);
+    if constexpr (sizeof(To) == 8)
+      out[i] = val;
+    else
+      out[i] = Store<To>::from((float)val);
+  }
+}
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t st) {
+  k_convert<Ti, To><<<grid_for(count, 256), 256, 0, st>>>(in, out, count);
+}
+#define INST_CV(Ti, To) template void launch_convert<Ti, To>(const Ti*, To*, size_t, cudaStream_t);
+INST_CV(double, double)
+INST_CV(double, float)
+INST_CV(double, __nv_bfloat16)
+INST_CV(float, double)
+INST_CV(float, float)
+INST_CV(float, __nv_bfloat16)
+INST_CV(__nv_bfloat16, double)
+INST_CV(__nv_bfloat16, float)
+
+// ------------------------------------------------------------------ potential
+template <typename Ti>
+__global__ void k_set_potential(const Ti* __restrict__ in, size_t count, size_t offset, float* vf, double* vd,
+                                double* coefA, double* coefCB, double half_dtau, double c, int32_t* flags) {
+  int bad = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    double v = (double)in[i];
+    size_t o = offset + i;
+    if (!isfinite(v)) bad |= 1;
+    double onep = 1.0 + half_dtau * v;
+    if (!(onep > 0.0)) bad |= 2;
+    if (vd) {
+      vd[o] = v;
+      coefA[o] = (1.0 - half_dtau * v) / onep;
+      coefCB[o] = c / onep;
+    } else {
+      float vv = (float)v;
+      vf[o] = vv;
+      if (!(1.0f + (float)half_dtau * vv > 0.0f)) bad |= 2;
+    }
+  }
+  if (bad) atomicOr(flags, bad);
+}
+template <typename Ti>
+void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, double* vd, double* coefA,
+                          double* coefCB, const Params& p, int32_t* flags, cudaStream_t st) {
+  k_set_potential<Ti><<<grid_for(count, 256), 256, 0, st>>>(in, count, offset, vf, vd, coefA, coefCB, 0.5 * p.dtau,
+                                                           p.c, flags);
+}
+template void launch_set_potential<double>(const double*, size_t, size_t, float*, double*, double*, double*,
+                                           const Params&, int32_t*, cudaStream_t);
+template void launch_set_potential<float>(const float*, size_t, size_t, float*, double*, double*, double*,
+                                          const Params&, int32_t*, cudaStream_t);
+
+}  // namespace fdtd

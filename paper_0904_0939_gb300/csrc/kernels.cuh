@@ -1,0 +1,110 @@
+// Internal launch interface between the C ABI (fdtd_api.cu) and the kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdtd.h"
+
+namespace fdtd {
+
+// Per-lattice state kept in device memory: the check record of the last
+// evolve, the pending renormalisation factor and the run flags.
+struct LatState {
+  double e_prev;    // binding energy of the previous check
+  double s0, sh, sr, sv;
+  double energy, ebind, r2, vexp, delta_e;
+  double scale;     // 1 / sqrt(S0 a^3) of the last check
+  int64_t step;     // t of the last check
+  int32_t has_prev, active, converged, status;
+  int32_t checks, scale_seq, cur, pad;
+};
+
+enum : int32_t { STATUS_OK = 0, STATUS_NONFINITE = 1 };
+
+// Physical parameters a kernel needs, precomputed on the host.
+struct Params {
+  int n;
+  double a, dtau, mass;
+  double c;            // dtau / (2 m a^2)
+  float half_dtau_f;   // dtau / 2 (FP32)
+  float one_m6c_f;     // 1 - 6c (FP32)
+  float c_f;           // c (FP32)
+};
+
+// Tiling of the z-marching kernels: 32 x 8 threads per block, one site per
+// thread in x-y, each block walks `zc` planes.
+struct Tiling {
+  dim3 grid;
+  int zc;
+};
+Tiling tiling_for(int n, int min_blocks);
+
+// ---- launchers (all asynchronous on `st`) -----------------------------------
+// One update step psi_out = M psi_in (Eq. updateeq).
+void launch_step_f64(const double* in, double* out, const double* coefA, const double* coefCB, const Params& p,
+                     const int32_t* active, cudaStream_t st);
+template <typename T>
+void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st);
+
+// Temporal blocking: `depth` update steps in one pass (FP32 arithmetic).
+template <typename T>
+void launch_step_blocked(const T* in, T* out, const float* v, const Params& p, int depth, const int32_t* active,
+                         cudaStream_t st);
+int blocked_max_depth();
+// Temporal depth chosen for an n^3 lattice of the given precision.
+int auto_depth(int n, int precision);
+
+// ---- batched persistent driver (k_batched.cu) ---------------------------------
+// Device tables of the batched driver for `count` lattices (0 if count == 1).
+size_t batched_workspace_bytes(const fdtd_lattice_desc* d, int count);
+
+// Lattice sums S0, SH, Sr, SV into per-block partials; returns block count.
+template <typename T>
+int launch_sums(const T* psi, const void* v, const Params& p, double* partials, const int32_t* active,
+                cudaStream_t st);
+int sums_blocks(int n);
+
+// Reduce partials, compute E, E_b, <r^2>, the renormalisation factor and
+// the convergence decision.  record = 0: only the scale (for upsample).
+void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
+                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st);
+
+// out = P(scale * in): renormalisation and symmetry re-imposition.  With
+// s == nullptr the factor is 1 and the call is unconditional.
+template <typename T>
+void launch_scale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
+                         LatState* s_w, cudaStream_t st);
+
+template <typename T>
+void launch_init_random(T* out, int n, uint64_t seed, uint64_t lat, int dist, cudaStream_t st);
+
+template <typename Ti, typename To>
+void launch_upsample(const Ti* in, int nc, To* out, cudaStream_t st);
+
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t st);
+
+// V (FP64 or FP32 input) -> lattice storage; flags[0] |= 1 nonfinite,
+// flags[0] |= 2 unstable (1 + dtau V / 2 <= 0).  For FP64 lattices also
+// A = (1-h)/(1+h) and cB = c / (1+h).
+template <typename Ti>
+void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, double* vd, double* coefA,
+                          double* coefCB, const Params& p, int32_t* flags, cudaStream_t st);
+
+void launch_state_reset(LatState* s, int mode, cudaStream_t st);
+
+// ---- adjoint (k_adjoint.cu) ---------------------------------------------------
+template <typename T>
+void launch_adjoint_step(const T* lam_in, T* lam_out, const T* psi_prev, const void* v, const double* coefA,
+                         const double* coefCB, double* gv, const Params& p, cudaStream_t st);
+template <typename T>
+void launch_adjoint_seed(const T* psi, const void* v, const LatState* s, double w_e, double w_r, T* lam, double* gv,
+                         const Params& p, cudaStream_t st);
+template <typename T>
+void launch_parity_adjoint_scale(T* lam, int n, int mask, const double* scale, cudaStream_t st);
+void launch_store_scale(const LatState* s, double* dst, cudaStream_t st);
+template <typename T>
+void launch_scale_parity_from(const T* in, T* out, int n, int mask, const double* scale, cudaStream_t st);
+
+}  // namespace fdtd

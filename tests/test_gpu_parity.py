@@ -1,0 +1,288 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated per test):
+  * FP64 path: max |psi_gpu - psi_ref| / max |psi_ref| <= 1e-12 after 100
+    steps with checks; energies and radii to 1e-12 relative.
+  * FP32 path: the update rounds psi to 24 bits every step (relative error
+    <= 6e-8 per step, growing at most linearly over the 100 steps of a
+    check interval) -> 2e-5 on psi after 100 steps; converged energies to
+    1e-6 relative (the energy is second order in the error of psi).
+  * integer work (random start, symmetry copies) is bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fd():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0904_0939_gb300 as fd
+
+    return fd
+
+
+def rel_max(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def solver(fd, n, L, prec, **opt):
+    kw = dict(check_every=100, tol=0.0)
+    kw.update(opt)
+    return fd.Solver(fd.Lattice(n, L, prec), fd.default_options(**kw))
+
+
+# ------------------------------------------------------------------ random start
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 33])
+@pytest.mark.parametrize("dist", [0, 1])
+def test_random_start_matches_oracle(fd, orc, n, dist):
+    s = solver(fd, n, 4.0, fd.F64)
+    s.init_symmetric(77, 0, lat=0, dist=dist)
+    ref = orc.init_random(n, 77, 0, dist)
+    got = s.get_psi()
+    if dist == 0:
+        np.testing.assert_array_equal(got, ref)  # integer hash + exact scaling
+    else:
+        np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-14)  # libm vs CUDA log/cos
+
+
+@pytest.mark.parametrize("n", [4, 7, 8])
+@pytest.mark.parametrize("mask", [wl.ODD_X, wl.SYMMETRIC_ALL, wl.ODD_Z | 0b0100, wl.ODD_X | wl.ODD_Y | wl.ODD_Z])
+def test_symmetric_start_bit_exact(fd, orc, n, mask):
+    s = solver(fd, n, 4.0, fd.F64)
+    s.init_symmetric(5, mask)
+    np.testing.assert_array_equal(s.get_psi(), orc.init_symmetric(n, 5, mask))
+
+
+def test_lattice_index_selects_the_stream(fd, orc):
+    lats = [fd.Lattice(6, 4.0, fd.F64), fd.Lattice(6, 4.0, fd.F64)]
+    s = fd.Solver(lats, fd.default_options(tol=0.0))
+    s.init_symmetric(9, 0, lat=1)
+    np.testing.assert_array_equal(s.get_psi(lat=1), orc.init_random(6, 9, 1, 0))
+
+
+# ------------------------------------------------------------------ evolution, FP64
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8, 33, 48])
+def test_fp64_100_steps_match_oracle(fd, orc, n):
+    L = 0.75 * n if n > 3 else 3.0
+    a = L / n
+    rng = np.random.default_rng(n)
+    v = wl.harmonic(n, L) + rng.uniform(-0.3, 0.3, (n, n, n))
+    s = solver(fd, n, L, fd.F64, check_every=30)
+    s.set_potential(v)
+    s.init_symmetric(11, 0)
+    steps, _ = s.evolve(100)
+    ref, rec, _ = orc.evolve(orc.init_random(n, 11), v, a, a * a / 4, 100, 30)
+    assert steps == 100
+    assert rel_max(s.get_psi(), ref) <= 1e-12
+    o = s.last_check()
+    assert o["energy"] == pytest.approx(rec["E"], rel=1e-12, abs=1e-13)
+    assert o["r2"] == pytest.approx(rec["r2"], rel=1e-12)
+    assert o["norm"] == pytest.approx(rec["S0"] * a**3, rel=1e-12)
+
+
+@pytest.mark.parametrize("mask", [wl.ODD_X, wl.ODD_Z | wl.ODD_Y, wl.SYMMETRIC_ALL])
+@pytest.mark.parametrize("n", [9, 16])
+def test_fp64_sector_evolution_matches_oracle(fd, orc, n, mask):
+    L = 6.0
+    a = L / n
+    v = wl.harmonic(n, L)
+    s = solver(fd, n, L, fd.F64, check_every=25)
+    s.set_potential(v)
+    s.init_symmetric(3, mask)
+    s.evolve(100)
+    ref, rec, _ = orc.evolve(orc.init_symmetric(n, 3, mask), v, a, a * a / 4, 100, 25, 0.0, False, mask)
+    assert rel_max(s.get_psi(), ref) <= 1e-12
+    assert s.last_check()["energy"] == pytest.approx(rec["E"], rel=1e-12)
+
+
+def test_fp64_convergence_small_ho(fd, orc):
+    """The 32^3, L = 10 oscillator run to |dE| < 1e-10 between checks."""
+    lat = wl.config_small_ho()
+    v = lat.potential()
+    s = solver(fd, lat.n, lat.length, fd.F64, tol=1e-10, tol_relative=0)
+    s.set_potential(v)
+    s.init_symmetric(wl.BASE_SEED, 0)
+    steps, conv = s.evolve(100000)
+    _, rec, _ = orc.evolve(orc.init_random(lat.n, wl.BASE_SEED), v, lat.a, lat.dtau, 100000, 100, 1e-10)
+    assert conv and steps == rec["steps"]
+    o = s.last_check()
+    assert o["energy"] == pytest.approx(rec["E"], rel=1e-12)
+    assert o["r2"] == pytest.approx(rec["r2"], rel=1e-11)
+
+
+# ------------------------------------------------------------------ evolution, FP32
+
+@pytest.mark.parametrize("n", [3, 8, 33, 48])
+def test_fp32_100_steps_close_to_oracle(fd, orc, n):
+    L = 0.6 * n if n > 3 else 3.0
+    a = L / n
+    v = wl.harmonic(n, L)
+    s = solver(fd, n, L, fd.F32, check_every=50)
+    s.set_potential(v)
+    s.init_symmetric(8, 0)
+    s.evolve(100)
+    ref, rec, _ = orc.evolve(orc.init_random(n, 8), v, a, a * a / 4, 100, 50)
+    assert rel_max(s.get_psi(), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("mask", [0, wl.ODD_X])
+def test_fp32_converged_energy_within_1e6(fd, orc, mask):
+    lat = wl.config_small_ho()
+    v = lat.potential()
+    _, rec, _ = orc.evolve(orc.init_symmetric(lat.n, 2, mask), v, lat.a, lat.dtau, 200000, 100, 1e-13, False, mask)
+    s = solver(fd, lat.n, lat.length, fd.F32, tol=1e-9, tol_relative=1)
+    s.set_potential(v)
+    s.init_symmetric(2, mask)
+    steps, conv = s.evolve(200000)
+    o = s.last_check()
+    assert conv
+    assert o["energy"] == pytest.approx(rec["E"], rel=1e-6)
+    assert o["r2"] == pytest.approx(rec["r2"], rel=1e-5)
+
+
+def test_bf16_storage_runs_and_stays_close(fd, orc):
+    n, L = 32, 10.0
+    v = wl.harmonic(n, L)
+    _, rec, _ = orc.evolve(orc.init_random(n, 2), v, L / n, (L / n) ** 2 / 4, 100000, 100, 1e-12)
+    s = solver(fd, n, L, fd.BF16, tol=1e-4, tol_relative=1)
+    s.set_potential(v)
+    s.init_symmetric(2, 0)
+    s.evolve(20000)
+    assert s.last_check()["energy"] == pytest.approx(rec["E"], rel=2e-3)
+
+
+# ------------------------------------------------------------------ sums and transfer
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-6)])
+def test_observables_of_a_given_field(fd, orc, prec, tol):
+    n, L = 20, 7.0
+    rng = np.random.default_rng(1)
+    v = wl.anisotropic(n, L)
+    psi = np.exp(-wl.radius2(n, L)) * (1 + 0.1 * rng.standard_normal((n, n, n)))
+    if prec == 1:
+        psi = psi.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    s = solver(fd, n, L, prec)
+    s.set_potential(v)
+    s.set_psi(psi)
+    o = s.observables()
+    ref = orc.observables(psi, v, L / n)
+    assert o["energy"] == pytest.approx(ref["E"], rel=tol)
+    assert o["r2"] == pytest.approx(ref["r2"], rel=tol)
+    assert o["v_expect"] == pytest.approx(ref["V"], rel=tol)
+    assert o["norm"] == pytest.approx(ref["S0"] * (L / n) ** 3, rel=tol)
+
+
+@pytest.mark.parametrize("nc,mask", [(5, 0), (8, wl.ODD_Y), (12, wl.SYMMETRIC_ALL)])
+def test_upsample_matches_oracle(fd, orc, nc, mask):
+    L = 5.0
+    coarse = solver(fd, nc, L, fd.F64)
+    coarse.set_potential(wl.harmonic(nc, L))
+    coarse.init_symmetric(4, mask)
+    fine = solver(fd, 2 * nc, L, fd.F64)
+    fine.set_potential(wl.harmonic(2 * nc, L))
+    fine.upsample_from(coarse)
+    up = orc.upsample(orc.init_symmetric(nc, 4, mask))
+    af = L / (2 * nc)
+    up = up / math.sqrt(np.sum(up**2) * af**3)
+    up = orc.impose_parity(up, mask)
+    assert rel_max(fine.get_psi(), up) <= 1e-14
+
+
+def test_upsample_shape_mismatch(fd):
+    a = solver(fd, 8, 4.0, fd.F64)
+    b = solver(fd, 12, 4.0, fd.F64)
+    b.set_potential(np.zeros((12, 12, 12)))
+    a.init_symmetric(1)
+    with pytest.raises(fd.FdtdError) as e:
+        b.upsample_from(a)
+    assert e.value.code == fd.ERR_SHAPE
+
+
+def test_multires_reaches_same_energy_in_fewer_fine_steps(fd, orc):
+    L = 8.0
+    opts = fd.default_options(tol=1e-9, tol_relative=1)
+    levels = [fd.Lattice(16, L, fd.F64), fd.Lattice(32, L, fd.F64)]
+    pots = [wl.harmonic(16, L), wl.harmonic(32, L)]
+    out = fd.multires(levels, pots, options=opts)
+    _, rec, _ = orc.evolve(orc.init_random(32, 904939), pots[1], L / 32, (L / 32) ** 2 / 4, 100000, 100, 1e-12)
+    assert out[-1][1]["energy"] == pytest.approx(rec["E"], rel=1e-7)
+    direct, o = fd.solve(pots[1], 32, L, fd.F64, options=opts)
+    assert out[-1][1]["steps"] < o["steps"]
+
+
+# ------------------------------------------------------------------ errors
+
+def test_input_guards(fd):
+    s = solver(fd, 8, 4.0, fd.F32)
+    v = np.zeros((8, 8, 8))
+    v[1, 2, 3] = np.nan
+    with pytest.raises(fd.FdtdError) as e:
+        s.set_potential(v)
+    assert e.value.code == fd.ERR_NONFINITE
+    a = 4.0 / 8
+    v = np.full((8, 8, 8), -2.5 / (a * a / 4))  # 1 + dtau V / 2 < 0
+    with pytest.raises(fd.FdtdError) as e:
+        s.set_potential(v)
+    assert e.value.code == fd.ERR_UNSTABLE_DT
+    with pytest.raises(fd.FdtdError) as e:
+        s.evolve(10)
+    assert e.value.code == fd.ERR_STATE
+    with pytest.raises(fd.FdtdError) as e:
+        s.init_symmetric(1, 0b11)
+    assert e.value.code == fd.ERR_INVALID_ARG
+
+
+def test_zero_field_reports_nonfinite(fd):
+    s = solver(fd, 8, 4.0, fd.F64)
+    s.set_potential(np.zeros((8, 8, 8)))
+    s.set_psi(np.zeros((8, 8, 8)))
+    with pytest.raises(fd.FdtdError) as e:
+        s.evolve(10)
+    assert e.value.code == fd.ERR_NONFINITE
+
+
+# ------------------------------------------------------------------ full size, sampled
+
+def _cone(orc, psi, v, a, dtau, steps, site):
+    r = steps + 1
+    z, y, x = site
+    sub = psi[z - r:z + r + 1, y - r:y + r + 1, x - r:x + r + 1]
+    vs = v[z - r:z + r + 1, y - r:y + r + 1, x - r:x + r + 1]
+    out = orc.steps(sub, vs, a, dtau, steps)
+    return out[r, r, r]
+
+
+def test_full_size_256_sampled_sites(fd, orc):
+    """Coulomb workload at 256^3, L = 40 (FP32, the benchmark launch shapes):
+    sampled interior sites after 6 steps against the oracle applied to each
+    site's cone of dependence."""
+    n, L, steps = 256, 40.0, 6
+    a = L / n
+    v = wl.coulomb_soft(n, L)
+    s = solver(fd, n, L, fd.F32, check_every=1000)
+    s.set_potential(v)
+    s.init_symmetric(21, 0)
+    psi0 = s.get_psi()
+    s0 = float(np.sum(psi0**2))
+    s.evolve(steps)
+    sT = s.last_check()["norm"] / a**3
+    got = s.get_psi()
+    scale = 1.0 / math.sqrt(s0 * a**3) / math.sqrt(sT * a**3)
+    v32 = v.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(0)
+    sites = [(int(rng.integers(8, n - 8)), int(rng.integers(8, n - 8)), int(rng.integers(8, n - 8)))
+             for _ in range(24)] + [(128, 128, 128), (8, 8, 8), (247, 247, 247), (127, 128, 129)]
+    for site in sites:
+        want = scale * _cone(orc, psi0, v32, a, a * a / 4, steps, site)
+        assert got[site] == pytest.approx(want, rel=2e-5, abs=2e-5 * np.abs(got).max())
