@@ -175,6 +175,40 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def stencil_case(args):
+    """Fixed number of update steps on one lattice (512^3, L = 16 by default,
+    the size of the anisotropic-oscillator workload; the kernel's time does
+    not depend on V's values, so the oscillator r^2/2 stands in for it):
+    per-launch stencil time with CUDA events and the HBM fraction.  Small
+    enough to run under ncu."""
+    import numpy as np
+    import torch
+
+    import paper_0904_0939_gb300 as fd
+    import workloads as wl
+
+    n = args.n
+    prec = {"f32": fd.F32, "bf16": fd.BF16, "f64": fd.F64}[args.precision]
+    opts = fd.default_options(check_every=1 << 30, tol=0.0, temporal_depth=args.depth)
+    s = fd.Solver(fd.Lattice(n, 16.0, prec), opts)
+    v = torch.from_numpy(wl.harmonic(n, 16.0).astype(np.float32)).cuda()
+    s.set_potential(v)
+    s.init_symmetric(SEED, 0)
+    s.evolve(args.iters)  # warm-up
+    s.reset_stats()
+    s.set_profiling(True)
+    s.evolve(args.iters)
+    st = s.stats()
+    ms = st["stencil_ms"] / max(1, st["stencil_launches"])
+    upd = st["stencil_site_updates"] / (st["stencil_ms"] * 1e-3) / 1e9
+    gbs = st["stencil_bytes"] / (st["stencil_ms"] * 1e-3) / 1e9
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    print(json.dumps({"case": "stencil", "n": n, "precision": args.precision, "depth": args.depth,
+                      "launches": st["stencil_launches"], "ms_per_launch": ms, "gsite_per_s": upd,
+                      "achieved_gbs": gbs, "hbm_frac": gbs / peak, "effective_frac_12B": upd * 12 / peak}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,9 +216,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="solve", choices=["solve", "stencil"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--iters", type=int, default=40)
+    ap.add_argument("--depth", type=int, default=0)
+    ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.case == "stencil":
+        return stencil_case(args)
 
     import torch
     import torch.distributed as dist
