@@ -210,6 +210,26 @@ FDTD_API int fdtd_reset_stats(fdtd_handle h);
 /* on = 1: bracket every stencil launch with CUDA events on the handle's stream. */
 FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
 
+/* Allocation-free observables of a caller-held field (no counterpart in
+ * the paper; it serves callers that cannot allocate device memory, e.g.
+ * code running inside a fixed memory pool or handed only raw device
+ * pointers and a stream).  psi and v are DEVICE pointers to n^3 values
+ * (dense, x fastest), both FDTD_F64 or both FDTD_F32; out is a DEVICE
+ * pointer to 8 doubles that receive E, <r^2>, <V>, sum psi^2 a^3, and the
+ * raw sums S0, SH, Sr, SV, with the same arithmetic as fdtd_observables
+ * for that precision.  The work is enqueued on `stream` (cudaStream_t or
+ * NULL) and the call returns without synchronising.
+ * Nothing is allocated: the block partials live in a static 128 KiB device
+ * array that every GPU loading the library keeps until exit, so n is
+ * limited to 1 <= n <= 1024 (FDTD_ERR_SHAPE beyond).  The first call on a
+ * device looks the array's address up (make it before any stream capture
+ * on that device).  All calls share the array: calls whose kernels overlap
+ * on the GPU race and may return wrong sums.  A zero or non-finite field
+ * yields NaN/Inf in out (there is no status for it).  Errors are reported
+ * through fdtd_last_error(NULL). */
+FDTD_API int fdtd_observables_noalloc(const void* psi, const void* v, int dtype, int n, double length, double mass,
+                                      double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

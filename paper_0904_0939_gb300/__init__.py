@@ -75,7 +75,7 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
-            "fdtd_reset_stats", "fdtd_set_profiling"]
+            "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc"]
 
 
 def _load():
@@ -107,6 +107,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.fdtd_observables_noalloc.argtypes = [vp, vp, i32, i32, d, d, vp, vp]
+    lib.fdtd_observables_noalloc.restype = ctypes.c_int
     lib.fdtd_last_error.argtypes = [vp]
     lib.fdtd_last_error.restype = ctypes.c_char_p
     return lib
@@ -313,6 +315,29 @@ def multires(levels, potentials, mask: int = 0, seed: int = 904939, options: Opt
         s.evolve(max_steps)
         out.append((s, s.last_check()))
         prev = s
+    return out
+
+
+def observables_noalloc(psi, v, length: float, mass: float = 1.0, out=None, stream=None):
+    """Lattice sums of a caller-held CUDA field without any allocation in the
+    library (fdtd_observables_noalloc).  psi and v are contiguous CUDA
+    tensors of n^3 values, both float64 or both float32; out is a CUDA
+    float64 tensor of 8 values (allocated here if not given).  Returns out:
+    [E, <r^2>, <V>, sum psi^2 a^3, S0, SH, Sr, SV]."""
+    import torch
+
+    n = round(psi.numel() ** (1.0 / 3.0))
+    if psi.numel() != n**3 or v.numel() != n**3 or psi.dtype != v.dtype or not psi.is_cuda:
+        raise FdtdError(ERR_INVALID_ARG, "psi and v must be CUDA tensors of n^3 values with one dtype")
+    code = F64 if psi.dtype == torch.float64 else F32
+    if out is None:
+        out = torch.empty(8, dtype=torch.float64, device=psi.device)
+    st = stream if stream is not None else torch.cuda.current_stream(psi.device)
+    with torch.cuda.device(psi.device):
+        _check(lib.fdtd_observables_noalloc(ctypes.c_void_p(psi.contiguous().data_ptr()),
+                                            ctypes.c_void_p(v.contiguous().data_ptr()), code, n, float(length),
+                                            float(mass), ctypes.c_void_p(out.data_ptr()),
+                                            ctypes.c_void_p(st.cuda_stream)))
     return out
 
 

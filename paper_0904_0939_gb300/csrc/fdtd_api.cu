@@ -168,6 +168,11 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
 
 }  // namespace
 
+namespace fdtd {
+// Message for fdtd_last_error(NULL) from entry points that take no handle.
+void set_detached_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace fdtd
+
 struct fdtd_context {
   std::vector<Lat> lats;
   fdtd_options o{};
