@@ -94,7 +94,9 @@ typedef struct {
   int32_t backward_steps; /* largest T that fdtd_backward may be asked for; 0 = none */
   int32_t batched;        /* 1: all lattices of the handle advance in one persistent launch */
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
-  int32_t reserved[4];
+  int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
+                             (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
+  int32_t reserved[3];
 } fdtd_options;
 
 typedef struct {

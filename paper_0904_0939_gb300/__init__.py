@@ -53,7 +53,7 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int32), ("tol_relative", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("stencil_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Obs(ctypes.Structure):

@@ -60,6 +60,9 @@ struct Lat {
   // last evolve
   int64_t last_steps = 0;
   LatState host_state{};
+  // TMA descriptors of psi[0], psi[1], V for each temporal depth 1..3
+  bool tma_ok = false;
+  CUtensorMap maps[3][3];
 };
 
 struct Carve {
@@ -103,6 +106,10 @@ int check_options(const fdtd_options& o, std::string& err) {
   }
   if (o.temporal_depth < 0 || o.temporal_depth > blocked_max_depth()) {
     err = "temporal_depth out of range";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.stencil_kernel < 0 || o.stencil_kernel > 1) {
+    err = "stencil_kernel must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
   if (o.backward_steps < 0 || !std::isfinite(o.tol)) {
@@ -248,16 +255,22 @@ void with_type(int prec, F&& f) {
 // Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows).
 void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
   const int prec = L.d.precision;
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
   int depth = c->o.temporal_depth;
   if (depth == 0) depth = auto_depth(L.d.n, prec);
+  if (!tma) depth = 1;
   while (count > 0) {
-    int k = (int)std::min<int64_t>(count, prec == FDTD_F64 ? 1 : depth);
+    int k = (int)std::min<int64_t>(count, depth);
     prof_begin(c);
     if (prec == FDTD_F64) {
       launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
     } else if (prec == FDTD_F32) {
-      launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
-                             c->st);
+      if (tma)
+        launch_step_tma(L.maps[k - 1][L.cur], L.maps[k - 1][2], (float*)L.psi[1 - L.cur], L.p, k, 0, active,
+                        c->flags + 1, c->st);
+      else
+        launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
+                               c->st);
     } else {
       launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
                                      (const float*)L.v, L.p, active, c->st);
@@ -266,7 +279,7 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
     c->stats.launches += 1;
     c->stats.stencil_launches += 1;
     c->stats.stencil_site_updates += (int64_t)L.n3 * k;
-    // algorithmic bytes: psi read + psi write + V read once per launch
+    // algorithmic bytes: psi read + psi write + V (FP64: A and cB) read once per launch
     c->stats.stencil_bytes += (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0));
     L.cur ^= 1;
     count -= k;
@@ -303,14 +316,18 @@ void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
 }
 
 int read_state(fdtd_context* c, Lat& L) {
+  int32_t err = 0;
   cudaMemcpyAsync(&L.host_state, &L.state[0], sizeof(LatState), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("evolve: ") + cudaGetErrorString(e));
   prof_collect(c);
+  if (err) return fail(c, FDTD_ERR_TIMEOUT, "evolve: a bounded device-side wait expired in the stencil kernel");
   return FDTD_OK;
 }
 
 int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
+  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
   launch_state_reset(&L.state[0], 0, c->st);
   c->stats.launches += 1;
   const int64_t ce = c->o.check_every;
@@ -442,6 +459,7 @@ int fdtd_default_options(fdtd_options* o) {
   o->backward_steps = 0;
   o->batched = 0;
   o->reimpose_parity = 1;
+  o->stencil_kernel = 0;
   return FDTD_OK;
 }
 
@@ -504,10 +522,20 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
   Carve cv;
   cv.base = c->ws;
   layout(d, count, c->o, cv, &c->lats, &c->staging, &c->flags, &c->batch_ws, &c->batch_bytes);
+  cudaMemsetAsync(c->flags, 0, 256, c->st);
   for (auto& L : c->lats) {
     launch_state_reset(&L.state[0], 1, c->st);
     launch_state_reset(&L.state[1], 1, c->st);
     c->stats.launches += 2;
+    if (tma_supported(L.d.n, L.d.precision)) {
+      bool ok = true;
+      for (int k = 1; k <= blocked_max_depth() && ok; ++k) {
+        ok = encode_field_map(&L.maps[k - 1][0], (const float*)L.psi[0], L.d.n, k) == 0 &&
+             encode_field_map(&L.maps[k - 1][1], (const float*)L.psi[1], L.d.n, k) == 0 &&
+             encode_field_map(&L.maps[k - 1][2], (const float*)L.v, L.d.n, k) == 0;
+      }
+      L.tma_ok = ok;
+    }
   }
   if (cuda_check(c, "create")) {
     g_create_err = c->err;

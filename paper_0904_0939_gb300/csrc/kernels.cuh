@@ -1,5 +1,6 @@
 // Internal launch interface between the C ABI (fdtd_api.cu) and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,13 +48,17 @@ void launch_step_f64(const double* in, double* out, const double* coefA, const d
 template <typename T>
 void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st);
 
-// Temporal blocking: `depth` update steps in one pass (FP32 arithmetic).
-template <typename T>
-void launch_step_blocked(const T* in, T* out, const float* v, const Params& p, int depth, const int32_t* active,
-                         cudaStream_t st);
+// Temporal blocking with TMA plane streaming (k_tblock.cu): `depth` update
+// steps in one pass over HBM, FP32 lattices with n % 4 == 0.  Bit-identical
+// to `depth` calls of launch_step_f32.  *err |= 1 if a bounded wait expired.
+bool tma_supported(int n, int precision);
 int blocked_max_depth();
-// Temporal depth chosen for an n^3 lattice of the given precision.
 int auto_depth(int n, int precision);
+int tma_zchunk(int n, int depth);
+size_t tma_smem_bytes(int depth);
+int encode_field_map(CUtensorMap* map, const float* base, int n, int depth);
+void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
+                     int zc, const int32_t* active, int32_t* err, cudaStream_t st);
 
 // ---- batched persistent driver (k_batched.cu) ---------------------------------
 // Device tables of the batched driver for `count` lattices (0 if count == 1).

@@ -286,3 +286,26 @@ def test_full_size_256_sampled_sites(fd, orc):
     for site in sites:
         want = scale * _cone(orc, psi0, v32, a, a * a / 4, steps, site)
         assert got[site] == pytest.approx(want, rel=2e-5, abs=2e-5 * np.abs(got).max())
+
+
+# ------------------------------------------------------------------ temporal blocking
+
+@pytest.mark.parametrize("n", [64, 96, 132, 256])
+def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
+    """The TMA-streamed kernel at depth K reproduces K plain steps bit for
+    bit (ragged x/y tiles and z-chunks at n = 132; check cadence not a
+    multiple of K)."""
+    L = 0.3 * n
+    rng = np.random.default_rng(n)
+    v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
+    outs = {}
+    for name, kw in [("plain", dict(stencil_kernel=1)), ("k1", dict(temporal_depth=1)),
+                     ("k2", dict(temporal_depth=2)), ("k3", dict(temporal_depth=3))]:
+        s = solver(fd, n, L, fd.F32, check_every=50, **kw)
+        s.set_potential(v)
+        s.init_symmetric(31, wl.ODD_Z)
+        s.evolve(100)
+        outs[name] = s.get_psi(dtype=np.float32)
+        s.close()
+    for name in ("k1", "k2", "k3"):
+        np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
