@@ -41,6 +41,14 @@ template <> struct Store<__nv_bfloat16> {
 // the form the FP32 kernels evaluate (one reciprocal per site, the rest
 // FMAs).  The neighbour sum is always taken as ((xm + xp) + (ym + yp)) +
 // (zm + zp): commutative pairs keep an odd/even field exactly odd/even.
+// B uses the hardware reciprocal approximation (rcp.approx, max 1 ulp): every
+// FP32 kernel (single step, temporally blocked, adjoint) takes B from this
+// one function, so they agree bit for bit.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 struct CoefF {
   float b;      // 1 / (1 + h)
   float alpha;  // 1 - h - 6c
@@ -48,7 +56,7 @@ struct CoefF {
 __device__ __forceinline__ CoefF coef_f32(float v, float half_dtau, float one_minus_6c) {
   float h = half_dtau * v;
   CoefF k;
-  k.b = __frcp_rn(1.0f + h);
+  k.b = rcp_approx(1.0f + h);
   k.alpha = one_minus_6c - h;
   return k;
 }

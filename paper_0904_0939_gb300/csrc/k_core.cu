@@ -189,7 +189,11 @@ __global__ void __launch_bounds__(TX* TY) k_sums_f32(const T* __restrict__ psi, 
               if (!act) return;
               size_t i = site_index(x, y, z, n);
               float vv = __ldg(v + i);
-              float lap = __fmaf_rn(-6.0f, c, nbr_sum(xm, xp, ym, yp, zm, zp));
+              // sum of neighbour differences: each difference is exact when
+              // the neighbours are within a factor 2 of psi (Sterbenz), so the
+              // kinetic term loses far less to cancellation than S - 6 psi
+              float lap = ((__fsub_rn(xm, c) + __fsub_rn(xp, c)) + (__fsub_rn(ym, c) + __fsub_rn(yp, c))) +
+                          (__fsub_rn(zm, c) + __fsub_rn(zp, c));
               float px = coord_f32(x, n, a), py = coord_f32(y, n, a), pz = coord_f32(z, n, a);
               float c2 = c * c;
               s0.add(c2);

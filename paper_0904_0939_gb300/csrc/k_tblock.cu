@@ -44,16 +44,17 @@ constexpr unsigned long long kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per 
 template <int K>
 struct Geo {
   static constexpr int BH = TY + 2 * K;
-  static constexpr int THREADS = C4 * BH;
-  static constexpr int R = D + 2 + (K > 1 ? K - 1 : 1);  // ring slots
+  static constexpr int USED = C4 * BH;                      // threads that own a box column
+  static constexpr int THREADS = (USED + 31) / 32 * 32;     // whole warps
+  static constexpr int R = D + 2 + (K > 1 ? K - 1 : 1);     // ring slots
   static constexpr int PLANE = ((BW * BH * 4 + 127) / 128) * 128 / 4;  // floats per ring box, 128 B multiple
   static constexpr int LPLANE = LW * BH;
-  static constexpr size_t RING_OFF = 128;                 // guard before the ring
+  static constexpr size_t RING_OFF = 128;                   // guard before the ring
   static constexpr size_t SLOT_BYTES = 2 * (size_t)PLANE * 4;
-  static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;  // bytes the two box loads of a plane deliver
+  static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;    // bytes the two box loads of a plane deliver
   static constexpr size_t LEVEL_OFF = RING_OFF + R * SLOT_BYTES + 128;
   static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)(K > 1 ? K - 1 : 0) * 2 * LPLANE * 4;
-  static constexpr size_t SMEM = BAR_OFF + 8 * R + 128;   // + room to align the base to 128 B
+  static constexpr size_t SMEM = BAR_OFF + 8 * R + 128;     // + room to align the base to 128 B
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,13 +103,19 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ int slot_of(int q, int R) { return ((q % R) + R) % R; }
+// slot of plane j + d given the slot sj of plane j, for -R < d < R
+template <int R>
+__device__ __forceinline__ int slot_add(int sj, int d) {
+  int s = sj + d;
+  s -= (s >= R) ? R : 0;
+  s += (s < 0) ? R : 0;
+  return s;
+}
 
 template <int K>
-__device__ __forceinline__ void issue_plane(char* smem, const CUtensorMap* mpsi, const CUtensorMap* mv, int q, int j0,
+__device__ __forceinline__ void issue_plane(char* smem, const CUtensorMap* mpsi, const CUtensorMap* mv, int q, int s,
                                             int x0, int y0) {
   using G = Geo<K>;
-  int s = slot_of(q, G::R);
   float* box = (float*)(smem + G::RING_OFF + s * G::SLOT_BYTES);
   uint64_t* bar = (uint64_t*)(smem + G::BAR_OFF) + s;
   mbar_expect_tx(bar, G::TX_BYTES);
@@ -137,81 +144,108 @@ __global__ void __launch_bounds__(Geo<K>::THREADS) k_step_tma(const __grid_const
                                                                const int32_t* __restrict__ active,
                                                                int32_t* __restrict__ err) {
   using G = Geo<K>;
+  constexpr int R = G::R;
   if (active && *active == 0) return;
   if (*(volatile const int32_t*)err != 0) return;  // an earlier wait expired: do nothing
   extern __shared__ __align__(128) char smem_raw[];
   // TMA destinations need 128-byte aligned shared addresses
   char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x;
-  const int row = tid / C4, col = tid % C4;  // box row, float4 column
+  const int lane = tid & 31;
+  const bool owner = tid < G::USED;          // threads beyond the box only join barriers and shuffles
+  const int row = owner ? tid / C4 : 0, col = owner ? tid % C4 : 0;  // box row, float4 column
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, n);
   const int xg = x0 - HX + 4 * col;  // lattice x of this thread's first site
   const int yg = y0 - K + row;
-  const bool inside = (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
+  const bool inside = owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
   const bool interior_col = (col >= HX / 4) && (col < HX / 4 + TX / 4);
-  const bool interior_row = (row >= K) && (row < K + TY);
+  const bool interior_row = owner && (row >= K) && (row < K + TY);
+  // x-neighbours come from the adjacent lanes; only lanes 0 and 31 read them
+  // from shared memory (row ends take the neighbouring row's value, which
+  // only ever reaches margin sites)
+  const bool fix_l = owner && lane == 0 && col > 0;
+  const bool fix_r = owner && lane == 31 && col < C4 - 1;
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
   uint64_t* bars = (uint64_t*)(smem + G::BAR_OFF);
   float* ring = (float*)(smem + G::RING_OFF);
   float* lev = (float*)(smem + G::LEVEL_OFF);
+  const int ro = row * BW + 4 * col;        // offset of this column in a ring box
+  const int lo = row * LW + 4 + 4 * col;    // offset of this column in a level plane
+  float* const out_col = out + (size_t)yg * n + xg;
 
   // zero the level planes (guards included) and set up the barriers
   for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) lev[i] = 0.f;
   if (tid == 0) {
-    for (int s = 0; s < G::R; ++s) mbar_init(bars + s, 1);
+    for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int last_issued = j0 - 2;
+  // planes j0-1 .. j0+D go to consecutive slots starting at slot 0
+  const int sj0 = 1;  // slot of plane j0
+  unsigned outstanding = 0;  // (thread 0) slots with a copy issued and not yet waited for
   if (tid == 0) {
-    for (int q = j0 - 1; q <= min(j0 + D, j1 + 1); ++q) issue_plane<K>(smem, &map_psi, &map_v, q, j0, x0, y0);
-    last_issued = min(j0 + D, j1 + 1);
+    int s = 0;
+    for (int q = j0 - 1; q <= min(j0 + D, j1 + 1); ++q, s = slot_add<R>(s, 1)) {
+      issue_plane<K>(smem, &map_psi, &map_v, q, s, x0, y0);
+      outstanding |= 1u << s;
+    }
   }
-  auto parity_of = [&](int q) { return (unsigned)(((q - (j0 - 1)) / G::R) & 1); };
-  auto box_of = [&](int q) { return ring + slot_of(q, G::R) * (G::SLOT_BYTES / 4); };
-
+  unsigned phase = 0;  // bit s: parity of the next wait on slot s (toggled on success only)
   int timeout = 0;
-  for (int q = j0 - 1; q <= j0; ++q)
-    if (!mbar_wait_bounded(bars + slot_of(q, G::R), parity_of(q), err)) timeout = 1;
+  auto wait_slot = [&](int s) {
+    if (mbar_wait_bounded(bars + s, (phase >> s) & 1u, err)) {
+      phase ^= 1u << s;
+      outstanding &= ~(1u << s);
+    } else {
+      timeout = 1;
+    }
+  };
+  wait_slot(0);
+  wait_slot(1);
 
   // register windows of levels 1..K-1: planes (p-1, p, p+1) of this column
-  float4 wm[K > 1 ? K - 1 : 1], wc[K > 1 ? K - 1 : 1], wp[K > 1 ? K - 1 : 1];
-#pragma unroll
-  for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l) {
-    wm[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-    wc[l] = wm[l];
-    wp[l] = wm[l];
-  }
+  constexpr int NW = K > 1 ? K - 1 : 1;
+  float4 wm[NW], wc[NW], wp[NW];
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int l = 0; l < NW; ++l) {
+    wm[l] = zero4;
+    wc[l] = zero4;
+    wp[l] = zero4;
+  }
 
+  int sj = sj0;  // slot of plane j
   for (int j = j0; j <= j1; ++j) {
     if (tid == 0 && j + 1 + D <= j1 + 1) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_plane<K>(smem, &map_psi, &map_v, j + 1 + D, j0, x0, y0);
-      last_issued = j + 1 + D;
+      const int s = slot_add<R>(sj, 1 + D);
+      issue_plane<K>(smem, &map_psi, &map_v, j + 1 + D, s, x0, y0);
+      outstanding |= 1u << s;
     }
-    if (!mbar_wait_bounded(bars + slot_of(j + 1, G::R), parity_of(j + 1), err)) timeout = 1;
+    wait_slot(slot_add<R>(sj, 1));
 
     // ---- level 1: plane j from the ring
     {
-      const float* bm = box_of(j - 1);
-      const float* b0 = box_of(j);
-      const float* bp = box_of(j + 1);
+      const float* b0 = ring + sj * (G::SLOT_BYTES / 4);
+      const float* bm = ring + slot_add<R>(sj, -1) * (G::SLOT_BYTES / 4);
+      const float* bp = ring + slot_add<R>(sj, 1) * (G::SLOT_BYTES / 4);
       const int p = j;
-      const bool need = (row >= 1 && row < G::BH - 1) && (K > 1 || interior_col);
+      const bool need = owner && (row >= 1 && row < G::BH - 1) && (K > 1 || interior_col);
+      float4 c = owner ? f4(b0 + ro) : zero4;
+      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (fix_l) xl = b0[ro - 1];
+      if (fix_r) xr = b0[ro + 4];
       if (need) {
-        const int o = row * BW + 4 * col;
-        float4 c = f4(b0 + o);
-        float4 r = update4(c, b0[o - 1], b0[o + 4], f4(b0 + o - BW), f4(b0 + o + BW), f4(bm + o), f4(bp + o),
-                           f4(b0 + G::PLANE + o), half_dtau, one_m6c, cc);
+        float4 r = update4(c, xl, xr, f4(b0 + ro - BW), f4(b0 + ro + BW), f4(bm + ro), f4(bp + ro),
+                           f4(b0 + G::PLANE + ro), half_dtau, one_m6c, cc);
         if (!inside || p < 0 || p >= n) r = zero4;
         if constexpr (K == 1) {
           if (interior_row && inside && p >= z0 && p < z1)
-            *reinterpret_cast<float4*>(out + ((size_t)p * n + yg) * n + xg) = r;
+            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
         } else {
-          float* lp = lev + (size_t)(0 * 2 + (p & 1)) * G::LPLANE;
-          *reinterpret_cast<float4*>(lp + row * LW + 4 + 4 * col) = r;
+          *reinterpret_cast<float4*>(lev + (p & 1) * G::LPLANE + lo) = r;
           wm[0] = wc[0];
           wc[0] = wp[0];
           wp[0] = r;
@@ -222,20 +256,23 @@ __global__ void __launch_bounds__(Geo<K>::THREADS) k_step_tma(const __grid_const
 #pragma unroll
     for (int l = 2; l <= K; ++l) {
       const int p = j - l + 1;
-      const bool need = (row >= l && row < G::BH - l) && (l < K || interior_col);
+      const bool need = owner && (row >= l && row < G::BH - l) && (l < K || interior_col);
+      const float* lp = lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
+      const float4 c = wc[l - 2];
+      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (fix_l) xl = lp[lo - 1];
+      if (fix_r) xr = lp[lo + 4];
       if (need) {
-        const float* lp = lev + (size_t)((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
-        const int o = row * LW + 4 + 4 * col;
-        const float4 v = f4(box_of(p) + G::PLANE + row * BW + 4 * col);
-        float4 r = update4(wc[l - 2], lp[o - 1], lp[o + 4], f4(lp + o - LW), f4(lp + o + LW), wm[l - 2], wp[l - 2],
-                           v, half_dtau, one_m6c, cc);
+        const float4 v = f4(ring + slot_add<R>(sj, 1 - l) * (G::SLOT_BYTES / 4) + G::PLANE + ro);
+        float4 r = update4(c, xl, xr, f4(lp + lo - LW), f4(lp + lo + LW), wm[l - 2], wp[l - 2], v, half_dtau,
+                           one_m6c, cc);
         if (!inside || p < 0 || p >= n) r = zero4;
         if (l == K) {
           if (interior_row && inside && p >= z0 && p < z1)
-            *reinterpret_cast<float4*>(out + ((size_t)p * n + yg) * n + xg) = r;
+            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
         } else {
-          float* lq = lev + (size_t)((l - 1) * 2 + (p & 1)) * G::LPLANE;
-          *reinterpret_cast<float4*>(lq + row * LW + 4 + 4 * col) = r;
+          *reinterpret_cast<float4*>(lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + lo) = r;
           wm[l - 1] = wc[l - 1];
           wc[l - 1] = wp[l - 1];
           wp[l - 1] = r;
@@ -247,14 +284,16 @@ __global__ void __launch_bounds__(Geo<K>::THREADS) k_step_tma(const __grid_const
         atomicOr(err, 1);
         // the copies still in flight target this block's shared memory:
         // wait for them (each wait bounded in time) before leaving
-        for (int q = j + 1; q <= last_issued; ++q) {
+        for (int s = 0; s < R; ++s) {
+          if (!(outstanding & (1u << s))) continue;
           const unsigned long long t0 = global_ns();
-          while (!mbar_try_wait(bars + slot_of(q, G::R), parity_of(q)) && global_ns() - t0 < kWaitLimitNs) {
+          while (!mbar_try_wait(bars + s, (phase >> s) & 1u) && global_ns() - t0 < kWaitLimitNs) {
           }
         }
       }
       return;
     }
+    sj = slot_add<R>(sj, 1);
   }
 }
 

@@ -140,7 +140,9 @@ def test_fp32_converged_energy_within_1e6(fd, orc, mask):
     lat = wl.config_small_ho()
     v = lat.potential()
     _, rec, _ = orc.evolve(orc.init_symmetric(lat.n, 2, mask), v, lat.a, lat.dtau, 200000, 100, 1e-13, False, mask)
-    s = solver(fd, lat.n, lat.length, fd.F32, tol=1e-9, tol_relative=1)
+    # FP32 evaluation of E fluctuates between checks at ~1e-9..1e-8 relative
+    # once the iteration has converged, so the run stops at 1e-8
+    s = solver(fd, lat.n, lat.length, fd.F32, tol=1e-8, tol_relative=1)
     s.set_potential(v)
     s.init_symmetric(2, mask)
     steps, conv = s.evolve(200000)
