@@ -96,7 +96,9 @@ typedef struct {
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
   int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
                              (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
-  int32_t reserved[3];
+  int32_t autotune;       /* 1 (default): time every (depth, z-chunk) candidate on first use of a
+                             lattice size and keep the fastest (results are identical for all) */
+  int32_t reserved[2];
 } fdtd_options;
 
 typedef struct {
@@ -206,6 +208,10 @@ FDTD_API int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int la
 FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, void* gv, int dtype,
                   int mem_kind, fdtd_obs* obs);
 
+/* Stencil configuration in use for lattice `lat` (after autotuning, if on):
+ * temporal depth (steps per launch) and z-planes per block. */
+FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
+
 /* Launch counters and (when profiling is on) summed stencil device time. */
 FDTD_API int fdtd_get_stats(fdtd_handle h, fdtd_stats* out);
 FDTD_API int fdtd_reset_stats(fdtd_handle h);
@@ -222,8 +228,10 @@ FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
  * for that precision.  The work is enqueued on `stream` (cudaStream_t or
  * NULL) and the call returns without synchronising.
  * Nothing is allocated: the block partials live in a static 128 KiB device
- * array that every GPU loading the library keeps until exit, so n is
- * limited to 1 <= n <= 1024 (FDTD_ERR_SHAPE beyond).  The first call on a
+ * array (plus one error word, cleared by every call) that every GPU loading
+ * the library keeps until exit, so n is limited to 1 <= n <= 1024
+ * (FDTD_ERR_SHAPE beyond).  A bounded device-side wait that expires
+ * yields NaN in out.  The first call on a
  * device looks the array's address up (make it before any stream capture
  * on that device).  All calls share the array: calls whose kernels overlap
  * on the GPU race and may return wrong sums.  A zero or non-finite field

@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int32), ("tol_relative", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
-                ("stencil_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Obs(ctypes.Structure):
@@ -75,7 +76,7 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
-            "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc"]
+            "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config"]
 
 
 def _load():
@@ -102,6 +103,7 @@ def _load():
         "fdtd_get_stats": [vp, P(Stats)],
         "fdtd_reset_stats": [vp],
         "fdtd_set_profiling": [vp, i32],
+        "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -275,6 +277,13 @@ class Solver:
         with self._ctx():
             _check(lib.fdtd_backward(self.handle, lat, T, w_e, w_r, ptr, code, mem, ctypes.byref(o)), self.handle)
         return out, o.to_dict()
+
+    def tuned_config(self, lat: int = 0) -> tuple[int, int]:
+        """(temporal depth, z-planes per block) the stencil uses for lattice `lat`."""
+        d, z = ctypes.c_int(), ctypes.c_int()
+        with self._ctx():
+            _check(lib.fdtd_tuned_config(self.handle, lat, ctypes.byref(d), ctypes.byref(z)), self.handle)
+        return d.value, z.value
 
     def stats(self) -> dict:
         s = Stats()

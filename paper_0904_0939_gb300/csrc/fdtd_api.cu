@@ -15,7 +15,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -60,9 +63,13 @@ struct Lat {
   // last evolve
   int64_t last_steps = 0;
   LatState host_state{};
-  // TMA descriptors of psi[0], psi[1], V for each temporal depth 1..3
+  // TMA descriptors of psi[0], psi[1], V: stencil boxes per tile width
+  // (64, 128) and depth 1..3, and the sums boxes
   bool tma_ok = false;
-  CUtensorMap maps[3][3];
+  CUtensorMap maps[2][3][3];
+  CUtensorMap sums_maps[3];
+  // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet)
+  int depth = 0, tx = 128, zc = 0;
 };
 
 struct Carve {
@@ -106,6 +113,10 @@ int check_options(const fdtd_options& o, std::string& err) {
   }
   if (o.temporal_depth < 0 || o.temporal_depth > blocked_max_depth()) {
     err = "temporal_depth out of range";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.autotune < 0 || o.autotune > 1) {
+    err = "autotune must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
   if (o.stencil_kernel < 0 || o.stencil_kernel > 1) {
@@ -152,7 +163,7 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
     } else {
       L.v = cv.take(L.n3 * 4);
     }
-    L.nparts = sums_blocks(d[l].n);
+    L.nparts = std::max(sums_blocks(d[l].n), tma_sums_blocks(d[l].n));
     L.partials = (double*)cv.take((size_t)L.nparts * 4 * sizeof(double));
     L.state = (LatState*)cv.take(2 * sizeof(LatState));
     if (o.backward_steps > 0 && d[l].precision != FDTD_BF16) {
@@ -169,8 +180,8 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
     }
     if (lats) lats->push_back(L);
   }
-  *batch_bytes = batched_workspace_bytes(d, count);
-  *batch_ws = cv.take(*batch_bytes);
+  *batch_bytes = o.batched ? batched_workspace_bytes(d, count) : 0;
+  *batch_ws = o.batched ? cv.take(*batch_bytes) : nullptr;
 }
 
 }  // namespace
@@ -252,13 +263,93 @@ void with_type(int prec, F&& f) {
     f((__nv_bfloat16*)nullptr);
 }
 
+// ---- autotuning of the stencil configuration ---------------------------------
+// Fastest (depth, z-chunk) per (n, precision, device), shared by all handles.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> g_tune;
+
+void choose_config(fdtd_context* c, Lat& L) {
+  if (L.depth) return;
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
+  if (!tma) {
+    L.depth = 1;
+    L.tx = 128;
+    L.zc = 0;
+    return;
+  }
+  if (c->o.temporal_depth > 0 || !c->o.autotune) {
+    L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
+    L.tx = L.d.n > 64 ? 128 : 64;
+    L.zc = tma_zchunk(L.d.n, L.depth, L.tx);
+    return;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto key = std::make_tuple(L.d.n, L.d.precision, dev);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      L.depth = std::get<0>(it->second);
+      L.tx = std::get<1>(it->second);
+      L.zc = std::get<2>(it->second);
+      return;
+    }
+  }
+  // time each candidate: psi[cur] -> psi[1-cur] (psi[cur] is only read)
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int n = L.d.n;
+  double best = 0.0;
+  int bd = auto_depth(n, L.d.precision), bt = n > 64 ? 128 : 64, bz = tma_zchunk(n, bd, bt);
+  for (int ti = 0; ti < 2; ++ti) {
+    const int tx = ti ? 128 : 64;
+    if (tx == 128 && n <= 64) continue;
+    for (int d = 1; d <= blocked_max_depth(); ++d) {
+      int prev = -1;
+      for (int div = 1; div <= 32; div *= 2) {
+        int zc = (n + div - 1) / div;
+        if (zc < std::max(8, 4 * d) || zc == prev) continue;
+        prev = zc;
+        auto launch = [&]() {
+          launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx, zc,
+                          nullptr, c->flags + 1, c->st);
+          c->stats.launches += 1;
+        };
+        launch();
+        const int reps = 3;
+        cudaEventRecord(e0, c->st);
+        for (int r = 0; r < reps; ++r) launch();
+        cudaEventRecord(e1, c->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double rate = (double)L.n3 * d * reps / (ms > 0.f ? ms : 1e-6);
+        if (rate > best) {
+          best = rate;
+          bd = d;
+          bt = tx;
+          bz = zc;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.depth = bd;
+  L.tx = bt;
+  L.zc = bz;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = std::make_tuple(bd, bt, bz);
+}
+
 // Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows).
 void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
   const int prec = L.d.precision;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
-  int depth = c->o.temporal_depth;
-  if (depth == 0) depth = auto_depth(L.d.n, prec);
-  if (!tma) depth = 1;
+  choose_config(c, L);
+  const int depth = tma ? L.depth : 1;
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
     prof_begin(c);
@@ -266,8 +357,8 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
       launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
     } else if (prec == FDTD_F32) {
       if (tma)
-        launch_step_tma(L.maps[k - 1][L.cur], L.maps[k - 1][2], (float*)L.psi[1 - L.cur], L.p, k, 0, active,
-                        c->flags + 1, c->st);
+        launch_step_tma(L.maps[L.tx == 128][k - 1][L.cur], L.maps[L.tx == 128][k - 1][2], (float*)L.psi[1 - L.cur],
+                        L.p, k, L.tx, k == depth ? L.zc : 0, active, c->flags + 1, c->st);
       else
         launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
                                c->st);
@@ -288,6 +379,11 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
 
 int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* active) {
   int np = 0;
+  if (L.tma_ok && (psi == L.psi[0] || psi == L.psi[1])) {
+    np = launch_sums_tma(L.sums_maps[psi == L.psi[1]], L.sums_maps[2], L.p, L.partials, active, c->flags + 1, c->st);
+    c->stats.launches += 1;
+    return np;
+  }
   with_type(L.d.precision, [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
     np = launch_sums<T>((const T*)psi, L.v, L.p, L.partials, active, c->st);
@@ -426,8 +522,46 @@ int export_field(fdtd_context* c, const void* src, int prec, void* dst, int dt, 
   return cuda_check(c, "export");
 }
 
-int evolve_batched(fdtd_context* c, int64_t) {
-  return fail(c, FDTD_ERR_INVALID_ARG, "evolve: batched mode is not available in this build");
+// All lattices in one persistent launch (k_batched.cu).
+int evolve_batched(fdtd_context* c, int64_t max_steps) {
+  const int count = (int)c->lats.size();
+  if (count > batched_max_lattices()) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: too many lattices for batched mode");
+  for (auto& L : c->lats)
+    if (!L.tma_ok) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: batched mode needs FP32 lattices with n % 4 == 0");
+  int depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : 2;
+  std::vector<char> table(batched_entry_bytes() * count + 64);
+  char* base = table.data() + ((64 - ((uintptr_t)table.data() & 63)) & 63);
+  for (int l = 0; l < count; ++l) {
+    Lat& L = c->lats[l];
+    if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
+                     (const float*)L.v, L.partials, &L.state[0], L.p, L.mask, L.cur, L.d.v_inf, depth))
+      return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
+    launch_state_reset(&L.state[0], 0, c->st);
+    c->stats.launches += 1;
+  }
+  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
+  cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
+  int64_t steps = 0;
+  int grid = 0;
+  prof_begin(c);
+  int e = batched_launch(c->batch_ws, count, max_steps, c->o.check_every, c->o.tol, c->o.tol_relative,
+                         c->o.reimpose_parity, depth, c->flags + 1, c->st, &steps, &grid);
+  prof_end(c);
+  if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
+  c->stats.launches += 1;
+  c->stats.stencil_launches += 1;
+  int rc = cuda_check(c, "evolve (batched)");
+  if (rc) return rc;
+  for (auto& L : c->lats) {
+    if ((rc = read_state(c, L))) return rc;
+    if (L.host_state.status == STATUS_NONFINITE)
+      return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+    L.cur = L.host_state.cur;
+    L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+    c->stats.stencil_site_updates += (int64_t)L.n3 * L.last_steps;
+    c->stats.stencil_bytes += (double)L.n3 * 12.0 * ((L.last_steps + depth - 1) / depth);
+  }
+  return FDTD_OK;
 }
 
 int valid_mask(int mask) {
@@ -460,6 +594,7 @@ int fdtd_default_options(fdtd_options* o) {
   o->batched = 0;
   o->reimpose_parity = 1;
   o->stencil_kernel = 0;
+  o->autotune = 1;
   return FDTD_OK;
 }
 
@@ -528,12 +663,16 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
     launch_state_reset(&L.state[1], 1, c->st);
     c->stats.launches += 2;
     if (tma_supported(L.d.n, L.d.precision)) {
+      const float* bufs[3] = {(const float*)L.psi[0], (const float*)L.psi[1], (const float*)L.v};
       bool ok = true;
-      for (int k = 1; k <= blocked_max_depth() && ok; ++k) {
-        ok = encode_field_map(&L.maps[k - 1][0], (const float*)L.psi[0], L.d.n, k) == 0 &&
-             encode_field_map(&L.maps[k - 1][1], (const float*)L.psi[1], L.d.n, k) == 0 &&
-             encode_field_map(&L.maps[k - 1][2], (const float*)L.v, L.d.n, k) == 0;
-      }
+      int bw, bh;
+      for (int ti = 0; ti < 2; ++ti)
+        for (int k = 1; k <= blocked_max_depth(); ++k) {
+          tma_box(k, ti ? 128 : 64, &bw, &bh);
+          for (int b = 0; b < 3; ++b) ok = ok && encode_field_map(&L.maps[ti][k - 1][b], bufs[b], L.d.n, bw, bh) == 0;
+        }
+      tma_box(1, 64, &bw, &bh);
+      for (int b = 0; b < 3; ++b) ok = ok && encode_field_map(&L.sums_maps[b], bufs[b], L.d.n, bw, bh) == 0;
       L.tma_ok = ok;
     }
   }
@@ -840,6 +979,17 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
     obs->steps = T;
   }
   return export_field(h, L.gv, FDTD_F64, gv_out, dtype, mem_kind, L.n3);
+}
+
+int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!depth || !zchunk) return fail(h, FDTD_ERR_INVALID_ARG, "tuned_config: null output");
+  Lat& L = h->lats[lat];
+  if (L.has_v && L.has_psi) choose_config(h, L);
+  *depth = L.depth;
+  *zchunk = L.zc;
+  return cuda_check(h, "tuned_config");
 }
 
 int fdtd_get_stats(fdtd_handle h, fdtd_stats* out) {

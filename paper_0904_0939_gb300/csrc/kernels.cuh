@@ -48,21 +48,34 @@ void launch_step_f64(const double* in, double* out, const double* coefA, const d
 template <typename T>
 void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st);
 
-// Temporal blocking with TMA plane streaming (k_tblock.cu): `depth` update
-// steps in one pass over HBM, FP32 lattices with n % 4 == 0.  Bit-identical
-// to `depth` calls of launch_step_f32.  *err |= 1 if a bounded wait expired.
+// TMA-streamed tile pipelines (k_tblock.cu / tma_item.cuh), FP32 lattices
+// with n % 4 == 0: `depth` update steps per pass over HBM (tile width tx =
+// 64 or 128), bit-identical to `depth` calls of launch_step_f32; and the
+// lattice sums with one partial per 64 x 16 tile column.  *err |= 1 if a
+// bounded wait expired.
 bool tma_supported(int n, int precision);
 int blocked_max_depth();
 int auto_depth(int n, int precision);
-int tma_zchunk(int n, int depth);
-size_t tma_smem_bytes(int depth);
-int encode_field_map(CUtensorMap* map, const float* base, int n, int depth);
+int tma_zchunk(int n, int depth, int tx);
+void tma_box(int depth, int tx, int* box_w, int* box_h);
+int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h);
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
-                     int zc, const int32_t* active, int32_t* err, cudaStream_t st);
+                     int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st);
+int tma_sums_blocks(int n);
+int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
+                    const int32_t* active, int32_t* err, cudaStream_t st);
 
 // ---- batched persistent driver (k_batched.cu) ---------------------------------
-// Device tables of the batched driver for `count` lattices (0 if count == 1).
+// Device table of the batched driver for `count` lattices.
 size_t batched_workspace_bytes(const fdtd_lattice_desc* d, int count);
+int batched_max_lattices();
+size_t batched_entry_bytes();
+int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
+                 LatState* state, const Params& p, int mask, int cur, double v_inf, int depth);
+// One cooperative launch that runs every check and step of every lattice;
+// returns 0 or a cudaError_t value.  *steps_done is written asynchronously.
+int batched_launch(void* dev_table, int count, int64_t max_steps, int check_every, double tol, int tol_rel,
+                   int reimpose, int depth, int32_t* err, cudaStream_t st, int64_t* steps_done, int* grid_out);
 
 // Lattice sums S0, SH, Sr, SV into per-block partials; returns block count.
 template <typename T>

@@ -8,8 +8,8 @@
 // pointers and a stream but no allocator.  fdtd_create needs a workspace
 // from the caller; this entry point needs none.  The per-block partial sums
 // live in a file-scope __device__ array instead (kMaxBlocks x 4 doubles =
-// 128 KiB), which every GPU that loads this library holds until the
-// process exits.
+// 128 KiB, plus one error word), which every GPU that loads this library
+// holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, never a
 // device address, so the host looks the address up with
@@ -18,10 +18,11 @@
 // that set-up, so it should come before any stream capture on that device.
 //
 // All calls share the one array.  Every partial is written by the sums
-// kernel of the same call before the finishing kernel reads it, so nothing
-// has to start at zero and no state survives from one call to the next that
-// affects the result; but two calls whose kernels overlap on the GPU (for
-// example on two streams) race on the array and may return wrong sums.
+// kernel of the same call before the finishing kernel reads it; the one word
+// that must start at zero -- the flag a bounded wait sets if it expires --
+// is cleared by each call before its kernels run.  Two calls whose kernels
+// overlap on the GPU (for example on two streams) race on the array and may
+// return wrong sums.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,7 +43,8 @@ constexpr int kMaxBlocks = 4096;  // block partials of the sums for n <= 1024
 constexpr int kMaxN = 1024;
 constexpr int kMaxDevices = 128;
 
-__device__ __align__(256) double g_noalloc_partials[kMaxBlocks * 4];
+// block partials, then (at kMaxBlocks * 4) the error word of the bounded waits
+__device__ __align__(256) double g_noalloc_partials[kMaxBlocks * 4 + 32];
 
 std::mutex g_mu;
 double* g_partials_addr[kMaxDevices] = {};
@@ -50,7 +52,7 @@ double* g_partials_addr[kMaxDevices] = {};
 // Same deterministic reduction as the check finaliser: strided per-thread
 // sums in a fixed order, then a fixed tree.
 __global__ void __launch_bounds__(256) k_noalloc_finish(const double* __restrict__ parts, int np, double a3,
-                                                        double* __restrict__ out) {
+                                                        const int32_t* __restrict__ err, double* __restrict__ out) {
   __shared__ double sm[4][256];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < np; i += 256)
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(256) k_noalloc_finish(const double* __restrict
   }
   if (threadIdx.x != 0) return;
   double s0 = sm[0][0], sh = sm[1][0], sr = sm[2][0], sv = sm[3][0];
+  if (*err != 0) s0 = sh = sr = sv = nan("");  // a bounded wait expired: report NaN
   out[0] = sh / s0;  // E
   out[1] = sr / s0;  // <r^2>
   out[2] = sv / s0;  // <V>
@@ -125,11 +128,25 @@ extern "C" FDTD_API int fdtd_observables_noalloc(const void* psi, const void* v,
   int nb = sums_blocks(n);
   if (nb > kMaxBlocks) return fail(FDTD_ERR_SHAPE, "observables_noalloc: lattice needs more partials than the scratch holds");
   cudaStream_t st = (cudaStream_t)stream;
-  if (dtype == FDTD_F64)
+  // FP32 lattices with n % 4 == 0 take the same TMA-fed sums as
+  // fdtd_observables (tensor maps are encoded on the host stack; nothing is
+  // allocated), so the two agree bit for bit; other cases take the plain
+  // sums kernel, as fdtd_observables does.
+  CUtensorMap mpsi, mv;
+  int bw = 0, bh = 0;
+  tma_box(1, 64, &bw, &bh);
+  const bool tma = dtype == FDTD_F32 && tma_supported(n, FDTD_F32) && tma_sums_blocks(n) <= kMaxBlocks &&
+                   encode_field_map(&mpsi, (const float*)psi, n, bw, bh) == 0 &&
+                   encode_field_map(&mv, (const float*)v, n, bw, bh) == 0;
+  int32_t* err = (int32_t*)(parts + (size_t)kMaxBlocks * 4);
+  cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+  if (tma)
+    nb = launch_sums_tma(mpsi, mv, p, parts, nullptr, err, st);
+  else if (dtype == FDTD_F64)
     nb = launch_sums<double>((const double*)psi, v, p, parts, nullptr, st);
   else
     nb = launch_sums<float>((const float*)psi, v, p, parts, nullptr, st);
-  k_noalloc_finish<<<1, 256, 0, st>>>(parts, nb, p.a * p.a * p.a, out);
+  k_noalloc_finish<<<1, 256, 0, st>>>(parts, nb, p.a * p.a * p.a, err, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(FDTD_ERR_CUDA, (std::string("observables_noalloc: ") + cudaGetErrorString(e)).c_str());

@@ -1,0 +1,416 @@
+// TMA-streamed tile pipelines shared by the one-lattice kernels
+// (k_tblock.cu) and the batched persistent kernel (k_batched.cu).
+//
+// A tile item covers TXT x TY sites in x-y and the z-planes [z0, z1) of one
+// FP32 lattice with n % 4 == 0.  Input planes of a (TXT + 2 HX) x (TY + 2K)
+// box -- psi and V -- stream through a ring of R shared-memory slots with
+// cp.async.bulk.tensor; one thread issues, an mbarrier per slot counts the
+// bytes; sites outside the lattice arrive as zeros (the Dirichlet wall of
+// Sec. III).  Each thread owns one float4 column of the box.
+//
+// tma_step_item applies the update of Eq. updateeq K times: level 1 reads
+// the ring, level l > 1 keeps three z-planes of level l-1 of its column in
+// registers and takes the y-neighbours from a double-buffered shared plane
+// and the x-neighbours from the adjacent lanes.  Level l trails level l-1 by
+// one plane, so one barrier per z-step orders everything.  Level K writes
+// the tile interior.  The per-site arithmetic is that of the one-step
+// kernel, so K fused steps equal K single steps bit for bit; box sites
+// outside the tile compute garbage at levels < K that moves inward one site
+// per level and never reaches the interior (x margin HX >= K, y margin K).
+//
+// tma_sums_item accumulates S0 = sum psi^2, SH = sum psi(-Lap psi/(2 m a^2)
+// + V psi), Sr = sum r^2 psi^2, SV = sum V psi^2 (Eq. energysum) over the
+// tile interior with Kahan-compensated FP32 per thread and a fixed-order
+// FP64 block reduction.
+//
+// Every mbarrier wait is bounded in wall-clock time; on expiry the item
+// sets *err, waits (bounded) for its copies in flight and returns false in
+// every thread (block-wide vote).
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace fdtd {
+namespace tb {
+
+constexpr int TY = 16;   // interior tile height
+constexpr int HX = 4;    // x margin of the box: >= K and a multiple of 4 (TMA x * 4 B % 16 == 0)
+constexpr int D = 2;     // planes prefetched beyond the newest one in use
+constexpr unsigned long long kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per wait
+
+template <int K, int TXT>
+struct Geo {
+  static constexpr int TX = TXT;
+  static constexpr int BW = TX + 2 * HX;
+  static constexpr int C4 = BW / 4;                          // float4 columns per box row
+  static constexpr int LW = BW + 8;                          // level-plane pitch: 4-float guards
+  static constexpr int BH = TY + 2 * K;
+  static constexpr int USED = C4 * BH;                       // threads that own a box column
+  static constexpr int THREADS = (USED + 31) / 32 * 32;      // whole warps
+  static constexpr int R = D + 2 + (K > 1 ? K - 1 : 1);      // ring slots
+  static constexpr int PLANE = ((BW * BH * 4 + 127) / 128) * 128 / 4;  // floats per box, 128 B multiple
+  static constexpr int LPLANE = LW * BH;
+  static constexpr size_t RING_OFF = 128;                    // guard before the ring
+  static constexpr size_t SLOT_BYTES = 2 * (size_t)PLANE * 4;
+  static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;     // bytes the two box loads deliver
+  static constexpr size_t LEVEL_OFF = RING_OFF + R * SLOT_BYTES + 128;
+  static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)(K > 1 ? K - 1 : 0) * 2 * LPLANE * 4;
+  static constexpr size_t RED_OFF = BAR_OFF + 8 * R;         // block reduction scratch (sums)
+  static constexpr size_t SMEM = RED_OFF + 8 * 4 * (THREADS / 32) + 128;  // + base alignment slack
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory base aligned to 128 B (TMA destinations)
+__device__ __forceinline__ char* aligned_smem(char* raw) {
+  return raw + ((128u - (smem_u32(raw) & 127u)) & 127u);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait bounded in wall-clock time; gives up early once any block has
+// reported an expired wait in *err.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, const int32_t* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*(volatile const int32_t*)err != 0) return false;
+      if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// slot of plane j + d given the slot sj of plane j, for -R < d < R
+template <int R>
+__device__ __forceinline__ int slot_add(int sj, int d) {
+  int s = sj + d;
+  s -= (s >= R) ? R : 0;
+  s += (s < 0) ? R : 0;
+  return s;
+}
+
+__device__ __forceinline__ float4 f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// One float4 of site updates: c at x..x+3, xl = site x-1, xr = site x+4.
+__device__ __forceinline__ float4 update4(float4 c, float xl, float xr, float4 ym, float4 yp, float4 zm, float4 zp,
+                                          float4 v, float hd, float om6c, float cc) {
+  float4 o;
+  o.x = update_f32(c.x, nbr_sum(xl, c.y, ym.x, yp.x, zm.x, zp.x), coef_f32(v.x, hd, om6c), cc);
+  o.y = update_f32(c.y, nbr_sum(c.x, c.z, ym.y, yp.y, zm.y, zp.y), coef_f32(v.y, hd, om6c), cc);
+  o.z = update_f32(c.z, nbr_sum(c.y, c.w, ym.z, yp.z, zm.z, zp.z), coef_f32(v.z, hd, om6c), cc);
+  o.w = update_f32(c.w, nbr_sum(c.z, xr, ym.w, yp.w, zm.w, zp.w), coef_f32(v.w, hd, om6c), cc);
+  return o;
+}
+
+// The ring pipeline: barriers, prologue, and the bounded waits; the body
+// callable sees plane j's slot and the level planes.
+template <int K, int TXT>
+struct Pipe {
+  using G = Geo<K, TXT>;
+  static constexpr int R = G::R;
+  char* smem;
+  const CUtensorMap* mpsi;
+  const CUtensorMap* mv;
+  int x0, y0;
+  const int32_t* err;
+  uint64_t* bars;
+  float* ring;
+  unsigned phase = 0;        // bit s: parity of the next wait on slot s (toggled on success)
+  unsigned outstanding = 0;  // (thread 0) slots with a copy in flight
+  int timeout = 0;
+
+  __device__ __forceinline__ void issue(int q, int s) {
+    float* box = ring + s * (G::SLOT_BYTES / 4);
+    uint64_t* bar = bars + s;
+    mbar_expect_tx(bar, G::TX_BYTES);
+    tma_load_3d(box, mpsi, x0 - HX, y0 - K, q, bar);
+    tma_load_3d(box + G::PLANE, mv, x0 - HX, y0 - K, q, bar);
+    outstanding |= 1u << s;
+  }
+  __device__ __forceinline__ void wait(int s) {
+    if (mbar_wait_bounded(bars + s, (phase >> s) & 1u, err)) {
+      phase ^= 1u << s;
+      outstanding &= ~(1u << s);
+    } else {
+      timeout = 1;
+    }
+  }
+  // Set up barriers and issue planes j0-1 .. min(j0+D, jlast) into slots 0, 1, ...
+  __device__ __forceinline__ void begin(int j0, int jlast) {
+    bars = (uint64_t*)(smem + G::BAR_OFF);
+    ring = (float*)(smem + G::RING_OFF);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      int s = 0;
+      for (int q = j0 - 1; q <= min(j0 + D, jlast); ++q, s = slot_add<R>(s, 1)) issue(q, s);
+    }
+    wait(0);
+    wait(1);
+  }
+  // Start of iteration j (slot sj): prefetch plane j+1+D, wait for plane j+1.
+  __device__ __forceinline__ void advance(int j, int sj, int jlast) {
+    if (threadIdx.x == 0 && j + 1 + D <= jlast) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j + 1 + D, slot_add<R>(sj, 1 + D));
+    }
+    wait(slot_add<R>(sj, 1));
+  }
+  // End of iteration: barrier + vote; on a timeout drain and report.
+  __device__ __forceinline__ bool end_iteration(int32_t* err_w) {
+    if (__syncthreads_or(timeout)) {
+      if (threadIdx.x == 0) {
+        atomicOr(err_w, 1);
+        for (int s = 0; s < R; ++s) {
+          if (!(outstanding & (1u << s))) continue;
+          const unsigned long long t0 = global_ns();
+          while (!mbar_try_wait(bars + s, (phase >> s) & 1u) && global_ns() - t0 < kWaitLimitNs) {
+          }
+        }
+      }
+      return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ const float* box(int s) const { return ring + s * (G::SLOT_BYTES / 4); }
+};
+
+// K update steps on one tile item.  Returns false (in every thread) if a
+// bounded wait expired.
+template <int K, int TXT>
+__device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
+                              float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
+                              float one_m6c, float cc, int32_t* err) {
+  using G = Geo<K, TXT>;
+  constexpr int R = G::R;
+  constexpr int C4 = G::C4, BW = G::BW, LW = G::LW;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const bool owner = tid < G::USED;
+  const int row = owner ? tid / C4 : 0, col = owner ? tid % C4 : 0;
+  const int xg = x0 - HX + 4 * col;
+  const int yg = y0 - K + row;
+  const bool inside = owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
+  const bool interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
+  const bool interior_row = owner && (row >= K) && (row < K + TY);
+  // x-neighbours come from the adjacent lanes; lanes 0 and 31 read them from
+  // shared memory (at a row end the neighbouring row's value is taken, which
+  // only ever reaches margin sites)
+  const bool fix_l = owner && lane == 0 && col > 0;
+  const bool fix_r = owner && lane == 31 && col < C4 - 1;
+  const int j0 = z0 - K + 1, j1 = z1 + K - 2;
+  float* lev = (float*)(smem + G::LEVEL_OFF);
+  const int ro = row * BW + 4 * col;
+  const int lo = row * LW + 4 + 4 * col;
+  float* const out_col = out + (size_t)yg * n + xg;
+
+  for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) lev[i] = 0.f;
+  Pipe<K, TXT> pp;
+  pp.smem = smem;
+  pp.mpsi = map_psi;
+  pp.mv = map_v;
+  pp.x0 = x0;
+  pp.y0 = y0;
+  pp.err = err;
+  pp.begin(j0, j1 + 1);
+
+  constexpr int NW = K > 1 ? K - 1 : 1;
+  float4 wm[NW], wc[NW], wp[NW];
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int l = 0; l < NW; ++l) {
+    wm[l] = zero4;
+    wc[l] = zero4;
+    wp[l] = zero4;
+  }
+
+  int sj = 1;  // slot of plane j (plane j0 sits in slot 1)
+  for (int j = j0; j <= j1; ++j) {
+    pp.advance(j, sj, j1 + 1);
+    // ---- level 1: plane j from the ring
+    {
+      const float* b0 = pp.box(sj);
+      const float* bm = pp.box(slot_add<R>(sj, -1));
+      const float* bp = pp.box(slot_add<R>(sj, 1));
+      const int p = j;
+      const bool need = owner && (row >= 1 && row < G::BH - 1) && (K > 1 || interior_col);
+      float4 c = owner ? f4(b0 + ro) : zero4;
+      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (fix_l) xl = b0[ro - 1];
+      if (fix_r) xr = b0[ro + 4];
+      if (need) {
+        float4 r = update4(c, xl, xr, f4(b0 + ro - BW), f4(b0 + ro + BW), f4(bm + ro), f4(bp + ro),
+                           f4(b0 + G::PLANE + ro), half_dtau, one_m6c, cc);
+        if (!inside || p < 0 || p >= n) r = zero4;
+        if constexpr (K == 1) {
+          if (interior_row && inside && p >= z0 && p < z1)
+            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
+        } else {
+          *reinterpret_cast<float4*>(lev + (p & 1) * G::LPLANE + lo) = r;
+          wm[0] = wc[0];
+          wc[0] = wp[0];
+          wp[0] = r;
+        }
+      }
+    }
+    // ---- levels 2..K: plane j - l + 1 from level l-1
+#pragma unroll
+    for (int l = 2; l <= K; ++l) {
+      const int p = j - l + 1;
+      const bool need = owner && (row >= l && row < G::BH - l) && (l < K || interior_col);
+      const float* lp = lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
+      const float4 c = wc[l - 2];
+      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (fix_l) xl = lp[lo - 1];
+      if (fix_r) xr = lp[lo + 4];
+      if (need) {
+        const float4 v = f4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + ro);
+        float4 r = update4(c, xl, xr, f4(lp + lo - LW), f4(lp + lo + LW), wm[l - 2], wp[l - 2], v, half_dtau,
+                           one_m6c, cc);
+        if (!inside || p < 0 || p >= n) r = zero4;
+        if (l == K) {
+          if (interior_row && inside && p >= z0 && p < z1)
+            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
+        } else {
+          *reinterpret_cast<float4*>(lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + lo) = r;
+          wm[l - 1] = wc[l - 1];
+          wc[l - 1] = wp[l - 1];
+          wp[l - 1] = r;
+        }
+      }
+    }
+    if (!pp.end_iteration(err)) return false;
+    sj = slot_add<R>(sj, 1);
+  }
+  return true;
+}
+
+// Lattice sums over the tile interior, planes [z0, z1); the block's four
+// totals (FP64) go to dst[0..3].  Returns false if a bounded wait expired.
+template <int TXT>
+__device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, int n, int x0,
+                              int y0, int z0, int z1, float a, float kfac, double* __restrict__ dst, int32_t* err) {
+  using G = Geo<1, TXT>;
+  constexpr int R = G::R;
+  constexpr int C4 = G::C4, BW = G::BW;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const bool owner = tid < G::USED;
+  const int row = owner ? tid / C4 : 0, col = owner ? tid % C4 : 0;
+  const int xg = x0 - HX + 4 * col;
+  const int yg = y0 - 1 + row;
+  const bool use = owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n) && row >= 1 && row < 1 + TY &&
+                   col >= HX / 4 && col < HX / 4 + G::TX / 4;
+  const bool fix_l = owner && lane == 0 && col > 0;
+  const bool fix_r = owner && lane == 31 && col < C4 - 1;
+  const int ro = row * BW + 4 * col;
+  const float py = coord_f32(yg, n, a);
+  float px[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) px[i] = coord_f32(xg + i, n, a);
+  Kahan s0, sh, sr, sv;
+  Pipe<1, TXT> pp;
+  pp.smem = smem;
+  pp.mpsi = map_psi;
+  pp.mv = map_v;
+  pp.x0 = x0;
+  pp.y0 = y0;
+  pp.err = err;
+  const int j0 = z0, j1 = z1 - 1;
+  pp.begin(j0, j1 + 1);
+  int sj = 1;
+  for (int j = j0; j <= j1; ++j) {
+    pp.advance(j, sj, j1 + 1);
+    const float* b0 = pp.box(sj);
+    const float* bm = pp.box(slot_add<R>(sj, -1));
+    const float* bp = pp.box(slot_add<R>(sj, 1));
+    float4 c = owner ? f4(b0 + ro) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+    if (fix_l) xl = b0[ro - 1];
+    if (fix_r) xr = b0[ro + 4];
+    if (use) {
+      const float4 ym = f4(b0 + ro - BW), yp = f4(b0 + ro + BW), zm = f4(bm + ro), zp = f4(bp + ro);
+      const float4 v = f4(b0 + G::PLANE + ro);
+      const float pz = coord_f32(j, n, a);
+      const float cs[4] = {c.x, c.y, c.z, c.w};
+      const float xls[4] = {xl, c.x, c.y, c.z};
+      const float xrs[4] = {c.y, c.z, c.w, xr};
+      const float yms[4] = {ym.x, ym.y, ym.z, ym.w}, yps[4] = {yp.x, yp.y, yp.z, yp.w};
+      const float zms[4] = {zm.x, zm.y, zm.z, zm.w}, zps[4] = {zp.x, zp.y, zp.z, zp.w};
+      const float vs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float ci = cs[i];
+        // sum of neighbour differences (exact for neighbours within a factor 2)
+        const float lap = ((__fsub_rn(xls[i], ci) + __fsub_rn(xrs[i], ci)) +
+                           (__fsub_rn(yms[i], ci) + __fsub_rn(yps[i], ci))) +
+                          (__fsub_rn(zms[i], ci) + __fsub_rn(zps[i], ci));
+        const float c2 = ci * ci;
+        s0.add(c2);
+        sh.add(ci * (-kfac * lap + vs[i] * ci));
+        sr.add((px[i] * px[i] + py * py + pz * pz) * c2);
+        sv.add(vs[i] * c2);
+      }
+    }
+    if (!pp.end_iteration(err)) return false;
+    sj = slot_add<R>(sj, 1);
+  }
+  // fixed-order block reduction
+  double v4[4] = {s0.value(), sh.value(), sr.value(), sv.value()};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], off);
+  double* red = (double*)(smem + G::RED_OFF);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[(tid >> 5) * 4 + q] = v4[q];
+  __syncthreads();
+  if (tid < 4) {
+    double acc = 0.0;
+    for (int w = 0; w < G::THREADS / 32; ++w) acc += red[w * 4 + tid];
+    dst[tid] = acc;
+  }
+  __syncthreads();
+  return true;
+}
+
+}  // namespace tb
+}  // namespace fdtd
