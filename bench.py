@@ -39,6 +39,10 @@ LENGTH = 40.0
 SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 TOL = 1e-6
 SEED = 904939
+# dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
+# from an ncu capture of the current kernel, by (depth, z-chunk); a tuned
+# configuration without a capture reports traffic null
+TRAFFIC_256 = {(2, 16): 173_572_864}
 
 
 def dist_env():
@@ -62,14 +66,16 @@ def potentials(resident: bool, device):
 
 
 def run_step(fd, pots, seed, opts):
-    """Both sectors, three levels each.  Returns (site_updates, launches, stencil_ms, stencil_bytes, results)."""
-    updates, launches, st_ms, st_bytes = 0, 0, 0.0, 0.0
-    results = {}
+    """Both sectors, three levels each.  Returns a dict of totals: site
+    updates, kernel launches, and the stencil time / algorithmic bytes of the
+    finest level (the dominant kernel), plus per-level results."""
+    tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0,
+           "fine_launches": 0, "results": {}, "config": None}
     for name, mask in SECTORS:
         prev = None
         for lvl, n in enumerate(LEVELS):
             s = fd.Solver(fd.Lattice(n, LENGTH, fd.F32), opts)
-            s.set_profiling(True)
+            s.set_profiling(n == LEVELS[-1])
             s.set_potential(pots[lvl])
             if prev is None:
                 s.init_symmetric(seed, mask)
@@ -78,16 +84,129 @@ def run_step(fd, pots, seed, opts):
             steps, conv = s.evolve(2_000_000)
             o = s.last_check()
             st = s.stats()
-            updates += n**3 * steps
-            launches += st["launches"]
-            st_ms += st["stencil_ms"]
-            st_bytes += st["stencil_bytes"]
-            results[f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": steps, "converged": conv}
+            tot["updates"] += n**3 * steps
+            tot["launches"] += st["launches"]
+            if n == LEVELS[-1]:
+                tot["fine_ms"] += st["stencil_ms"]
+                tot["fine_bytes"] += st["stencil_bytes"]
+                tot["fine_updates"] += st["stencil_site_updates"]
+                tot["fine_launches"] += st["stencil_launches"]
+                tot["config"] = s.tuned_config()
+            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": steps, "converged": conv}
             if prev is not None:
                 prev.close()
             prev = s
         prev.close()
-    return updates, launches, st_ms, st_bytes, results
+    return tot
+
+
+def time_to_e0(fd, pots, seed, opts, dev):
+    """Wall time until |E - E_ref| < 1e-6 |E_ref| per sector, E_ref being the
+    plain FP64 256^3 solve converged to 1e-11 (relative): the FP32
+    multi-resolution path (coarse levels to a part in 10^6, the 256^3 level in
+    chunks of 100 steps until within 1e-6 of E_ref) against the plain FP64
+    form from a random start on the same GB300, both timed with CUDA events
+    (the checks against E_ref run on the host between chunks)."""
+    import torch
+
+    import workloads as wl
+
+    out = {}
+    v64 = torch.from_numpy(wl.coulomb_soft(LEVELS[-1], LENGTH)).to(dev)
+    ref_opts = fd.default_options(check_every=100, tol=1e-11, tol_relative=1)
+    chunk_opts = fd.default_options(check_every=100, tol=0.0)
+
+    def until_within(s, e_ref, limit=400_000):
+        steps, t_ms = 0, 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        while steps < limit:
+            e0.record()
+            s.evolve(100)
+            e1.record()
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            steps += 100
+            if abs(s.last_check()["energy"] - e_ref) < 1e-6 * abs(e_ref):
+                break
+        return steps, t_ms * 1e-3
+
+    for name, mask in SECTORS:
+        r = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F64), ref_opts)
+        r.set_potential(v64)
+        r.init_symmetric(seed + 17, mask)
+        ref_steps, _ = r.evolve(1_000_000)
+        e_ref = r.last_check()["energy"]
+        r.close()
+        # FP32 multi-resolution
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prev = None
+        for lvl, n in enumerate(LEVELS[:-1]):
+            s = fd.Solver(fd.Lattice(n, LENGTH, fd.F32), opts)
+            s.set_potential(pots[lvl])
+            if prev is None:
+                s.init_symmetric(seed, mask)
+            else:
+                s.upsample_from(prev)
+            s.evolve(2_000_000)
+            prev = s
+        fine = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F32), chunk_opts)
+        fine.set_potential(pots[-1])
+        fine.upsample_from(prev)
+        e1.record()
+        torch.cuda.synchronize()
+        coarse_s = e0.elapsed_time(e1) * 1e-3
+        mr_steps, mr_s = until_within(fine, e_ref)
+        e_mr = fine.last_check()["energy"]
+        # plain FP64 from a random start
+        p64 = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F64), chunk_opts)
+        e0.record()
+        p64.set_potential(v64)
+        p64.init_symmetric(seed, mask)
+        e1.record()
+        torch.cuda.synchronize()
+        p_steps, p_s = until_within(p64, e_ref)
+        p_s += e0.elapsed_time(e1) * 1e-3
+        e_p = p64.last_check()["energy"]
+        out[name] = {"E_ref_fp64": e_ref, "E_ref_steps": ref_steps,
+                     "fp32_multires_s": coarse_s + mr_s, "fp32_multires_fine_steps": mr_steps,
+                     "fp32_multires_rel_err": abs(e_mr - e_ref) / abs(e_ref),
+                     "fp64_plain_s": p_s, "fp64_plain_steps": p_steps,
+                     "fp64_plain_rel_err": abs(e_p - e_ref) / abs(e_ref),
+                     "speedup": p_s / (coarse_s + mr_s)}
+    return out
+
+
+def batched_run(fd, dev, seed):
+    """The 64-lattice batch (sizes 48..160, oscillator or soft Coulomb,
+    four symmetry sectors), FP32, one persistent launch to a part in 10^6."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+
+    lats = wl.config_batch()
+    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1, batched=1)
+    s = fd.Solver([fd.Lattice(l.n, l.length, fd.F32) for l in lats], opts)
+    for i, l in enumerate(lats):
+        s.set_potential(torch.from_numpy(l.potential().astype(np.float32)).to(dev), lat=i)
+        s.init_symmetric(seed, l.mask, lat=i)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    steps, conv = s.evolve(200_000)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    upd = 0
+    worst = 0
+    for i, l in enumerate(lats):
+        o = s.last_check(lat=i)
+        upd += l.n**3 * o["steps"]
+        worst = max(worst, o["steps"])
+    s.close()
+    return {"lattices": len(lats), "sites": int(sum(l.n**3 for l in lats)), "site_updates": upd, "ms": ms,
+            "gsite_per_s": upd / (ms * 1e-3) / 1e9, "max_steps_taken": worst, "all_converged": bool(conv),
+            "launches": 1}
 
 
 class Clocks:
@@ -140,11 +259,14 @@ def cpu_baseline(target_s: float = 12.0):
     a = LENGTH / n
     v = wl.coulomb_soft(n, LENGTH)
     psi = oracle.init_symmetric(n, SEED, SECTORS[0][1])
+    # per-step cost from two short runs (each call also pads/unpads the field)
     t0 = time.perf_counter()
     psi, _, _ = oracle.evolve(psi, v, a, a * a / 4, 2, 100, 0.0, False, SECTORS[0][1])
     t1 = time.perf_counter()
-    per = (t1 - t0) / 2
-    steps = max(2, min(200, int(target_s / max(per, 1e-3))))
+    psi, _, _ = oracle.evolve(psi, v, a, a * a / 4, 6, 100, 0.0, False, SECTORS[0][1])
+    t2 = time.perf_counter()
+    per = max((t2 - t1) - (t1 - t0), 1e-3) / 4
+    steps = max(4, min(2000, int(target_s / per)))
     t0 = time.perf_counter()
     oracle.evolve(psi, v, a, a * a / 4, steps, 100, 0.0, False, SECTORS[0][1])
     dt = time.perf_counter() - t0
@@ -189,7 +311,7 @@ def stencil_case(args):
 
     n = args.n
     prec = {"f32": fd.F32, "bf16": fd.BF16, "f64": fd.F64}[args.precision]
-    opts = fd.default_options(check_every=1 << 30, tol=0.0, temporal_depth=args.depth)
+    opts = fd.default_options(check_every=1 << 30, tol=0.0, temporal_depth=args.depth, zchunk=args.zc)
     s = fd.Solver(fd.Lattice(n, 16.0, prec), opts)
     v = torch.from_numpy(wl.harmonic(n, 16.0).astype(np.float32)).cuda()
     s.set_potential(v)
@@ -205,6 +327,7 @@ def stencil_case(args):
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     print(json.dumps({"case": "stencil", "n": n, "precision": args.precision, "depth": args.depth,
+                      "tuned": s.tuned_config(),
                       "launches": st["stencil_launches"], "ms_per_launch": ms, "gsite_per_s": upd,
                       "achieved_gbs": gbs, "hbm_frac": gbs / peak, "effective_frac_12B": upd * 12 / peak}))
 
@@ -216,10 +339,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--case", default="solve", choices=["solve", "stencil"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--depth", type=int, default=0)
+    ap.add_argument("--zc", type=int, default=0)
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f64"])
     args = ap.parse_args()
     if args.impl == "reference":
@@ -253,22 +378,25 @@ def main():
         torch.cuda.synchronize()
 
     clocks = Clocks(local)
-    tot_ms, tot_upd, tot_launch, st_ms, st_bytes = 0.0, 0, 0, 0.0, 0.0
-    results = None
+    tot_ms, tot_upd, tot_launch = 0.0, 0, 0
+    fine_ms, fine_bytes, fine_upd, fine_launches = 0.0, 0.0, 0, 0
+    tot = None
     barrier()
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        upd, nl, sms, sb, results = run_step(fd, pots_dev, seed, opts)
+        tot = run_step(fd, pots_dev, seed, opts)
         e1.record()
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
-        tot_upd += upd
-        tot_launch += nl
-        st_ms += sms
-        st_bytes += sb
+        tot_upd += tot["updates"]
+        tot_launch += tot["launches"]
+        fine_ms += tot["fine_ms"]
+        fine_bytes += tot["fine_bytes"]
+        fine_upd += tot["fine_updates"]
+        fine_launches += tot["fine_launches"]
     barrier()
     clk = clocks.stop()
 
@@ -279,10 +407,9 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        upd, _, _, _, _ = run_step(fd, pots_host, seed, opts)
+        e2e_upd += run_step(fd, pots_host, seed, opts)["updates"]
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_upd += upd
 
     t_local = torch.tensor([tot_ms, e2e_ms], dtype=torch.float64, device=dev)
     u_local = torch.tensor([float(tot_upd), float(e2e_upd)], dtype=torch.float64, device=dev)
@@ -291,6 +418,10 @@ def main():
         dist.all_reduce(u_local, op=dist.ReduceOp.SUM)
     ms_max, e2e_max = t_local.tolist()
     upd_all, e2e_upd_all = u_local.tolist()
+    extra = {}
+    if not args.no_extras:
+        extra["time_to_E0"] = time_to_e0(fd, pots_dev, seed, opts, dev)
+        extra["batched_64_lattices"] = batched_run(fd, dev, seed)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -305,7 +436,9 @@ def main():
     hbm = peaks.get("hbm_gbs")
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    achieved = st_bytes / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
+    achieved = fine_bytes / (fine_ms * 1e-3) / 1e9 if fine_ms > 0 else None
+    eff = fine_upd * 12.0 / (fine_ms * 1e-3) / 1e9 / hbm if fine_ms > 0 else None
+    depth, zc = tot["config"] if tot and tot["config"] else (None, None)
     h2d = sum(n**3 * 4 for n in LEVELS) * len(SECTORS)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -315,12 +448,16 @@ def main():
                    "length": LENGTH, "tol_rel": TOL, "check_every": 100, "precision": "fp32 stencil, fp64 sums",
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                     "kernel": "stencil (all levels)", "peak_kind": peak_note},
+                     "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc)),
+                     "kernel": f"k_step_tma (256^3 level, depth {depth}, z-chunk {zc})",
+                     "launches": fine_launches, "ms_per_launch": fine_ms / max(1, fine_launches),
+                     "bytes_per_launch": fine_bytes / max(1, fine_launches), "peak_kind": peak_note,
+                     "effective_frac": eff},
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 6 * 96},
         "gpu_launches": tot_launch,
         "clocks": clk,
-        "results": results,
+        "results": tot["results"] if tot else None,
+        "extra": extra,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -98,7 +98,9 @@ typedef struct {
                              (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
   int32_t autotune;       /* 1 (default): time every (depth, z-chunk) candidate on first use of a
                              lattice size and keep the fastest (results are identical for all) */
-  int32_t reserved[2];
+  int32_t zchunk;         /* z-planes per block of the TMA stencil when temporal_depth > 0;
+                             0 = heuristic */
+  int32_t reserved[1];
 } fdtd_options;
 
 typedef struct {

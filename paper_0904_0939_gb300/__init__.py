@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
                 ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("zchunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class Obs(ctypes.Structure):

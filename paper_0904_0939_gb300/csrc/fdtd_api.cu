@@ -115,6 +115,10 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "temporal_depth out of range";
     return FDTD_ERR_INVALID_ARG;
   }
+  if (o.zchunk < 0) {
+    err = "zchunk must be >= 0";
+    return FDTD_ERR_INVALID_ARG;
+  }
   if (o.autotune < 0 || o.autotune > 1) {
     err = "autotune must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
@@ -208,6 +212,14 @@ struct fdtd_context {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   int check_seq = 0;
+  // stencil launches not yet credited to the stats: a launch enqueued past
+  // the check at which its lattice converged runs as a no-op and is dropped
+  struct Pending {
+    int64_t t_start, updates;
+    double bytes;
+    long ev;  // index of its start event, or -1
+  };
+  std::vector<Pending> pending;
 };
 
 namespace {
@@ -230,27 +242,36 @@ int lat_check(fdtd_context* c, int lat) {
 }
 
 // ---- profiling of the stencil launches --------------------------------------
-void prof_begin(fdtd_context* c) {
-  if (!c->profiling) return;
+long prof_begin(fdtd_context* c) {
+  if (!c->profiling) return -1;
   while (c->ev.size() < c->ev_used + 2) {
     cudaEvent_t e;
     cudaEventCreate(&e);
     c->ev.push_back(e);
   }
   cudaEventRecord(c->ev[c->ev_used], c->st);
+  return (long)c->ev_used;
 }
 void prof_end(fdtd_context* c) {
   if (!c->profiling) return;
   cudaEventRecord(c->ev[c->ev_used + 1], c->st);
   c->ev_used += 2;
 }
-void prof_collect(fdtd_context* c) {  // call after a stream synchronisation
-  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+// Credit the pending stencil launches that started before step `cutoff`
+// (call after a stream synchronisation).
+void flush_pending(fdtd_context* c, int64_t cutoff) {
+  for (const auto& p : c->pending) {
+    if (p.t_start >= cutoff) continue;
+    c->stats.stencil_launches += 1;
+    c->stats.stencil_site_updates += p.updates;
+    c->stats.stencil_bytes += p.bytes;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) c->stats.stencil_ms += ms;
+    if (p.ev >= 0 && cudaEventElapsedTime(&ms, c->ev[p.ev], c->ev[p.ev + 1]) == cudaSuccess) c->stats.stencil_ms += ms;
   }
+  c->pending.clear();
   c->ev_used = 0;
 }
+void prof_collect(fdtd_context* c) { flush_pending(c, INT64_MAX); }
 
 // ---- typed dispatch helpers ---------------------------------------------------
 template <typename F>
@@ -280,7 +301,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
     L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
     L.tx = L.d.n > 64 ? 128 : 64;
-    L.zc = tma_zchunk(L.d.n, L.depth, L.tx);
+    L.zc = c->o.zchunk > 0 ? std::min(c->o.zchunk, L.d.n) : tma_zchunk(L.d.n, L.depth, L.tx);
     return;
   }
   int dev = 0;
@@ -344,15 +365,16 @@ void choose_config(fdtd_context* c, Lat& L) {
   g_tune[key] = std::make_tuple(bd, bt, bz);
 }
 
-// Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows).
-void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
+// Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows),
+// the first of them being step t0 of the current evolve.
+void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0 = 0) {
   const int prec = L.d.precision;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
   choose_config(c, L);
   const int depth = tma ? L.depth : 1;
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
-    prof_begin(c);
+    const long ev = prof_begin(c);
     if (prec == FDTD_F64) {
       launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
     } else if (prec == FDTD_F32) {
@@ -368,12 +390,11 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active) {
     }
     prof_end(c);
     c->stats.launches += 1;
-    c->stats.stencil_launches += 1;
-    c->stats.stencil_site_updates += (int64_t)L.n3 * k;
     // algorithmic bytes: psi read + psi write + V (FP64: A and cB) read once per launch
-    c->stats.stencil_bytes += (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0));
+    c->pending.push_back({t0, (int64_t)L.n3 * k, (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0)), ev});
     L.cur ^= 1;
     count -= k;
+    t0 += k;
   }
 }
 
@@ -417,7 +438,7 @@ int read_state(fdtd_context* c, Lat& L) {
   cudaMemcpyAsync(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("evolve: ") + cudaGetErrorString(e));
-  prof_collect(c);
+  flush_pending(c, L.host_state.converged ? L.host_state.step : INT64_MAX);
   if (err) return fail(c, FDTD_ERR_TIMEOUT, "evolve: a bounded device-side wait expired in the stencil kernel");
   return FDTD_OK;
 }
@@ -431,6 +452,8 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
   int check_id = 0;
   int groups = 2;
   bool done = false;
+  int prev_checks = 0;
+  double prev_delta = -1.0;
   while (!done) {
     for (int g = 0; g < groups && !done; ++g) {
       enqueue_check(c, L, check_id++, t);
@@ -439,7 +462,7 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
         break;
       }
       int64_t nst = std::min<int64_t>(ce, max_steps - t);
-      run_steps(c, L, nst, &L.state[0].active);
+      run_steps(c, L, nst, &L.state[0].active, t);
       t += nst;
     }
     int rc = cuda_check(c, "evolve launch");
@@ -447,7 +470,21 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
     rc = read_state(c, L);
     if (rc) return rc;
     if (!L.host_state.active) done = true;
-    groups = std::min(groups * 2, 64);
+    // segments to enqueue before the next look: predicted from the decay of
+    // |dE_b| per check, so that little work is queued past convergence
+    const LatState& hs = L.host_state;
+    int next = std::min(groups * 2, 32);
+    if (c->o.tol > 0.0 && hs.delta_e > 0.0 && prev_delta > 0.0 && hs.checks > prev_checks) {
+      const double rate = std::pow(hs.delta_e / prev_delta, 1.0 / (hs.checks - prev_checks));
+      const double thr = c->o.tol * (c->o.tol_relative ? std::fabs(hs.ebind) : 1.0);
+      if (rate < 0.999 && thr > 0.0) {
+        double m = std::log(thr / hs.delta_e) / std::log(rate);
+        next = (int)std::max(1.0, std::min(32.0, std::ceil(m)));
+      }
+    }
+    prev_checks = hs.checks;
+    prev_delta = hs.delta_e;
+    groups = next;
   }
   if (L.host_state.status == STATUS_NONFINITE)
     return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
@@ -543,13 +580,12 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
   cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
   int64_t steps = 0;
   int grid = 0;
-  prof_begin(c);
+  const long bev = prof_begin(c);
   int e = batched_launch(c->batch_ws, count, max_steps, c->o.check_every, c->o.tol, c->o.tol_relative,
                          c->o.reimpose_parity, depth, c->flags + 1, c->st, &steps, &grid);
   prof_end(c);
   if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
   c->stats.launches += 1;
-  c->stats.stencil_launches += 1;
   int rc = cuda_check(c, "evolve (batched)");
   if (rc) return rc;
   for (auto& L : c->lats) {
@@ -558,9 +594,13 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
       return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
     L.cur = L.host_state.cur;
     L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
-    c->stats.stencil_site_updates += (int64_t)L.n3 * L.last_steps;
-    c->stats.stencil_bytes += (double)L.n3 * 12.0 * ((L.last_steps + depth - 1) / depth);
+    c->pending.push_back({0, (int64_t)L.n3 * L.last_steps, (double)L.n3 * 12.0 * ((L.last_steps + depth - 1) / depth),
+                          -1});
   }
+  // the persistent launch is one timed unit: credit its time once
+  if (!c->pending.empty()) c->pending[0].ev = bev;
+  flush_pending(c, INT64_MAX);
+  c->stats.stencil_launches += 1 - (int64_t)c->lats.size();
   return FDTD_OK;
 }
 
