@@ -29,6 +29,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fdtd {
@@ -209,6 +211,83 @@ struct Pipe {
   __device__ __forceinline__ const float* box(int s) const { return ring + s * (G::SLOT_BYTES / 4); }
 };
 
+// Per-thread constants of a step item.
+template <int K, int TXT>
+struct StepCtx {
+  using G = Geo<K, TXT>;
+  float* lev;
+  float* out_col;
+  int n, z0, z1, ro, lo;
+  bool owner, inside, interior_col, interior_row, fix_l, fix_r;
+  int row;
+  float hd, om6c, cc;
+};
+
+// One z-step of a step item.  ROT (compile time, 0..2) names which of the
+// three window registers of each level holds the oldest plane, so the
+// windows rotate by renaming instead of moving.  After level l computes
+// its new plane into w[l][ROT], the window reads zm = w[(ROT+1)%3],
+// c = w[(ROT+2)%3], zp = w[ROT].
+template <int K, int TXT, int ROT>
+__device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int j, int sj,
+                                               float4 (&w)[K > 1 ? K - 1 : 1][3]) {
+  using G = Geo<K, TXT>;
+  constexpr int R = G::R;
+  constexpr int BW = G::BW, LW = G::LW;
+  constexpr int I0 = ROT, I1 = (ROT + 1) % 3, I2 = (ROT + 2) % 3;  // newest, oldest, middle after update
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // ---- level 1: plane j from the ring
+  {
+    const float* b0 = pp.box(sj);
+    const float* bm = pp.box(slot_add<R>(sj, -1));
+    const float* bp = pp.box(slot_add<R>(sj, 1));
+    const int p = j;
+    const bool need = x.owner && (x.row >= 1 && x.row < G::BH - 1) && (K > 1 || x.interior_col);
+    float4 c = x.owner ? f4(b0 + x.ro) : zero4;
+    float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+    if (x.fix_l) xl = b0[x.ro - 1];
+    if (x.fix_r) xr = b0[x.ro + 4];
+    if (need) {
+      float4 r = update4(c, xl, xr, f4(b0 + x.ro - BW), f4(b0 + x.ro + BW), f4(bm + x.ro), f4(bp + x.ro),
+                         f4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
+      if (!x.inside || p < 0 || p >= x.n) r = zero4;
+      if constexpr (K == 1) {
+        if (x.interior_row && x.inside && p >= x.z0 && p < x.z1)
+          *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = r;
+      } else {
+        *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = r;
+        w[0][I0] = r;
+      }
+    }
+  }
+  // ---- levels 2..K: plane j - l + 1 from level l-1
+#pragma unroll
+  for (int l = 2; l <= K; ++l) {
+    const int p = j - l + 1;
+    const bool need = x.owner && (x.row >= l && x.row < G::BH - l) && (l < K || x.interior_col);
+    const float* lp = x.lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
+    const float4 c = w[l - 2][I2];
+    float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+    if (x.fix_l) xl = lp[x.lo - 1];
+    if (x.fix_r) xr = lp[x.lo + 4];
+    if (need) {
+      const float4 v = f4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + x.ro);
+      float4 r = update4(c, xl, xr, f4(lp + x.lo - LW), f4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v, x.hd,
+                         x.om6c, x.cc);
+      if (!x.inside || p < 0 || p >= x.n) r = zero4;
+      if (l == K) {
+        if (x.interior_row && x.inside && p >= x.z0 && p < x.z1)
+          *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = r;
+      } else {
+        *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = r;
+        w[l - 1][I0] = r;
+      }
+    }
+  }
+}
+
 // K update steps on one tile item.  Returns false (in every thread) if a
 // bounded wait expired.
 template <int K, int TXT>
@@ -217,28 +296,36 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
                               float one_m6c, float cc, int32_t* err) {
   using G = Geo<K, TXT>;
   constexpr int R = G::R;
-  constexpr int C4 = G::C4, BW = G::BW, LW = G::LW;
+  constexpr int C4 = G::C4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const bool owner = tid < G::USED;
-  const int row = owner ? tid / C4 : 0, col = owner ? tid % C4 : 0;
+  StepCtx<K, TXT> x;
+  x.owner = tid < G::USED;
+  x.row = x.owner ? tid / C4 : 0;
+  const int col = x.owner ? tid % C4 : 0;
   const int xg = x0 - HX + 4 * col;
-  const int yg = y0 - K + row;
-  const bool inside = owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
-  const bool interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
-  const bool interior_row = owner && (row >= K) && (row < K + TY);
+  const int yg = y0 - K + x.row;
+  x.inside = x.owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
+  x.interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
+  x.interior_row = x.owner && (x.row >= K) && (x.row < K + TY);
   // x-neighbours come from the adjacent lanes; lanes 0 and 31 read them from
   // shared memory (at a row end the neighbouring row's value is taken, which
   // only ever reaches margin sites)
-  const bool fix_l = owner && lane == 0 && col > 0;
-  const bool fix_r = owner && lane == 31 && col < C4 - 1;
+  x.fix_l = x.owner && lane == 0 && col > 0;
+  x.fix_r = x.owner && lane == 31 && col < C4 - 1;
+  x.n = n;
+  x.z0 = z0;
+  x.z1 = z1;
+  x.lev = (float*)(smem + G::LEVEL_OFF);
+  x.ro = x.row * G::BW + 4 * col;
+  x.lo = x.row * G::LW + 4 + 4 * col;
+  x.out_col = out + (size_t)yg * n + xg;
+  x.hd = half_dtau;
+  x.om6c = one_m6c;
+  x.cc = cc;
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
-  float* lev = (float*)(smem + G::LEVEL_OFF);
-  const int ro = row * BW + 4 * col;
-  const int lo = row * LW + 4 + 4 * col;
-  float* const out_col = out + (size_t)yg * n + xg;
 
-  for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) lev[i] = 0.f;
+  for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) x.lev[i] = 0.f;
   Pipe<K, TXT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
@@ -248,76 +335,30 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   pp.err = err;
   pp.begin(j0, j1 + 1);
 
-  constexpr int NW = K > 1 ? K - 1 : 1;
-  float4 wm[NW], wc[NW], wp[NW];
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 w[K > 1 ? K - 1 : 1][3];
 #pragma unroll
-  for (int l = 0; l < NW; ++l) {
-    wm[l] = zero4;
-    wc[l] = zero4;
-    wp[l] = zero4;
-  }
+  for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l) w[l][0] = w[l][1] = w[l][2] = zero4;
 
   int sj = 1;  // slot of plane j (plane j0 sits in slot 1)
-  for (int j = j0; j <= j1; ++j) {
+  int j = j0;
+  auto one = [&](auto rot) -> bool {
+    constexpr int ROT = decltype(rot)::value;
     pp.advance(j, sj, j1 + 1);
-    // ---- level 1: plane j from the ring
-    {
-      const float* b0 = pp.box(sj);
-      const float* bm = pp.box(slot_add<R>(sj, -1));
-      const float* bp = pp.box(slot_add<R>(sj, 1));
-      const int p = j;
-      const bool need = owner && (row >= 1 && row < G::BH - 1) && (K > 1 || interior_col);
-      float4 c = owner ? f4(b0 + ro) : zero4;
-      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
-      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-      if (fix_l) xl = b0[ro - 1];
-      if (fix_r) xr = b0[ro + 4];
-      if (need) {
-        float4 r = update4(c, xl, xr, f4(b0 + ro - BW), f4(b0 + ro + BW), f4(bm + ro), f4(bp + ro),
-                           f4(b0 + G::PLANE + ro), half_dtau, one_m6c, cc);
-        if (!inside || p < 0 || p >= n) r = zero4;
-        if constexpr (K == 1) {
-          if (interior_row && inside && p >= z0 && p < z1)
-            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
-        } else {
-          *reinterpret_cast<float4*>(lev + (p & 1) * G::LPLANE + lo) = r;
-          wm[0] = wc[0];
-          wc[0] = wp[0];
-          wp[0] = r;
-        }
-      }
-    }
-    // ---- levels 2..K: plane j - l + 1 from level l-1
-#pragma unroll
-    for (int l = 2; l <= K; ++l) {
-      const int p = j - l + 1;
-      const bool need = owner && (row >= l && row < G::BH - l) && (l < K || interior_col);
-      const float* lp = lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
-      const float4 c = wc[l - 2];
-      float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
-      float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-      if (fix_l) xl = lp[lo - 1];
-      if (fix_r) xr = lp[lo + 4];
-      if (need) {
-        const float4 v = f4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + ro);
-        float4 r = update4(c, xl, xr, f4(lp + lo - LW), f4(lp + lo + LW), wm[l - 2], wp[l - 2], v, half_dtau,
-                           one_m6c, cc);
-        if (!inside || p < 0 || p >= n) r = zero4;
-        if (l == K) {
-          if (interior_row && inside && p >= z0 && p < z1)
-            *reinterpret_cast<float4*>(out_col + (size_t)p * n * n) = r;
-        } else {
-          *reinterpret_cast<float4*>(lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + lo) = r;
-          wm[l - 1] = wc[l - 1];
-          wc[l - 1] = wp[l - 1];
-          wp[l - 1] = r;
-        }
-      }
-    }
+    step_iteration<K, TXT, ROT>(x, pp, j, sj, w);
     if (!pp.end_iteration(err)) return false;
     sj = slot_add<R>(sj, 1);
+    ++j;
+    return true;
+  };
+  using R0 = std::integral_constant<int, 0>;
+  using R1 = std::integral_constant<int, 1>;
+  using R2 = std::integral_constant<int, 2>;
+  while (j + 2 <= j1) {
+    if (!one(R0{}) || !one(R1{}) || !one(R2{})) return false;
   }
+  if (j <= j1 && !one(R0{})) return false;
+  if (j <= j1 && !one(R1{})) return false;
   return true;
 }
 

@@ -66,10 +66,13 @@ def coulomb_paper(n: int, length: float) -> np.ndarray:
 
 
 def gaussian_bumps(n: int, length: float, centres, widths, amplitudes) -> np.ndarray:
-    z, y, x = grid(n, length)
+    """sum_k amp_k exp(-|r - c_k|^2 / (2 w_k^2)), built from per-axis factors."""
+    ax = axis(n, length)
     out = np.zeros((n, n, n))
     for (cx, cy, cz), w, amp in zip(centres, widths, amplitudes):
-        out += amp * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2.0 * w * w))
+        s = 2.0 * w * w
+        ex, ey, ez = (np.exp(-((ax - c) ** 2) / s) for c in (cx, cy, cz))
+        out += amp * ez[:, None, None] * (ey[:, None] * ex[None, :])[None, :, :]
     return out
 
 
@@ -95,10 +98,9 @@ def theta_basis(n: int, length: float, seed: int = BASE_SEED + 5, count: int = 1
     s_k in U[0.5, 1.5], and a seeded theta_k in U[-1, 1].
     Returns (G[count, N, N, N], theta[count])."""
     c, s, th = gaussian_params(seed, count, length / 4.0, (-1.0, 1.0), (0.5, 1.5))
-    z, y, x = grid(n, length)
     g = np.empty((count, n, n, n))
     for k in range(count):
-        g[k] = np.exp(-((x - c[k, 0]) ** 2 + (y - c[k, 1]) ** 2 + (z - c[k, 2]) ** 2) / (2.0 * s[k] ** 2))
+        g[k] = gaussian_bumps(n, length, c[k:k + 1], s[k:k + 1], [1.0])
     return g, th
 
 
@@ -109,8 +111,13 @@ def v_theta(n: int, length: float, theta, basis) -> np.ndarray:
 PHI = 0.5 * (1.0 + math.sqrt(5.0))
 
 
-def dodecahedron_vertices() -> np.ndarray:
-    """The 20 vertices of Sec. VII.E, Eq. dodecahedronpotential."""
+def dodecahedron_vertices(printed: bool = False) -> np.ndarray:
+    """20 vertices of the dodecahedron of Sec. VII.E, Eq. dodecahedronpotential:
+    (+-1/phi, +-1/phi, +-1/phi), (0, +-1/phi^2, +-1), (+-1/phi^2, +-1, 0) and a
+    third group that the paper prints as (+-1/phi^2, 0, +-1).  That printed
+    group does not close a regular solid; the regular dodecahedron the text
+    names needs the cyclic permutation (+-1, 0, +-1/phi^2), which is the
+    default here (printed=True gives the list as printed)."""
     p, q = 1.0 / PHI, 1.0 / (PHI * PHI)
     v = []
     for sx in (-1, 1):
@@ -121,17 +128,17 @@ def dodecahedron_vertices() -> np.ndarray:
         for s2 in (-1, 1):
             v.append((0.0, s1 * q, s2 * 1.0))
             v.append((s1 * q, s2 * 1.0, 0.0))
-            v.append((s1 * q, 0.0, s2 * 1.0))
+            v.append((s1 * q, 0.0, s2 * 1.0) if printed else (s2 * 1.0, 0.0, s1 * q))
     return np.array(v)
 
 
-def dodecahedron(n: int, depth: float = -100.0) -> np.ndarray:
+def dodecahedron(n: int, depth: float = -100.0, printed: bool = False) -> np.ndarray:
     """V = depth inside the convex hull of the 20 vertices, 0 outside.
     Lattice index 1 maps to the coordinate -1 and index N to +1 on every
     axis (Sec. VII.E)."""
     from scipy.spatial import ConvexHull
 
-    verts = dodecahedron_vertices()
+    verts = dodecahedron_vertices(printed)
     hull = ConvexHull(verts)
     u = -1.0 + 2.0 * (np.arange(1, n + 1, dtype=np.float64) - 1.0) / (n - 1.0)
     z, y, x = u[:, None, None], u[None, :, None], u[None, None, :]
