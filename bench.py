@@ -177,6 +177,70 @@ def time_to_e0(fd, pots, seed, opts, dev):
     return out
 
 
+def anisotropic_multires(fd, dev, seed):
+    """The 512^3, L = 16 anisotropic workload (oscillator + 32 Gaussians):
+    128^3 and 256^3 levels with BF16 storage (to 1e-4), the 512^3 level in
+    FP32 to a part in 10^6."""
+    import torch
+
+    import workloads as wl
+
+    L = 16.0
+    plan = ((128, fd.BF16, 1e-4), (256, fd.BF16, 1e-4), (512, fd.F32, TOL))
+    pots = [wl.anisotropic_device(n, L, dev, dtype=torch.float32) for n, _, _ in plan]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prev, upd, levels = None, 0, {}
+    for (n, prec, tol), v in zip(plan, pots):
+        s = fd.Solver(fd.Lattice(n, L, prec), fd.default_options(check_every=100, tol=tol, tol_relative=1))
+        s.set_potential(v)
+        if prev is None:
+            s.init_symmetric(seed, 0)
+        else:
+            s.upsample_from(prev)
+        steps, conv = s.evolve(2_000_000)
+        o = s.last_check()
+        upd += n**3 * steps
+        levels[f"{n}_{'bf16' if prec == fd.BF16 else 'f32'}"] = {"steps": steps, "E": o["energy"], "r2": o["r2"],
+                                                                  "converged": conv}
+        prev = s
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"levels": levels, "ms": ms, "site_updates": upd, "gsite_per_s": upd / (ms * 1e-3) / 1e9}
+
+
+def backward_run(fd, dev):
+    """Gradient of E w.r.t. V through 4000 unrolled FP32 steps on 128^3
+    (V_theta = r^2/2 + 16 Gaussians, L = 10), sqrt(T) checkpointing: forward,
+    segment recompute and adjoint, all inside fdtd_backward."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+
+    n, L, T = 128, 10.0, 4000
+    g, th = wl.config_theta(n, L)
+    v = torch.from_numpy(wl.v_theta(n, L, th, g).astype(np.float32)).to(dev)
+    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=100, tol=0.0, backward_steps=T))
+    s.set_potential(v)
+    s.set_psi(torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev))
+    out = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    s.backward(T, 1.0, 0.0, out=out)  # warm-up
+    s.set_psi(torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, obs = s.backward(T, 1.0, 0.0, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dtheta = torch.tensordot(torch.from_numpy(g).to(dev), out, dims=3).cpu().numpy()
+    s.close()
+    return {"n": n, "T": T, "checkpoint_every": int(np.ceil(np.sqrt(T))), "ms": ms,
+            "forward_equivalent_gsite_per_s": 3 * n**3 * T / (ms * 1e-3) / 1e9, "E_T": obs["energy"],
+            "dE_dtheta_first4": [float(x) for x in dtheta[:4]]}
+
+
 def batched_run(fd, dev, seed):
     """The 64-lattice batch (sizes 48..160, oscillator or soft Coulomb,
     four symmetry sectors), FP32, one persistent launch to a part in 10^6."""
@@ -297,6 +361,20 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def reduce_over_ranks(times, counts, device, world_size):
+    """Whole-job figures: the slowest rank's times (max) and the units all
+    ranks processed (sum).  With one rank the inputs come back unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    u = torch.tensor(counts, dtype=torch.float64, device=device)
+    if world_size > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.tolist(), u.tolist()
+
+
 def stencil_case(args):
     """Fixed number of update steps on one lattice (512^3, L = 16 by default,
     the size of the anisotropic-oscillator workload; the kernel's time does
@@ -411,17 +489,14 @@ def main():
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
 
-    t_local = torch.tensor([tot_ms, e2e_ms], dtype=torch.float64, device=dev)
-    u_local = torch.tensor([float(tot_upd), float(e2e_upd)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u_local, op=dist.ReduceOp.SUM)
-    ms_max, e2e_max = t_local.tolist()
-    upd_all, e2e_upd_all = u_local.tolist()
+    (ms_max, e2e_max), (upd_all, e2e_upd_all) = reduce_over_ranks([tot_ms, e2e_ms],
+                                                                  [float(tot_upd), float(e2e_upd)], dev, ws)
     extra = {}
     if not args.no_extras:
         extra["time_to_E0"] = time_to_e0(fd, pots_dev, seed, opts, dev)
         extra["batched_64_lattices"] = batched_run(fd, dev, seed)
+        extra["anisotropic_512_multires_bf16_coarse"] = anisotropic_multires(fd, dev, seed)
+        extra["backward_128_T4000"] = backward_run(fd, dev)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()

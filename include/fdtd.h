@@ -12,6 +12,8 @@
  *   Dirichlet boundary: psi = 0 outside the N^3 sites (Sec. III, Sec. V).
  * - Field layout across the ABI: dense N^3 arrays, x fastest, then y, then z
  *   (element (i, j, k) at offset ((k-1) N + (j-1)) N + (i-1)).  No padding.
+ * - Sizes: every field pointer must address n^3 elements of the stated
+ *   dtype; the library cannot check the length of a raw buffer.
  * - Memory: every pointer argument is paired with a mem_kind (FDTD_MEM_HOST
  *   or FDTD_MEM_DEVICE).  Inputs are borrowed for the duration of the call
  *   only: the library copies them into its own layout.  Outputs are written
@@ -100,7 +102,10 @@ typedef struct {
                              lattice size and keep the fastest (results are identical for all) */
   int32_t zchunk;         /* z-planes per block of the TMA stencil when temporal_depth > 0;
                              0 = heuristic */
-  int32_t reserved[1];
+  int32_t wait_limit_us;  /* bound on every device-side wait: 0 = default (0.2 s per pipeline
+                             wait, 2 s per grid barrier), > 0 = microseconds, < 0 = none (a wait
+                             that is not already complete expires at once; for testing the
+                             FDTD_ERR_TIMEOUT path) */
 } fdtd_options;
 
 typedef struct {

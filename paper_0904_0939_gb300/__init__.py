@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
                 ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("zchunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
 class Obs(ctypes.Structure):
@@ -219,9 +219,19 @@ class Solver:
 
         return torch.cuda.device(self.device)
 
+    def _sized(self, arr, lat: int, what: str):
+        """The C ABI reads or writes exactly n^3 elements: check the buffer."""
+        if not 0 <= lat < len(self.lattices):
+            raise FdtdError(ERR_INVALID_ARG, f"{what}: lattice index {lat} out of range")
+        n = self.lattices[lat].n
+        size = arr.numel() if hasattr(arr, "numel") else np.asarray(arr).size
+        if size != n**3:
+            raise FdtdError(ERR_SHAPE, f"{what}: expected {n}^3 = {n**3} values, got {size}")
+        return arr
+
     # --- calls ---------------------------------------------------------------
     def set_potential(self, v, lat: int = 0):
-        ptr, code, mem, keep = _buffer(v)
+        ptr, code, mem, keep = _buffer(self._sized(v, lat, "set_potential"))
         with self._ctx():
             _check(lib.fdtd_set_potential(self.handle, lat, ptr, code, mem), self.handle)
 
@@ -230,7 +240,7 @@ class Solver:
             _check(lib.fdtd_init_symmetric(self.handle, lat, seed, mask, dist), self.handle)
 
     def set_psi(self, psi, lat: int = 0, mask: int = 0):
-        ptr, code, mem, keep = _buffer(psi)
+        ptr, code, mem, keep = _buffer(self._sized(psi, lat, "set_psi"))
         with self._ctx():
             _check(lib.fdtd_set_psi(self.handle, lat, ptr, code, mem, mask), self.handle)
 
@@ -239,7 +249,7 @@ class Solver:
         n = self.lattices[lat].n
         if out is None:
             out = np.empty((n, n, n), dtype=dtype)
-        ptr, code, mem, keep = _buffer(out)
+        ptr, code, mem, keep = _buffer(self._sized(out, lat, "get_psi"))
         with self._ctx():
             _check(lib.fdtd_get_psi(self.handle, lat, ptr, code, mem), self.handle)
         return out
@@ -272,7 +282,7 @@ class Solver:
         n = self.lattices[lat].n
         if out is None:
             out = np.empty((n, n, n), dtype=np.float64)
-        ptr, code, mem, keep = _buffer(out)
+        ptr, code, mem, keep = _buffer(self._sized(out, lat, "backward"))
         o = Obs()
         with self._ctx():
             _check(lib.fdtd_backward(self.handle, lat, T, w_e, w_r, ptr, code, mem, ctypes.byref(o)), self.handle)

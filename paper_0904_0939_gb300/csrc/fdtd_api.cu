@@ -358,6 +358,14 @@ void choose_config(fdtd_context* c, Lat& L) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  int32_t err = 0;
+  cudaMemcpy(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (err) {  // the timed launches did no work: keep the heuristic, cache nothing
+    L.depth = auto_depth(n, L.d.precision);
+    L.tx = n > 64 ? 128 : 64;
+    L.zc = tma_zchunk(n, L.depth, L.tx);
+    return;
+  }
   L.depth = bd;
   L.tx = bt;
   L.zc = bz;
@@ -698,6 +706,8 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
   cv.base = c->ws;
   layout(d, count, c->o, cv, &c->lats, &c->staging, &c->flags, &c->batch_ws, &c->batch_bytes);
   cudaMemsetAsync(c->flags, 0, 256, c->st);
+  // flags[1]: error flag of the bounded device waits; flags[2]: their budget
+  cudaMemcpyAsync(c->flags + 2, &c->o.wait_limit_us, sizeof(int32_t), cudaMemcpyHostToDevice, c->st);
   for (auto& L : c->lats) {
     launch_state_reset(&L.state[0], 1, c->st);
     launch_state_reset(&L.state[1], 1, c->st);

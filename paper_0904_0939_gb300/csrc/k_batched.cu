@@ -83,11 +83,15 @@ __device__ bool grid_barrier(BatchRun* run, int32_t* err) {
       __threadfence();
       atomicAdd(&run->bar_gen, 1u);
     } else {
+      // budget: the word after the error flag (0 = 2 s, > 0 = microseconds,
+      // < 0 = none: give up unless the barrier has already opened)
+      const int us = *(volatile const int32_t*)(err + 1);
+      const unsigned long long budget = us == 0 ? 2000ull * 1000 * 1000 : (us > 0 ? 1000ull * us : 0ull);
       const unsigned long long t0 = tb::global_ns();
       unsigned it = 0;
       while (ld_acquire(&run->bar_gen) == gen) {
-        if ((++it & 63u) == 0) {
-          if (*(volatile int32_t*)err != 0 || tb::global_ns() - t0 > 2000ull * 1000 * 1000) {
+        if (us < 0 || (++it & 63u) == 0) {
+          if (us < 0 || *(volatile int32_t*)err != 0 || tb::global_ns() - t0 > budget) {
             atomicOr(err, 1);
             bad = 1;
             break;

@@ -11,6 +11,8 @@
 // row tile; only the tile's rim is loaded twice.  Loads for plane z+1 are
 // issued one iteration ahead.  HBM traffic is the ideal one-read-one-write
 // of psi plus one read of V per site.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -355,6 +357,75 @@ __global__ void k_scale_parity(const T* __restrict__ in, T* __restrict__ out, in
   }
 }
 
+// FP32, n % 4 == 0: one float4 per thread.  The mirror of an aligned float4
+// along x is the aligned float4 ending at n-1-4i, read reversed; each site
+// gets exactly the expression of k_scale_parity, so the two agree bit for bit.
+__global__ void k_scale_parity_f4(const float* __restrict__ in, float* __restrict__ out, int n, int mask,
+                                  const LatState* __restrict__ s, int check_id, int out_idx, LatState* sw) {
+  double scale = 1.0;
+  if (s) {
+    if (s->scale_seq != check_id) return;
+    scale = s->scale;
+  }
+  if (sw && blockIdx.x == 0 && threadIdx.x == 0) sw->cur = out_idx;
+  const int n4 = n >> 2;
+  const size_t total = (size_t)n * n * n4;
+  const int mx = mask & 3, my = (mask >> 2) & 3, mz = (mask >> 4) & 3;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x4 = (int)(i % n4), y = (int)((i / n4) % n), z = (int)(i / ((size_t)n4 * n));
+    int ys = y, zs = z;
+    double sgn = 1.0;
+    bool zero = false;
+    if (my) {
+      const int mm = n - 1 - y;
+      if (y > mm) {
+        ys = mm;
+        if (my == 2) sgn = -sgn;
+      } else if (y == mm && my == 2) {
+        zero = true;
+      }
+    }
+    if (mz) {
+      const int mm = n - 1 - z;
+      if (z > mm) {
+        zs = mm;
+        if (mz == 2) sgn = -sgn;
+      } else if (z == mm && mz == 2) {
+        zero = true;
+      }
+    }
+    const float* row = in + ((size_t)zs * n + ys) * n;
+    const float4 a = *reinterpret_cast<const float4*>(row + 4 * x4);
+    float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (mx) {
+      const float4 b = *reinterpret_cast<const float4*>(row + (n - 4 - 4 * x4));
+      mv[0] = b.w;  // mirror of site 4 x4 + 0 is n - 1 - 4 x4
+      mv[1] = b.z;
+      mv[2] = b.y;
+      mv[3] = b.x;
+    }
+    float o[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int x = 4 * x4 + c, mm = n - 1 - x;
+      double sg = sgn;
+      bool zc = zero;
+      float src = av[c];
+      if (mx) {
+        if (x > mm) {
+          src = mv[c];
+          if (mx == 2) sg = -sg;
+        } else if (x == mm && mx == 2) {
+          zc = true;
+        }
+      }
+      const double val = zc ? 0.0 : sg * ((double)src * scale);
+      o[c] = (float)val;
+    }
+    *reinterpret_cast<float4*>(out + 4 * i) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
 static int grid_for(size_t total, int threads) {
   size_t b = (total + threads - 1) / threads;
   if (b > 152 * 32) b = 152 * 32;
@@ -365,6 +436,12 @@ template <typename T>
 void launch_scale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
                          LatState* s_w, cudaStream_t st) {
   size_t total = (size_t)n * n * n;
+  if constexpr (std::is_same_v<T, float>) {
+    if (n % 4 == 0) {
+      k_scale_parity_f4<<<grid_for(total / 4, 256), 256, 0, st>>>(in, out, n, mask, s, check_id, out_idx, s_w);
+      return;
+    }
+  }
   k_scale_parity<T><<<grid_for(total, 256), 256, 0, st>>>(in, out, n, mask, s, check_id, out_idx, s_w);
 }
 template void launch_scale_parity<double>(const double*, double*, int, int, const LatState*, int, int, LatState*,

@@ -43,7 +43,7 @@ constexpr int kMaxBlocks = 4096;  // block partials of the sums for n <= 1024
 constexpr int kMaxN = 1024;
 constexpr int kMaxDevices = 128;
 
-// block partials, then (at kMaxBlocks * 4) the error word of the bounded waits
+// block partials, then (at kMaxBlocks * 4) the error word and the wait budget of the bounded waits
 __device__ __align__(256) double g_noalloc_partials[kMaxBlocks * 4 + 32];
 
 std::mutex g_mu;
@@ -138,8 +138,8 @@ extern "C" FDTD_API int fdtd_observables_noalloc(const void* psi, const void* v,
   const bool tma = dtype == FDTD_F32 && tma_supported(n, FDTD_F32) && tma_sums_blocks(n) <= kMaxBlocks &&
                    encode_field_map(&mpsi, (const float*)psi, n, bw, bh) == 0 &&
                    encode_field_map(&mv, (const float*)v, n, bw, bh) == 0;
-  int32_t* err = (int32_t*)(parts + (size_t)kMaxBlocks * 4);
-  cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+  int32_t* err = (int32_t*)(parts + (size_t)kMaxBlocks * 4);  // error flag, then the wait budget (0 = default)
+  cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st);
   if (tma)
     nb = launch_sums_tma(mpsi, mv, p, parts, nullptr, err, st);
   else if (dtype == FDTD_F64)

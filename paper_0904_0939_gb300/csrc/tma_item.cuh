@@ -87,21 +87,41 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// Wait budget in ns from the word after the error flag: 0 = default,
+// > 0 = that many microseconds, < 0 = none (a wait that is not already
+// complete gives up at once -- the mode the timeout test uses).
+__device__ __forceinline__ long long wait_budget_ns(const int32_t* err) {
+  const int us = *(volatile const int32_t*)(err + 1);
+  return us == 0 ? (long long)kWaitLimitNs : (us > 0 ? 1000ll * us : -1);
+}
 // Wait bounded in wall-clock time; gives up early once any block has
 // reported an expired wait in *err.  Returns false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, const int32_t* err) {
+  const long long budget = wait_budget_ns(err);
+  if (budget < 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (unsigned it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (*(volatile const int32_t*)err != 0) return false;
-      if (global_ns() - t0 > kWaitLimitNs) return false;
+      if (global_ns() - t0 > (unsigned long long)budget) return false;
     }
   }
 }

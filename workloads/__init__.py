@@ -93,6 +93,23 @@ def anisotropic(n: int, length: float, seed: int = BASE_SEED, count: int = 32) -
     return base + gaussian_bumps(n, length, c, w, amp)
 
 
+def anisotropic_device(n: int, length: float, device, seed: int = BASE_SEED, count: int = 32, dtype=None):
+    """anisotropic() evaluated on a torch device (same seeded parameters,
+    same per-axis construction); for lattices too large to build quickly in
+    numpy."""
+    import torch
+
+    dtype = dtype or torch.float64
+    ax = torch.as_tensor(axis(n, length), dtype=torch.float64, device=device)
+    v = 0.5 * (ax[None, None, :] ** 2 + 2.0 * ax[None, :, None] ** 2 + 3.0 * ax[:, None, None] ** 2)
+    c, w, amp = gaussian_params(seed, count, length / 4.0, (-0.5, 0.5), (0.5, 2.0))
+    for (cx, cy, cz), wk, ak in zip(c, w, amp):
+        s = 2.0 * wk * wk
+        ex, ey, ez = (torch.exp(-((ax - float(cc)) ** 2) / s) for cc in (cx, cy, cz))
+        v += float(ak) * ez[:, None, None] * (ey[:, None] * ex[None, :])[None, :, :]
+    return v.to(dtype)
+
+
 def theta_basis(n: int, length: float, seed: int = BASE_SEED + 5, count: int = 16):
     """Basis G_k(r) = exp(-|r - c_k|^2 / (2 s_k^2)), c_k in [-L/4, L/4]^3,
     s_k in U[0.5, 1.5], and a seeded theta_k in U[-1, 1].
