@@ -58,6 +58,9 @@ struct Lat {
   void* pool = nullptr;
   void* seg = nullptr;
   void* lam[2] = {nullptr, nullptr};
+  void* bw_u = nullptr;    // B lam of the split adjoint step
+  void* bw_raw = nullptr;  // step outputs before a check (and the segment's last output)
+  int bw_nraw = 0;
   double* gv = nullptr;
   double* scales = nullptr;
   // last evolve
@@ -179,6 +182,9 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
       L.seg = cv.take((size_t)L.bw_K * L.n3 * L.es);
       L.lam[0] = cv.take(L.n3 * L.es);
       L.lam[1] = cv.take(L.n3 * L.es);
+      L.bw_u = cv.take(L.n3 * L.es);
+      L.bw_nraw = (L.bw_K - 1) / o.check_every + 2;  // check steps inside a segment + its last step
+      L.bw_raw = cv.take((size_t)L.bw_nraw * L.n3 * L.es);
       L.gv = (double*)cv.take(L.n3 * 8);
       L.scales = (double*)cv.take((size_t)(L.bw_T / o.check_every + 2) * sizeof(double));
     }
@@ -986,37 +992,46 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
       launch_adjoint_seed<T_>((const T_*)L.psi[L.cur], L.v, scratch, w_e, w_r, (T_*)L.lam[0], L.gv, L.p, h->st);
   });
   h->stats.launches += 1;
-  void* tmp = L.psi[1 - L.cur];  // psi[cur] keeps psi_T
+  // psi[cur] keeps psi_T
   for (int64_t sgi = (T - 1) / K; sgi >= 0; --sgi) {
     const int64_t t0 = sgi * K, t1 = std::min<int64_t>(t0 + K, T);
+    // raw output of the step ending at t (t0 < t <= t1): the segment's last
+    // one and those of check steps go to bw_raw, the others are the seg fields
+    auto raw_slot = [&](int64_t t) -> void* {
+      if (t == t1) return field(L.bw_raw, 0);
+      return field(L.bw_raw, 1 + (t - (t0 / ce + 1) * ce) / ce);
+    };
+    auto raw_of = [&](int64_t t) -> void* { return (t == t1 || t % ce == 0) ? raw_slot(t) : field(L.seg, t - t0); };
     cudaMemcpyAsync(field(L.seg, 0), field(L.pool, sgi), fb, cudaMemcpyDeviceToDevice, h->st);
-    for (int64_t t = t0; t + 1 < t1; ++t) {
+    for (int64_t t = t0; t < t1; ++t) {
       with_type(L.d.precision, [&](auto* tag) {
         using T_ = std::remove_pointer_t<decltype(tag)>;
-        void* nxt = ((t + 1) % ce == 0) ? tmp : field(L.seg, t + 1 - t0);
+        void* nxt = raw_of(t + 1);
         if constexpr (std::is_same_v<T_, double>)
           launch_step_f64((const double*)field(L.seg, t - t0), (double*)nxt, L.coefA, L.coefCB, L.p, nullptr, h->st);
         else if constexpr (std::is_same_v<T_, float>)
           launch_step_f32<float>((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr,
                                  h->st);
         if constexpr (!std::is_same_v<T_, __nv_bfloat16>)
-          if ((t + 1) % ce == 0)
-            launch_scale_parity_from<T_>((const T_*)tmp, (T_*)field(L.seg, t + 1 - t0), L.d.n, mask,
+          if ((t + 1) % ce == 0 && t + 1 < t1)
+            launch_scale_parity_from<T_>((const T_*)nxt, (T_*)field(L.seg, t + 1 - t0), L.d.n, mask,
                                          L.scales + (t + 1) / ce, h->st);
       });
-      h->stats.launches += ((t + 1) % ce == 0) ? 2 : 1;
+      h->stats.launches += ((t + 1) % ce == 0 && t + 1 < t1) ? 2 : 1;
     }
     for (int64_t t = t1; t > t0; --t) {
       with_type(L.d.precision, [&](auto* tag) {
         using T_ = std::remove_pointer_t<decltype(tag)>;
         if constexpr (!std::is_same_v<T_, __nv_bfloat16>) {
-          launch_adjoint_step<T_>((const T_*)L.lam[lc], (T_*)L.lam[1 - lc], (const T_*)field(L.seg, t - 1 - t0), L.v,
-                                  L.coefA, L.coefCB, L.gv, L.p, h->st);
+          launch_adjoint_pointwise<T_>((const T_*)L.lam[lc], (const T_*)field(L.seg, t - 1 - t0), (const T_*)raw_of(t),
+                                       L.v, L.coefCB, (T_*)L.bw_u, L.gv, L.p, h->st);
+          launch_adjoint_stencil<T_>((const T_*)L.bw_u, (const T_*)L.lam[lc], (T_*)L.lam[1 - lc], L.v, L.coefA, L.p,
+                                     h->st);
           if ((t - 1) % ce == 0)
             launch_parity_adjoint_scale<T_>((T_*)L.lam[1 - lc], L.d.n, mask, L.scales + (t - 1) / ce, h->st);
         }
       });
-      h->stats.launches += ((t - 1) % ce == 0) ? 2 : 1;
+      h->stats.launches += ((t - 1) % ce == 0) ? 3 : 2;
       lc ^= 1;
     }
   }

@@ -7,11 +7,12 @@
 //   M^T lam = A lam + c [ Adj(B lam) - 6 B lam ].
 // Differentiating (1 + h) psi' = (1 - h) psi + c (Adj - 6) psi, h = dtau V/2,
 // at one site gives  d psi'(s)/d V(s) = -(dtau/2) B(s) (psi'(s) + psi(s)),
-// equivalently  dA/dV psi + dB/dV c (Adj - 6) psi  with dA/dV = -dtau B^2,
-// dB/dV = -(dtau/2) B^2; the kernels use the latter form on psi_t alone.
+// with psi' the step's raw output (before any check).
 //
-// These kernels are one thread per site with cached global loads: the
-// backward pass is a minor share of any run.
+// One adjoint step is split in two passes: a pointwise pass (u = B lam and
+// the g_V accumulation, one thread per site) and a z-marching stencil pass
+// over u (launch_adjoint_stencil in k_core.cu).  The seed and the transpose
+// of the checks are one thread per site.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -40,55 +41,37 @@ __device__ __forceinline__ double b_at(const void* v, const double* coefCB, size
   }
 }
 
+// Pointwise half of the adjoint step from psi_prev to psi_next (the raw
+// output of that step):  u = B lam  and
+//   g_V += lam * d psi_next / dV = lam * (-(dtau/2) B (psi_next + psi_prev)),
+// which is the derivative of (1 + h) psi' = (1 - h) psi + c Lap psi at one site.
 template <typename T>
-__global__ void k_adjoint_step(const T* __restrict__ lam, T* __restrict__ lam_out, const T* __restrict__ psi,
-                               const void* __restrict__ v, const double* __restrict__ coefA,
-                               const double* __restrict__ coefCB, double* __restrict__ gv, Params p) {
-  const int n = p.n;
-  const size_t total = (size_t)n * n * n;
+__global__ void k_adjoint_pointwise(const T* __restrict__ lam, const T* __restrict__ psi_prev,
+                                    const T* __restrict__ psi_next, const void* __restrict__ v,
+                                    const double* __restrict__ coefCB, T* __restrict__ u, double* __restrict__ gv,
+                                    Params p) {
+  const size_t total = (size_t)p.n * p.n * p.n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
-    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
-    double bl_sum = 0.0, psi_sum = 0.0;
-    for (int q = 0; q < 6; ++q) {
-      int xx = x + dx[q], yy = y + dy[q], zz = z + dz[q];
-      if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n) {
-        size_t j = site_index(xx, yy, zz, n);
-        bl_sum += b_at<T>(v, coefCB, j, p) * (double)Store<T>::to(lam[j]);
-        psi_sum += (double)Store<T>::to(psi[j]);
-      }
-    }
-    double l = (double)Store<T>::to(lam[i]);
-    double ps = (double)Store<T>::to(psi[i]);
-    double b = b_at<T>(v, coefCB, i, p);
-    double A;
-    if constexpr (sizeof(T) == 8) {
-      A = coefA[i];
-    } else {
-      CoefF k = coef_f32(((const float*)v)[i], p.half_dtau_f, p.one_m6c_f);
-      A = (double)k.b * ((double)k.alpha + 6.0 * (double)p.c_f);
-    }
-    double cc = (sizeof(T) == 8) ? p.c : (double)p.c_f;
-    double out = A * l + cc * (bl_sum - 6.0 * b * l);
-    double lap = psi_sum - 6.0 * ps;
-    gv[i] += l * (-p.dtau * b * b * ps - 0.5 * p.dtau * b * b * cc * lap);
+    const double b = b_at<T>(v, coefCB, i, p);
+    const double l = (double)Store<T>::to(lam[i]);
+    const double sum = (double)Store<T>::to(psi_next[i]) + (double)Store<T>::to(psi_prev[i]);
+    gv[i] += l * (-0.5 * p.dtau * b * sum);
     if constexpr (sizeof(T) == 8)
-      lam_out[i] = out;
+      u[i] = b * l;
     else
-      lam_out[i] = Store<T>::from((float)out);
+      u[i] = Store<T>::from((float)(b * l));
   }
 }
-
 template <typename T>
-void launch_adjoint_step(const T* lam_in, T* lam_out, const T* psi_prev, const void* v, const double* coefA,
-                         const double* coefCB, double* gv, const Params& p, cudaStream_t st) {
+void launch_adjoint_pointwise(const T* lam, const T* psi_prev, const T* psi_next, const void* v, const double* coefCB,
+                              T* u, double* gv, const Params& p, cudaStream_t st) {
   size_t total = (size_t)p.n * p.n * p.n;
-  k_adjoint_step<T><<<grid_1d(total), 256, 0, st>>>(lam_in, lam_out, psi_prev, v, coefA, coefCB, gv, p);
+  k_adjoint_pointwise<T><<<grid_1d(total), 256, 0, st>>>(lam, psi_prev, psi_next, v, coefCB, u, gv, p);
 }
-template void launch_adjoint_step<double>(const double*, double*, const double*, const void*, const double*,
-                                          const double*, double*, const Params&, cudaStream_t);
-template void launch_adjoint_step<float>(const float*, float*, const float*, const void*, const double*,
-                                         const double*, double*, const Params&, cudaStream_t);
+template void launch_adjoint_pointwise<double>(const double*, const double*, const double*, const void*, const double*,
+                                               double*, double*, const Params&, cudaStream_t);
+template void launch_adjoint_pointwise<float>(const float*, const float*, const float*, const void*, const double*,
+                                              float*, double*, const Params&, cudaStream_t);
 
 // Seed at T:  lam = w_e 2 (H psi - E psi) / S0 + w_r 2 (r^2 - <r^2>) psi / S0,
 // and the direct term gv = w_e psi^2 / S0 (E depends on V explicitly).

@@ -128,6 +128,43 @@ template void launch_step_f32<float>(const float*, float*, const float*, const P
 template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
                                              const int32_t*, cudaStream_t);
 
+// ------------------------------------------------------------------ adjoint stencil
+// lam_out = A lam + c (sum of the 6 neighbours of u - 6 u), u = B lam given;
+// the transpose of the update with the symmetric lattice Laplacian.
+template <typename T>
+__global__ void __launch_bounds__(TX* TY) k_adjoint_stencil(const T* __restrict__ u, const T* __restrict__ lam,
+                                                            T* __restrict__ lam_out, const void* __restrict__ v,
+                                                            const double* __restrict__ coefA, int n, int zc,
+                                                            float half_dtau, float one_m6c, float cc, double c64) {
+  using C = typename Store<T>::C;
+  __shared__ RowTile<C> tile;
+  zmarch<T>(u, n, zc, tile, [&](int x, int y, int z, bool act, C cu, C xm, C xp, C ym, C yp, C zm, C zp) {
+    if (!act) return;
+    size_t i = site_index(x, y, z, n);
+    if constexpr (sizeof(T) == 8) {
+      double s = nbr_sum(xm, xp, ym, yp, zm, zp);
+      lam_out[i] = __fma_rn(c64, __fma_rn(-6.0, cu, s), __dmul_rn(coefA[i], (double)lam[i]));
+    } else {
+      CoefF k = coef_f32(__ldg((const float*)v + i), half_dtau, one_m6c);
+      float A = k.b * (k.alpha + 6.0f * cc);
+      float s = nbr_sum(xm, xp, ym, yp, zm, zp);
+      lam_out[i] = Store<T>::from(__fmaf_rn(cc, __fmaf_rn(-6.0f, cu, s), A * Store<T>::to(lam[i])));
+    }
+  });
+}
+
+template <typename T>
+void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v, const double* coefA, const Params& p,
+                            cudaStream_t st) {
+  Tiling t = tiling_for(p.n, 1216);
+  k_adjoint_stencil<T><<<t.grid, dim3(TX, TY), 0, st>>>(u, lam, lam_out, v, coefA, p.n, t.zc, p.half_dtau_f,
+                                                         p.one_m6c_f, p.c_f, p.c);
+}
+template void launch_adjoint_stencil<double>(const double*, const double*, double*, const void*, const double*,
+                                             const Params&, cudaStream_t);
+template void launch_adjoint_stencil<float>(const float*, const float*, float*, const void*, const double*,
+                                            const Params&, cudaStream_t);
+
 // ------------------------------------------------------------------ sums
 __device__ __forceinline__ void block_sum4_store(double v0, double v1, double v2, double v3, double* dst) {
   __shared__ double red[TY][4];

@@ -113,9 +113,14 @@ void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, 
 void launch_state_reset(LatState* s, int mode, cudaStream_t st);
 
 // ---- adjoint (k_adjoint.cu) ---------------------------------------------------
+// Split adjoint step: u = B lam with the g_V accumulation (pointwise), then
+// lam_out = A lam + c (Adj u - 6 u) (z-marching stencil over u).
 template <typename T>
-void launch_adjoint_step(const T* lam_in, T* lam_out, const T* psi_prev, const void* v, const double* coefA,
-                         const double* coefCB, double* gv, const Params& p, cudaStream_t st);
+void launch_adjoint_pointwise(const T* lam, const T* psi_prev, const T* psi_next, const void* v, const double* coefCB,
+                              T* u, double* gv, const Params& p, cudaStream_t st);
+template <typename T>
+void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v, const double* coefA, const Params& p,
+                            cudaStream_t st);
 template <typename T>
 void launch_adjoint_seed(const T* psi, const void* v, const LatState* s, double w_e, double w_r, T* lam, double* gv,
                          const Params& p, cudaStream_t st);

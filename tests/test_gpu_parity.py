@@ -311,3 +311,24 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         s.close()
     for name in ("k1", "k2", "k3"):
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
+
+
+# ------------------------------------------------------------------ adjoint
+
+@pytest.mark.parametrize("n,mask,T,ce", [(8, 0, 40, 15), (12, wl.ODD_X, 57, 10), (9, wl.SYMMETRIC_ALL, 30, 7)])
+def test_backward_matches_oracle(fd, orc, n, mask, T, ce):
+    """dL/dV of L = E + 0.3 <r^2> after T steps (sqrt(T) checkpoints,
+    checks inside segments, symmetry projection) against the oracle's
+    full-trajectory adjoint: FP64 to 1e-10, FP32 to 1e-4 (max-norm relative)."""
+    L = 0.5 * n
+    a = L / n
+    v = wl.harmonic(n, L) + 0.1 * wl.grid(n, L)[2] ** 2
+    psi0 = orc.init_symmetric(n, 4, mask)
+    ref, obs = orc.backward(psi0, v, a, a * a / 4, T, ce, mask, 1.0, 0.3)
+    for prec, tol in ((fd.F64, 1e-10), (fd.F32, 1e-4)):
+        s = solver(fd, n, L, prec, check_every=ce, backward_steps=T)
+        s.set_potential(v)
+        s.set_psi(psi0, mask=mask)
+        g, o = s.backward(T, 1.0, 0.3)
+        assert rel_max(g, ref) <= tol, prec
+        assert o["energy"] == pytest.approx(obs["E"], rel=1e-12 if prec == fd.F64 else 1e-6)
