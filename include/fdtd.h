@@ -106,6 +106,8 @@ typedef struct {
                              wait, 2 s per grid barrier), > 0 = microseconds, < 0 = none (a wait
                              that is not already complete expires at once; for testing the
                              FDTD_ERR_TIMEOUT path) */
+  int32_t snapshots;      /* snapshot slots per lattice (Sec. III excited states); 0 = none */
+  int32_t reserved[3];
 } fdtd_options;
 
 typedef struct {
@@ -218,6 +220,25 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
 /* Stencil configuration in use for lattice `lat` (after autotuning, if on):
  * temporal depth (steps per launch) and z-planes per block. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
+
+/* Snapshots (Sec. III): full copies of psi kept in the workspace, in
+ * options.snapshots slots per lattice.  save: psi -> slot; load: slot -> psi
+ * (also recorded as the start of fdtd_backward; the symmetry mask is kept). */
+FDTD_API int fdtd_snapshot_save(fdtd_handle h, int lat, int slot);
+FDTD_API int fdtd_snapshot_load(fdtd_handle h, int lat, int slot);
+
+/* Projection of Sec. III: psi <- psi - phi <phi|psi> / <phi|phi> for each
+ * snapshot slot listed, one after another (Gram-Schmidt order), then
+ * renormalised to sum psi^2 a^3 = 1.  With psi a snapshot taken at tau_snap
+ * >> 1/(E2 - E1) and the slots holding the lower states, the result
+ * approximates the next excited state (fdtd_observables gives its energy).
+ * Sums in FP64 (FP64 lattices) or compensated FP32. */
+FDTD_API int fdtd_project_out(fdtd_handle h, int lat, const int* slots, int count);
+
+/* Linear combination as an initial condition (Sec. VI): psi <- sum_k
+ * weights[k] * slot_k, renormalised; the field becomes the start of
+ * fdtd_backward.  FDTD_ERR_NONFINITE if the combination vanishes. */
+FDTD_API int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double* weights, int count);
 
 /* Launch counters and (when profiling is on) summed stencil device time. */
 FDTD_API int fdtd_get_stats(fdtd_handle h, fdtd_stats* out);

@@ -20,6 +20,8 @@ Every function cites the passage of the paper it follows:
   upsample             Sec. VI / VII.G multi-resolution transfer (trilinear)
   adjoint_step, grad_v_accum, backward
                        adjoint of Eq. updateeq (gradients w.r.t. V)
+  project_out          Sec. III snapshot projection of lower states
+  combine              Sec. VI linear combination of states as a start
 """
 from __future__ import annotations
 
@@ -224,6 +226,22 @@ def grad_v_accum(psi, lam_next, v, a, dtau, mass=1.0, gv=None):
     _load().oracle_grad_v_accum(n, a, dtau, mass, _ptr(_dense(v)), _ptr(pad(psi)), _ptr(pad(lam_next)),
                                 _ptr(g))
     return g
+
+
+def project_out(psi, states, a):
+    """Sec. III: |psi> - |phi><phi|psi> / <phi|phi> for each phi in `states`,
+    one after another, then scaled to sum psi^2 a^3 = 1."""
+    out = np.array(psi, dtype=np.float64, copy=True)
+    for phi in states:
+        phi = np.asarray(phi, dtype=np.float64)
+        out = out - phi * (np.sum(phi * out) / np.sum(phi * phi))
+    return out / np.sqrt(np.sum(out * out) * a**3)
+
+
+def combine(states, weights, a):
+    """Sec. VI: sum_k weights[k] states[k], scaled to sum psi^2 a^3 = 1."""
+    out = sum(w * np.asarray(s, dtype=np.float64) for s, w in zip(states, weights))
+    return out / np.sqrt(np.sum(out * out) * a**3)
 
 
 def backward(psi0, v, a, dtau, T, check_every=100, mask=0, w_e=1.0, w_r=0.0, mass=1.0):

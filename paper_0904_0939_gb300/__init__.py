@@ -54,7 +54,8 @@ class Options(ctypes.Structure):
                 ("temporal_depth", ctypes.c_int32), ("backward_steps", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
+                ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("snapshots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Obs(ctypes.Structure):
@@ -76,7 +77,8 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
-            "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config"]
+            "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
+            "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine"]
 
 
 def _load():
@@ -104,6 +106,10 @@ def _load():
         "fdtd_reset_stats": [vp],
         "fdtd_set_profiling": [vp, i32],
         "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
+        "fdtd_snapshot_save": [vp, i32, i32],
+        "fdtd_snapshot_load": [vp, i32, i32],
+        "fdtd_project_out": [vp, i32, P(ctypes.c_int), i32],
+        "fdtd_combine": [vp, i32, P(ctypes.c_int), P(ctypes.c_double), i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -287,6 +293,28 @@ class Solver:
         with self._ctx():
             _check(lib.fdtd_backward(self.handle, lat, T, w_e, w_r, ptr, code, mem, ctypes.byref(o)), self.handle)
         return out, o.to_dict()
+
+    # --- snapshots (Sec. III) and combinations (Sec. VI) -----------------------
+    def snapshot_save(self, slot: int, lat: int = 0):
+        with self._ctx():
+            _check(lib.fdtd_snapshot_save(self.handle, lat, slot), self.handle)
+
+    def snapshot_load(self, slot: int, lat: int = 0):
+        with self._ctx():
+            _check(lib.fdtd_snapshot_load(self.handle, lat, slot), self.handle)
+
+    def project_out(self, slots, lat: int = 0):
+        """psi <- psi minus its components along the snapshot slots, renormalised."""
+        arr = (ctypes.c_int * max(1, len(slots)))(*slots)
+        with self._ctx():
+            _check(lib.fdtd_project_out(self.handle, lat, arr, len(slots)), self.handle)
+
+    def combine(self, slots, weights, lat: int = 0):
+        """psi <- sum_k weights[k] * slot_k, renormalised."""
+        a = (ctypes.c_int * len(slots))(*slots)
+        w = (ctypes.c_double * len(weights))(*weights)
+        with self._ctx():
+            _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
 
     def tuned_config(self, lat: int = 0) -> tuple[int, int]:
         """(temporal depth, z-planes per block) the stencil uses for lattice `lat`."""

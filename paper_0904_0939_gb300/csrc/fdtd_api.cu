@@ -63,6 +63,11 @@ struct Lat {
   int bw_nraw = 0;
   double* gv = nullptr;
   double* scales = nullptr;
+  // snapshots (Sec. III) and the scratch of the snapshot algebra
+  void* snaps = nullptr;
+  int nsnap = 0;
+  double* dot_parts = nullptr;
+  double* coef = nullptr;
   // last evolve
   int64_t last_steps = 0;
   LatState host_state{};
@@ -130,6 +135,10 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "stencil_kernel must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
+  if (o.snapshots < 0 || o.snapshots > 1024) {
+    err = "snapshots must be in [0, 1024]";
+    return FDTD_ERR_INVALID_ARG;
+  }
   if (o.backward_steps < 0 || !std::isfinite(o.tol)) {
     err = "backward_steps must be >= 0 and tol finite";
     return FDTD_ERR_INVALID_ARG;
@@ -188,6 +197,12 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
       L.gv = (double*)cv.take(L.n3 * 8);
       L.scales = (double*)cv.take((size_t)(L.bw_T / o.check_every + 2) * sizeof(double));
     }
+    if (o.snapshots > 0) {
+      L.nsnap = o.snapshots;
+      L.snaps = cv.take((size_t)L.nsnap * L.n3 * L.es);
+    }
+    L.dot_parts = (double*)cv.take((size_t)152 * 8 * 2 * sizeof(double));
+    L.coef = (double*)cv.take(8 * sizeof(double));
     if (lats) lats->push_back(L);
   }
   *batch_bytes = o.batched ? batched_workspace_bytes(d, count) : 0;
@@ -1044,6 +1059,101 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
     obs->steps = T;
   }
   return export_field(h, L.gv, FDTD_F64, gv_out, dtype, mem_kind, L.n3);
+}
+
+namespace {
+
+void* snap_field(Lat& L, int slot) { return (char*)L.snaps + (size_t)slot * L.n3 * L.es; }
+
+int snap_check(fdtd_context* h, int lat, int slot) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (slot < 0 || slot >= h->lats[lat].nsnap)
+    return fail(h, FDTD_ERR_INVALID_ARG, "snapshot slot out of range (options.snapshots)");
+  return FDTD_OK;
+}
+
+// psi[cur] <- s psi[cur] with sum psi^2 a^3 = 1 (no symmetry pass).
+int renormalise(fdtd_context* c, Lat& L) {
+  const int id = 3000000 + (c->check_seq++);
+  int np = launch_sums_any(c, L, L.psi[L.cur], nullptr);
+  launch_state_reset(&L.state[1], 0, c->st);
+  launch_finalize(&L.state[1], L.partials, np, id, 0, L.p, L.d.v_inf, 0.0, 0, 0, c->st);
+  scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], 0, &L.state[1], id, 1 - L.cur, nullptr);
+  c->stats.launches += 2;
+  LatState s;
+  cudaMemcpyAsync(&s, &L.state[1], sizeof(LatState), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("renormalise: ") + cudaGetErrorString(e));
+  if (s.status == STATUS_NONFINITE) return fail(c, FDTD_ERR_NONFINITE, "the field vanished or is not finite");
+  L.cur ^= 1;
+  return cuda_check(c, "renormalise");
+}
+
+}  // namespace
+
+int fdtd_snapshot_save(fdtd_handle h, int lat, int slot) {
+  int rc = snap_check(h, lat, slot);
+  if (rc) return rc;
+  Lat& L = h->lats[lat];
+  if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "snapshot_save: no wavefunction yet");
+  cudaMemcpyAsync(snap_field(L, slot), L.psi[L.cur], L.n3 * L.es, cudaMemcpyDeviceToDevice, h->st);
+  return cuda_check(h, "snapshot_save");
+}
+
+int fdtd_snapshot_load(fdtd_handle h, int lat, int slot) {
+  int rc = snap_check(h, lat, slot);
+  if (rc) return rc;
+  Lat& L = h->lats[lat];
+  cudaMemcpyAsync(L.psi[L.cur], snap_field(L, slot), L.n3 * L.es, cudaMemcpyDeviceToDevice, h->st);
+  L.has_psi = true;
+  record_start(h, L);
+  return cuda_check(h, "snapshot_load");
+}
+
+int fdtd_project_out(fdtd_handle h, int lat, const int* slots, int count) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (count < 0 || (count > 0 && !slots)) return fail(h, FDTD_ERR_INVALID_ARG, "project_out: bad slot list");
+  Lat& L = h->lats[lat];
+  if (!L.has_psi || !L.has_v) return fail(h, FDTD_ERR_STATE, "project_out: set_potential and a wavefunction first");
+  for (int k = 0; k < count; ++k)
+    if ((rc = snap_check(h, lat, slots[k]))) return rc;
+  for (int k = 0; k < count; ++k) {
+    with_type(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      const T* phi = (const T*)snap_field(L, slots[k]);
+      int np = launch_dot2<T>(phi, (const T*)L.psi[L.cur], L.n3, L.dot_parts, h->st);
+      launch_ratio(L.dot_parts, np, L.coef, h->st);
+      launch_axpy<T>((T*)L.psi[L.cur], phi, L.coef, -1.0, 0.0, L.n3, h->st);
+    });
+    h->stats.launches += 3;
+  }
+  return renormalise(h, L);
+}
+
+int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double* weights, int count) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (count < 1 || !slots || !weights) return fail(h, FDTD_ERR_INVALID_ARG, "combine: bad slot or weight list");
+  Lat& L = h->lats[lat];
+  if (!L.has_v) return fail(h, FDTD_ERR_STATE, "combine: set_potential first");
+  for (int k = 0; k < count; ++k) {
+    if ((rc = snap_check(h, lat, slots[k]))) return rc;
+    if (!std::isfinite(weights[k])) return fail(h, FDTD_ERR_INVALID_ARG, "combine: weights must be finite");
+  }
+  cudaMemsetAsync(L.psi[L.cur], 0, L.n3 * L.es, h->st);
+  for (int k = 0; k < count; ++k) {
+    with_type(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      launch_axpy<T>((T*)L.psi[L.cur], (const T*)snap_field(L, slots[k]), nullptr, 0.0, weights[k], L.n3, h->st);
+    });
+    h->stats.launches += 1;
+  }
+  L.has_psi = true;
+  if ((rc = renormalise(h, L))) return rc;
+  record_start(h, L);
+  return FDTD_OK;
 }
 
 int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {

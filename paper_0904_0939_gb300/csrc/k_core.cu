@@ -11,6 +11,7 @@
 // row tile; only the tile's rim is loaded twice.  Loads for plane z+1 are
 // issued one iteration ahead.  HBM traffic is the ideal one-read-one-write
 // of psi plus one read of V per site.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -575,6 +576,92 @@ INST_UP(float, __nv_bfloat16)
 INST_UP(__nv_bfloat16, double)
 INST_UP(__nv_bfloat16, float)
 INST_UP(__nv_bfloat16, __nv_bfloat16)
+
+// ------------------------------------------------------------------ snapshot algebra
+constexpr int kDotBlocks = 152 * 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot2(const T* __restrict__ phi, const T* __restrict__ psi, size_t count,
+                                              double* __restrict__ partials) {
+  double a = 0.0, b = 0.0;
+  if constexpr (sizeof(T) == 8) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+      const double f = phi[i];
+      a += f * (double)psi[i];
+      b += f * f;
+    }
+  } else {
+    Kahan ka, kb;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+      const float f = Store<T>::to(phi[i]);
+      ka.add(f * Store<T>::to(psi[i]));
+      kb.add(f * f);
+    }
+    a = ka.value();
+    b = kb.value();
+  }
+  __shared__ double red[8][2];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = a;
+    red[threadIdx.x >> 5][1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+    partials[2 * blockIdx.x + threadIdx.x] = s;
+  }
+}
+template <typename T>
+int launch_dot2(const T* phi, const T* psi, size_t count, double* partials, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>(kDotBlocks, (count + 255) / 256);
+  k_dot2<T><<<blocks, 256, 0, st>>>(phi, psi, count, partials);
+  return blocks;
+}
+template int launch_dot2<double>(const double*, const double*, size_t, double*, cudaStream_t);
+template int launch_dot2<float>(const float*, const float*, size_t, double*, cudaStream_t);
+template int launch_dot2<__nv_bfloat16>(const __nv_bfloat16*, const __nv_bfloat16*, size_t, double*, cudaStream_t);
+
+// coef[0] = <phi|psi> / <phi|phi> (0 for a vanishing phi), fixed-order sum.
+__global__ void k_ratio(const double* __restrict__ partials, int np, double* coef) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < np; ++i) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  coef[0] = b > 0.0 ? a / b : 0.0;
+}
+void launch_ratio(const double* partials, int nparts, double* coef, cudaStream_t st) {
+  k_ratio<<<1, 32, 0, st>>>(partials, nparts, coef);
+}
+
+template <typename T>
+__global__ void k_axpy(T* __restrict__ psi, const T* __restrict__ phi, const double* __restrict__ coef, double sign,
+                       double alpha, size_t count) {
+  const double w = coef ? sign * coef[0] : alpha;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const double val = (double)Store<T>::to(psi[i]) + w * (double)Store<T>::to(phi[i]);
+    if constexpr (sizeof(T) == 8)
+      psi[i] = val;
+    else
+      psi[i] = Store<T>::from((float)val);
+  }
+}
+template <typename T>
+void launch_axpy(T* psi, const T* phi, const double* coef, double sign, double alpha, size_t count, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>(152 * 32, (count + 255) / 256);
+  k_axpy<T><<<blocks, 256, 0, st>>>(psi, phi, coef, sign, alpha, count);
+}
+template void launch_axpy<double>(double*, const double*, const double*, double, double, size_t, cudaStream_t);
+template void launch_axpy<float>(float*, const float*, const double*, double, double, size_t, cudaStream_t);
+template void launch_axpy<__nv_bfloat16>(__nv_bfloat16*, const __nv_bfloat16*, const double*, double, double, size_t,
+                                         cudaStream_t);
 
 // ------------------------------------------------------------------ conversions
 template <typename Ti, typename To>

@@ -112,6 +112,15 @@ void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, 
 
 void launch_state_reset(LatState* s, int mode, cudaStream_t st);
 
+// Snapshot algebra (Sec. III / Sec. VI): block partials of <phi|psi> and
+// <phi|phi> (returns the block count), the ratio on the device, and
+// psi += (sign * coef[0] or alpha) * phi.
+template <typename T>
+int launch_dot2(const T* phi, const T* psi, size_t count, double* partials, cudaStream_t st);
+void launch_ratio(const double* partials, int nparts, double* coef, cudaStream_t st);
+template <typename T>
+void launch_axpy(T* psi, const T* phi, const double* coef, double sign, double alpha, size_t count, cudaStream_t st);
+
 // ---- adjoint (k_adjoint.cu) ---------------------------------------------------
 // Split adjoint step: u = B lam with the g_V accumulation (pointwise), then
 // lam_out = A lam + c (Adj u - 6 u) (z-marching stencil over u).

@@ -188,3 +188,24 @@ def test_paper_antisymmetric_z_coulomb_256(fd):
     steps, conv = s.evolve(400_000)
     assert conv
     assert s.last_check()["binding_energy"] == pytest.approx(g["E1"], abs=2e-4)
+
+
+def test_paper_antisymmetric_z_second_state_by_projection(fd):
+    """Sec. VII.F: in the A_z run on 256^3, a = 0.2, dtau = 0.01, the next
+    state antisymmetric about z follows from a snapshot with the first one
+    projected out (Sec. III): E2 = -0.055360.  FP64, so that the projected
+    part (~1e-6 of the snapshot) keeps its precision."""
+    g = paper("coulomb_antisym_z_256")
+    n, a = g["n"], g["a"]
+    lat = fd.Lattice(n, n * a, fd.F64, dtau=g["dtau"], v_inf=1.0 / a)
+    s = fd.Solver(lat, fd.default_options(check_every=100, tol=0.0, snapshots=2))
+    s.set_potential(wl.coulomb_paper(n, n * a))
+    s.init_symmetric(5, wl.ODD_Z)
+    s.evolve(15000)               # tau = 150: the n = 4 states have decayed
+    s.snapshot_save(0)
+    s.evolve(10000)               # tau = 250: the 2p_z state
+    s.snapshot_save(1)
+    s.snapshot_load(0)
+    s.project_out([1])
+    e2 = s.observables()["binding_energy"]
+    assert e2 == pytest.approx(g["E2"], abs=5e-4)

@@ -332,3 +332,33 @@ def test_backward_matches_oracle(fd, orc, n, mask, T, ce):
         g, o = s.backward(T, 1.0, 0.3)
         assert rel_max(g, ref) <= tol, prec
         assert o["energy"] == pytest.approx(obs["E"], rel=1e-12 if prec == fd.F64 else 1e-6)
+
+
+# ------------------------------------------------------------------ snapshots
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
+def test_snapshot_projection_matches_oracle(fd, orc, prec, tol):
+    """Sec. III projection on the GPU (save, evolve, load, project) against
+    the oracle's definition on the same fields, FP64 to 1e-9 (the projected
+    part is ~1e-3 of the snapshot, so rounding is amplified), FP32 to 2e-3;
+    and the Sec. VI combination."""
+    n, L = 16, 8.0
+    a = L / n
+    dtau = a * a / 4
+    v = wl.harmonic(n, L)
+    s = solver(fd, n, L, prec, snapshots=2, tol=0.0)
+    s.set_potential(v)
+    s.init_symmetric(9, 0)
+    s.evolve(int(6.0 / dtau) // 100 * 100)
+    s.snapshot_save(0)
+    snap = s.get_psi()
+    s.evolve(20000)  # tau = 1250: the ground state
+    s.snapshot_save(1)
+    ground = s.get_psi()
+    s.snapshot_load(0)
+    s.project_out([1])
+    want = orc.project_out(snap, [ground], a)
+    assert rel_max(s.get_psi(), want) <= tol
+    assert s.observables()["energy"] == pytest.approx(orc.observables(want, v, a)["E"], rel=tol)
+    s.combine([0, 1], [0.5, -2.0])
+    assert rel_max(s.get_psi(), orc.combine([snap, ground], [0.5, -2.0], a)) <= (1e-12 if prec == 0 else 1e-5)

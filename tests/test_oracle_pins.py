@@ -362,3 +362,28 @@ def test_hellmann_feynman_at_convergence(orc):
         adj = float(np.sum(gv * g_basis[k]))
         hf = float(np.sum(g_basis[k] * psi**2) / np.sum(psi**2))
         assert adj == pytest.approx(hf, rel=0.02, abs=2e-3)
+
+
+# ----------------------------------------------------------------- snapshot projection
+
+def test_projection_of_a_snapshot_gives_the_first_excited_level(orc):
+    """Sec. III: a snapshot taken at tau_snap >> 1/(E2 - E1), with the
+    converged ground state projected out, has the energy of the first
+    excited level -- here the isotropic oscillator's p triplet, whose energy
+    the A_x sector (Sec. IV) gives independently."""
+    n, L = 16, 8.0
+    a = L / n
+    dtau = a * a / 4
+    v = wl.harmonic(n, L)
+    snap, _, _ = orc.evolve(orc.init_random(n, 9), v, a, dtau, int(6.0 / dtau), 100)
+    ground, rec0, _ = orc.evolve(snap, v, a, dtau, 200000, 100, 1e-14)
+    e1 = orc.observables(orc.project_out(snap, [ground], a), v, a)["E"]
+    _, rec_odd, _ = orc.evolve(orc.init_symmetric(n, 9, wl.ODD_X), v, a, dtau, 200000, 100, 1e-14, False, wl.ODD_X)
+    assert e1 == pytest.approx(rec_odd["E"], rel=1e-4)
+    assert e1 > rec0["E"] + 0.9
+    p = orc.project_out(snap, [ground], a)
+    assert abs(np.sum(p * ground)) < 1e-10 * np.sqrt(np.sum(p * p) * np.sum(ground * ground))
+    assert np.sum(p * p) * a**3 == pytest.approx(1.0, rel=1e-14)
+    c = orc.combine([ground, p], [2.0, -1.0], a)
+    assert np.sum(c * c) * a**3 == pytest.approx(1.0, rel=1e-14)
+    assert np.sum(c * ground) / np.sum(c * p) * np.sum(p * p) / np.sum(ground * ground) == pytest.approx(-2.0, rel=1e-10)
