@@ -42,7 +42,7 @@ SEED = 904939
 # dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
 # from an ncu capture of the current kernel, by (depth, z-chunk); a tuned
 # configuration without a capture reports traffic null
-TRAFFIC_256 = {(2, 16): 173_572_864}
+TRAFFIC_256 = {(3, 64): 181_200_384}
 
 
 def dist_env():
@@ -69,11 +69,15 @@ def run_step(fd, pots, seed, opts):
     """Both sectors, three levels each.  Returns a dict of totals: site
     updates, kernel launches, and the stencil time / algorithmic bytes of the
     finest level (the dominant kernel), plus per-level results."""
+    import torch
+
     tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0,
-           "fine_launches": 0, "results": {}, "config": None}
+           "fine_launches": 0, "results": {}, "config": None, "level_ms": {}}
     for name, mask in SECTORS:
         prev = None
         for lvl, n in enumerate(LEVELS):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
             s = fd.Solver(fd.Lattice(n, LENGTH, fd.F32), opts)
             s.set_profiling(n == LEVELS[-1])
             s.set_potential(pots[lvl])
@@ -92,7 +96,11 @@ def run_step(fd, pots, seed, opts):
                 tot["fine_updates"] += st["stencil_site_updates"]
                 tot["fine_launches"] += st["stencil_launches"]
                 tot["config"] = s.tuned_config()
-            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": steps, "converged": conv}
+            ev1.record()
+            ev1.synchronize()
+            tot["level_ms"][f"{name}_{n}"] = ev0.elapsed_time(ev1)
+            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": steps, "converged": conv,
+                                             "ms": ev0.elapsed_time(ev1)}
             if prev is not None:
                 prev.close()
             prev = s
@@ -524,7 +532,8 @@ def main():
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc)),
-                     "kernel": f"k_step_tma (256^3 level, depth {depth}, z-chunk {zc})",
+                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, z-chunk {zc})" if zc
+                                else "k_step_f32 (256^3 level, one-step z-marching)"),
                      "launches": fine_launches, "ms_per_launch": fine_ms / max(1, fine_launches),
                      "bytes_per_launch": fine_bytes / max(1, fine_launches), "peak_kind": peak_note,
                      "effective_frac": eff},

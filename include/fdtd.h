@@ -98,10 +98,14 @@ typedef struct {
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
   int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
                              (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
-  int32_t autotune;       /* 1 (default): time every (depth, z-chunk) candidate on first use of a
-                             lattice size and keep the fastest (results are identical for all) */
-  int32_t zchunk;         /* z-planes per block of the TMA stencil when temporal_depth > 0;
-                             0 = heuristic */
+  int32_t autotune;       /* 1 (default): time every (depth, tile width, span) candidate and the
+                             one-step kernel on first use of a lattice size and keep the
+                             fastest (results are identical for all) */
+  int32_t zchunk;         /* span of the TMA stencil when temporal_depth > 0: consecutive tile
+                             planes per block, the x-y tile columns laid end to end with z
+                             fastest (a span that divides n is a z-chunk; a longer or ragged
+                             one runs on into the next column); 0 = one equal span per
+                             resident block */
   int32_t wait_limit_us;  /* bound on every device-side wait: 0 = default (0.2 s per pipeline
                              wait, 2 s per grid barrier), > 0 = microseconds, < 0 = none (a wait
                              that is not already complete expires at once; for testing the
@@ -218,7 +222,9 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
                   int mem_kind, fdtd_obs* obs);
 
 /* Stencil configuration in use for lattice `lat` (after autotuning, if on):
- * temporal depth (steps per launch) and z-planes per block. */
+ * temporal depth (steps per launch) and the span (tile planes per block,
+ * options.zchunk) of the TMA kernel; zchunk = 0 (depth 1) when the one-step
+ * z-marching kernel is in use. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
 /* Snapshots (Sec. III): full copies of psi kept in the workspace, in

@@ -317,7 +317,8 @@ class Solver:
             _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
 
     def tuned_config(self, lat: int = 0) -> tuple[int, int]:
-        """(temporal depth, z-planes per block) the stencil uses for lattice `lat`."""
+        """(temporal depth, span in tile planes per block) the stencil uses for
+        lattice `lat`; span 0 means the one-step z-marching kernel (no TMA)."""
         d, z = ctypes.c_int(), ctypes.c_int()
         with self._ctx():
             _check(lib.fdtd_tuned_config(self.handle, lat, ctypes.byref(d), ctypes.byref(z)), self.handle)

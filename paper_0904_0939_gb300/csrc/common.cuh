@@ -32,6 +32,36 @@ template <> struct Store<__nv_bfloat16> {
   __device__ __forceinline__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
 };
 
+// ---------------------------------------------------------------- launch overlap
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while its predecessor on the stream is still running.  Every
+// such kernel calls pdl_wait() before it touches memory (it returns once the
+// predecessor has completed and its writes are visible) and pdl_trigger()
+// to let its own successor be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------- renormalisation
+// One site of psi <- P(s psi) (Secs. III, IV): FP64 lattices multiply in
+// FP64; FP32 / BF16 lattices multiply the FP32 value by s rounded to FP32
+// (ScaleT), so every kernel that renormalises an FP32 lattice rounds alike.
+template <typename T>
+struct ScaleT {
+  using S = float;
+};
+template <>
+struct ScaleT<double> {
+  using S = double;
+};
+__device__ __forceinline__ float scale_site(float v, float s, bool neg, bool zero) {
+  const float r = __fmul_rn(v, s);
+  return zero ? 0.0f : (neg ? -r : r);
+}
+__device__ __forceinline__ double scale_site(double v, double s, bool neg, bool zero) {
+  const double r = __dmul_rn(v, s);
+  return zero ? 0.0 : (neg ? -r : r);
+}
+
 // ---------------------------------------------------------------- coefficients
 // Eq. updateeq with h = dtau V / 2:
 //   psi' = A psi + (B dtau / 2m) sum_i (D . PsiHat)_i,

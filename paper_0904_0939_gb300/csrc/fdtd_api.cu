@@ -76,8 +76,10 @@ struct Lat {
   bool tma_ok = false;
   CUtensorMap maps[2][3][3];
   CUtensorMap sums_maps[3];
-  // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet)
+  // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet);
+  // plain = the one-step z-marching kernel (bit-identical) was timed fastest
   int depth = 0, tx = 128, zc = 0;
+  bool plain = false;
 };
 
 struct Carve {
@@ -308,21 +310,23 @@ void with_type(int prec, F&& f) {
 // ---- autotuning of the stencil configuration ---------------------------------
 // Fastest (depth, z-chunk) per (n, precision, device), shared by all handles.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> g_tune;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int, bool>> g_tune;
 
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
+  L.plain = false;
   if (!tma) {
     L.depth = 1;
     L.tx = 128;
     L.zc = 0;
+    L.plain = true;
     return;
   }
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
     L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
     L.tx = L.d.n > 64 ? 128 : 64;
-    L.zc = c->o.zchunk > 0 ? std::min(c->o.zchunk, L.d.n) : tma_zchunk(L.d.n, L.depth, L.tx);
+    L.zc = c->o.zchunk > 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
     return;
   }
   int dev = 0;
@@ -332,47 +336,72 @@ void choose_config(fdtd_context* c, Lat& L) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      L.depth = std::get<0>(it->second);
-      L.tx = std::get<1>(it->second);
-      L.zc = std::get<2>(it->second);
+      std::tie(L.depth, L.tx, L.zc, L.plain) = it->second;
       return;
     }
   }
-  // time each candidate: psi[cur] -> psi[1-cur] (psi[cur] is only read)
+  // time each candidate (every one of them is bit-identical):
+  // psi[cur] -> psi[1-cur], psi[cur] is only read
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int n = L.d.n;
   double best = 0.0;
   int bd = auto_depth(n, L.d.precision), bt = n > 64 ? 128 : 64, bz = tma_zchunk(n, bd, bt);
+  bool bp = false;
+  auto time_it = [&](auto&& launch, int depth) {
+    launch();
+    const int reps = 3;
+    cudaEventRecord(e0, c->st);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->stats.launches += reps + 1;
+    return (double)L.n3 * depth * reps / (ms > 0.f ? ms : 1e-6);
+  };
+  // the plain one-step kernel
+  {
+    double rate = time_it(
+        [&]() {
+          launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p,
+                                 nullptr, c->st);
+        },
+        1);
+    best = rate;
+    bd = 1;
+    bp = true;
+  }
   for (int ti = 0; ti < 2; ++ti) {
     const int tx = ti ? 128 : 64;
     if (tx == 128 && n <= 64) continue;
     for (int d = 1; d <= blocked_max_depth(); ++d) {
-      int prev = -1;
-      for (int div = 1; div <= 32; div *= 2) {
-        int zc = (n + div - 1) / div;
-        if (zc < std::max(8, 4 * d) || zc == prev) continue;
-        prev = zc;
-        auto launch = [&]() {
-          launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx, zc,
-                          nullptr, c->flags + 1, c->st);
-          c->stats.launches += 1;
-        };
-        launch();
-        const int reps = 3;
-        cudaEventRecord(e0, c->st);
-        for (int r = 0; r < reps; ++r) launch();
-        cudaEventRecord(e1, c->st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        double rate = (double)L.n3 * d * reps / (ms > 0.f ? ms : 1e-6);
+      // spans: z-chunks n / 2^i (depth 1 repeats no planes, deeper levels
+      // repeat 2(d-1) per item, so short chunks only for depth 1) and the
+      // spans that fill the resident blocks in one, two or three waves
+      std::vector<int> spans;
+      for (int div = 1; div <= 128; div *= 2) {
+        const int zc = (n + div - 1) / div;
+        if (zc >= (d == 1 ? 2 : std::max(8, 4 * d))) spans.push_back(zc);
+      }
+      const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx);
+      for (int m = 1; m <= 3; ++m) spans.push_back((int)std::max(1LL, (total + m * slots - 1) / (m * slots)));
+      std::sort(spans.begin(), spans.end());
+      spans.erase(std::unique(spans.begin(), spans.end()), spans.end());
+      for (int zc : spans) {
+        double rate = time_it(
+            [&]() {
+              launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx,
+                              zc, nullptr, c->flags + 1, c->st);
+            },
+            d);
         if (rate > best) {
           best = rate;
           bd = d;
           bt = tx;
           bz = zc;
+          bp = false;
         }
       }
     }
@@ -390,16 +419,17 @@ void choose_config(fdtd_context* c, Lat& L) {
   L.depth = bd;
   L.tx = bt;
   L.zc = bz;
+  L.plain = bp;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[key] = std::make_tuple(bd, bt, bz);
+  g_tune[key] = std::make_tuple(bd, bt, bz, bp);
 }
 
 // Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows),
 // the first of them being step t0 of the current evolve.
 void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0 = 0) {
   const int prec = L.d.precision;
-  const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
   choose_config(c, L);
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
@@ -1163,7 +1193,7 @@ int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
   Lat& L = h->lats[lat];
   if (L.has_v && L.has_psi) choose_config(h, L);
   *depth = L.depth;
-  *zchunk = L.zc;
+  *zchunk = L.plain ? 0 : L.zc;
   return cuda_check(h, "tuned_config");
 }
 

@@ -183,38 +183,34 @@ __global__ void k_store_scale(const LatState* s, double* dst) { *dst = s->scale;
 void launch_store_scale(const LatState* s, double* dst, cudaStream_t st) { k_store_scale<<<1, 1, 0, st>>>(s, dst); }
 
 // Recompute pass of the checkpointed forward: out = P(scale * in) with the
-// factor saved by the first forward pass.
+// factor saved by the first forward pass, rounded as the forward check
+// rounds it (scale_site), one site per thread on an (x, y, z) grid.
 template <typename T>
-__global__ void k_scale_parity_from(const T* __restrict__ in, T* __restrict__ out, int n, int mask,
-                                    const double* __restrict__ scale) {
-  const double s = *scale;
-  const size_t total = (size_t)n * n * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    int c[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / ((size_t)n * n))};
-    double sign = 1.0;
-    bool zero = false;
-    for (int ax = 0; ax < 3; ++ax) {
-      int mode = (mask >> (2 * ax)) & 3;
-      if (mode == 0) continue;
-      int mm = n - 1 - c[ax];
-      if (c[ax] > mm) {
-        c[ax] = mm;
-        if (mode == 2) sign = -sign;
-      } else if (c[ax] == mm && mode == 2) {
-        zero = true;
-      }
+__global__ void __launch_bounds__(256) k_scale_parity_from(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                           int mask, const double* __restrict__ scale) {
+  using S = typename ScaleT<T>::S;
+  const S s = (S)*scale;
+  const int x0 = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 8 + threadIdx.y, z0 = blockIdx.z;
+  if (x0 >= n || y0 >= n) return;
+  int c[3] = {x0, y0, z0};
+  bool neg = false, zero = false;
+  for (int ax = 0; ax < 3; ++ax) {
+    int mode = (mask >> (2 * ax)) & 3;
+    if (mode == 0) continue;
+    int mm = n - 1 - c[ax];
+    if (c[ax] > mm) {
+      c[ax] = mm;
+      neg ^= (mode == 2);
+    } else if (c[ax] == mm && mode == 2) {
+      zero = true;
     }
-    double val = zero ? 0.0 : sign * ((double)Store<T>::to(in[site_index(c[0], c[1], c[2], n)]) * s);
-    if constexpr (sizeof(T) == 8)
-      out[i] = val;
-    else
-      out[i] = Store<T>::from((float)val);
   }
+  const S v = (S)Store<T>::to(in[site_index(c[0], c[1], c[2], n)]);
+  out[site_index(x0, y0, z0, n)] = Store<T>::from(scale_site(v, s, neg, zero));
 }
 template <typename T>
 void launch_scale_parity_from(const T* in, T* out, int n, int mask, const double* scale, cudaStream_t st) {
-  size_t total = (size_t)n * n * n;
-  k_scale_parity_from<T><<<grid_1d(total), 256, 0, st>>>(in, out, n, mask, scale);
+  k_scale_parity_from<T><<<dim3((n + 31) / 32, (n + 7) / 8, n), dim3(32, 8), 0, st>>>(in, out, n, mask, scale);
 }
 template void launch_scale_parity_from<double>(const double*, double*, int, int, const double*, cudaStream_t);
 template void launch_scale_parity_from<float>(const float*, float*, int, int, const double*, cudaStream_t);

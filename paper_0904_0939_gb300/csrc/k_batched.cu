@@ -240,29 +240,31 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const 
         const BatchLat& L = lats[l];
         const LatState* st = L.state;
         if (*(volatile const int32_t*)&st->scale_seq != check_id) continue;
-        const double scale = *(volatile const double*)&st->scale;
+        const float scale = (float)*(volatile const double*)&st->scale;
         const int mask = run->reimpose ? L.mask : 0;
         const int n = L.n;
         const float* in = L.psi[s_cur[l]];
         float* out = L.psi[s_cur[l] ^ 1];
-        const size_t total = (size_t)n * n * n;
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-          int c[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / ((size_t)n * n))};
-          double sign = 1.0;
-          bool zero = false;
-          for (int ax = 0; ax < 3; ++ax) {
-            int mode = (mask >> (2 * ax)) & 3;
-            if (mode == 0) continue;
-            int mm = n - 1 - c[ax];
-            if (c[ax] > mm) {
-              c[ax] = mm;
-              if (mode == 2) sign = -sign;
-            } else if (c[ax] == mm && mode == 2) {
-              zero = true;
+        // rows (y, z) dealt to the grid's warps, x along the lanes
+        const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
+        for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n * n; r += nwarps) {
+          const int y0 = r % n, z0 = r / n;
+          for (int x0 = lane; x0 < n; x0 += 32) {
+            int c[3] = {x0, y0, z0};
+            bool neg = false, zero = false;
+            for (int ax = 0; ax < 3; ++ax) {
+              int mode = (mask >> (2 * ax)) & 3;
+              if (mode == 0) continue;
+              int mm = n - 1 - c[ax];
+              if (c[ax] > mm) {
+                c[ax] = mm;
+                neg ^= (mode == 2);
+              } else if (c[ax] == mm && mode == 2) {
+                zero = true;
+              }
             }
+            out[((size_t)z0 * n + y0) * n + x0] = scale_site(in[site_index(c[0], c[1], c[2], n)], scale, neg, zero);
           }
-          double val = zero ? 0.0 : sign * ((double)in[site_index(c[0], c[1], c[2], n)] * scale);
-          out[i] = (float)val;
         }
       }
       if (!grid_barrier(run, err)) return;

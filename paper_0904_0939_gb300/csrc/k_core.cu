@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(TX* TY) k_step_f64(const double* __restrict__ 
                                                      const double* __restrict__ coefA,
                                                      const double* __restrict__ coefCB, int n, int zc,
                                                      const int32_t* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<double> tile;
   zmarch<double>(in, n, zc, tile,
@@ -102,6 +104,8 @@ template <typename T>
 __global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T* __restrict__ out,
                                                      const float* __restrict__ v, int n, int zc, float half_dtau,
                                                      float one_m6c, float cc, const int32_t* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<float> tile;
   zmarch<T>(in, n, zc, tile,
@@ -117,13 +121,14 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T
 void launch_step_f64(const double* in, double* out, const double* coefA, const double* coefCB, const Params& p,
                      const int32_t* active, cudaStream_t st) {
   Tiling t = tiling_for(p.n, 1216);
-  k_step_f64<<<t.grid, dim3(TX, TY), 0, st>>>(in, out, coefA, coefCB, p.n, t.zc, active);
+  launch_pdl(k_step_f64, t.grid, dim3(TX, TY), 0, st, in, out, coefA, coefCB, p.n, t.zc, active);
 }
 
 template <typename T>
 void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st) {
   Tiling t = tiling_for(p.n, 1216);
-  k_step_f32<T><<<t.grid, dim3(TX, TY), 0, st>>>(in, out, v, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
+  launch_pdl(k_step_f32<T>, t.grid, dim3(TX, TY), 0, st, in, out, v, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f,
+             active);
 }
 template void launch_step_f32<float>(const float*, float*, const float*, const Params&, const int32_t*, cudaStream_t);
 template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
@@ -195,6 +200,8 @@ __device__ __forceinline__ void block_sum4_store(double v0, double v1, double v2
 __global__ void __launch_bounds__(TX* TY) k_sums_f64(const double* __restrict__ psi, const double* __restrict__ v,
                                                      int n, int zc, double a, double kfac, double* partials,
                                                      const int32_t* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<double> tile;
   double s0 = 0, sh = 0, sr = 0, sv = 0;
@@ -221,6 +228,8 @@ template <typename T>
 __global__ void __launch_bounds__(TX* TY) k_sums_f32(const T* __restrict__ psi, const float* __restrict__ v, int n,
                                                      int zc, float a, float kfac, double* partials,
                                                      const int32_t* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<float> tile;
   Kahan s0, sh, sr, sv;
@@ -254,16 +263,16 @@ template <>
 int launch_sums<double>(const double* psi, const void* v, const Params& p, double* partials, const int32_t* active,
                         cudaStream_t st) {
   Tiling t = sums_tiling(p.n);
-  k_sums_f64<<<t.grid, dim3(TX, TY), 0, st>>>(psi, (const double*)v, p.n, t.zc, p.a,
-                                               1.0 / (2.0 * p.mass * p.a * p.a), partials, active);
+  launch_pdl(k_sums_f64, t.grid, dim3(TX, TY), 0, st, psi, (const double*)v, p.n, t.zc, p.a,
+             1.0 / (2.0 * p.mass * p.a * p.a), partials, active);
   return (int)(t.grid.x * t.grid.y * t.grid.z);
 }
 template <typename T>
 int launch_sums(const T* psi, const void* v, const Params& p, double* partials, const int32_t* active,
                 cudaStream_t st) {
   Tiling t = sums_tiling(p.n);
-  k_sums_f32<T><<<t.grid, dim3(TX, TY), 0, st>>>(psi, (const float*)v, p.n, t.zc, (float)p.a,
-                                                  (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active);
+  launch_pdl(k_sums_f32<T>, t.grid, dim3(TX, TY), 0, st, psi, (const float*)v, p.n, t.zc, (float)p.a,
+             (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active);
   return (int)(t.grid.x * t.grid.y * t.grid.z);
 }
 template int launch_sums<float>(const float*, const void*, const Params&, double*, const int32_t*, cudaStream_t);
@@ -276,6 +285,8 @@ template int launch_sums<__nv_bfloat16>(const __nv_bfloat16*, const void*, const
 __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __restrict__ parts, int np, int check_id,
                                                   int64_t t, double a3, double v_inf, double tol, int tol_rel,
                                                   int record) {
+  pdl_wait();
+  pdl_trigger();
   if (record && s->active == 0) return;
   __shared__ double sm[4][256];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -329,7 +340,8 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
 
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
                      double v_inf, double tol, int tol_rel, int record, cudaStream_t st) {
-  k_finalize<<<1, 256, 0, st>>>(s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol, tol_rel, record);
+  launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol,
+             tol_rel, record);
 }
 
 __global__ void k_state_reset(LatState* s, int mode) {
@@ -372,96 +384,98 @@ __device__ __forceinline__ void parity_source(int& x, int& y, int& z, int n, int
   }
 }
 
+// psi_out = P(scale psi_in) (Secs. III, IV), one site per thread on an
+// (x, y, z) grid of 32 x 8 blocks; with s given, only if this check's factor
+// was posted (s->scale_seq == check_id).
 template <typename T>
-__global__ void k_scale_parity(const T* __restrict__ in, T* __restrict__ out, int n, int mask,
-                               const LatState* __restrict__ s, int check_id, int out_idx, LatState* sw) {
-  double scale = 1.0;
+__global__ void __launch_bounds__(256) k_scale_parity(const T* __restrict__ in, T* __restrict__ out, int n, int mask,
+                                                      const LatState* __restrict__ s, int check_id, int out_idx,
+                                                      LatState* sw) {
+  pdl_wait();
+  pdl_trigger();
+  using S = typename ScaleT<T>::S;
+  S scale = S(1);
   if (s) {
     if (s->scale_seq != check_id) return;
-    scale = s->scale;
+    scale = (S)s->scale;
   }
-  if (sw && blockIdx.x == 0 && threadIdx.x == 0) sw->cur = out_idx;
-  const size_t total = (size_t)n * n * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
-    double sign = 1.0;
-    bool zero = false;
-    if (mask) parity_source<T>(x, y, z, n, mask, sign, zero);
-    double val = zero ? 0.0 : sign * ((double)Store<T>::to(in[site_index(x, y, z, n)]) * scale);
-    if constexpr (sizeof(T) == 8)
-      out[i] = val;
-    else
-      out[i] = Store<T>::from((float)val);
-  }
+  const int x0 = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 8 + threadIdx.y, z0 = blockIdx.z;
+  if (sw && (x0 | y0 | z0) == 0) sw->cur = out_idx;
+  if (x0 >= n || y0 >= n) return;
+  int x = x0, y = y0, z = z0;
+  double sign = 1.0;
+  bool zero = false;
+  if (mask) parity_source<T>(x, y, z, n, mask, sign, zero);
+  const S v = (S)Store<T>::to(in[site_index(x, y, z, n)]);
+  out[site_index(x0, y0, z0, n)] = Store<T>::from(scale_site(v, scale, sign < 0.0, zero));
 }
 
-// FP32, n % 4 == 0: one float4 per thread.  The mirror of an aligned float4
-// along x is the aligned float4 ending at n-1-4i, read reversed; each site
-// gets exactly the expression of k_scale_parity, so the two agree bit for bit.
-__global__ void k_scale_parity_f4(const float* __restrict__ in, float* __restrict__ out, int n, int mask,
-                                  const LatState* __restrict__ s, int check_id, int out_idx, LatState* sw) {
-  double scale = 1.0;
+// FP32, n % 4 == 0: one float4 per thread (x over float4 columns).  The
+// mirror of an aligned float4 along x is the aligned float4 ending at
+// n-1-4i, read reversed; each site gets exactly the expression of
+// k_scale_parity, so the two agree bit for bit.
+__global__ void __launch_bounds__(256) k_scale_parity_f4(const float* __restrict__ in, float* __restrict__ out, int n,
+                                                         int mask, const LatState* __restrict__ s, int check_id,
+                                                         int out_idx, LatState* sw) {
+  pdl_wait();
+  pdl_trigger();
+  float scale = 1.0f;
   if (s) {
     if (s->scale_seq != check_id) return;
-    scale = s->scale;
+    scale = (float)s->scale;
   }
-  if (sw && blockIdx.x == 0 && threadIdx.x == 0) sw->cur = out_idx;
+  const int x4 = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if (sw && (x4 | y | z) == 0) sw->cur = out_idx;
   const int n4 = n >> 2;
-  const size_t total = (size_t)n * n * n4;
+  if (x4 >= n4 || y >= n) return;
   const int mx = mask & 3, my = (mask >> 2) & 3, mz = (mask >> 4) & 3;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int x4 = (int)(i % n4), y = (int)((i / n4) % n), z = (int)(i / ((size_t)n4 * n));
-    int ys = y, zs = z;
-    double sgn = 1.0;
-    bool zero = false;
-    if (my) {
-      const int mm = n - 1 - y;
-      if (y > mm) {
-        ys = mm;
-        if (my == 2) sgn = -sgn;
-      } else if (y == mm && my == 2) {
-        zero = true;
-      }
+  int ys = y, zs = z;
+  bool neg = false, zero = false;
+  if (my) {
+    const int mm = n - 1 - y;
+    if (y > mm) {
+      ys = mm;
+      neg ^= (my == 2);
+    } else if (y == mm && my == 2) {
+      zero = true;
     }
-    if (mz) {
-      const int mm = n - 1 - z;
-      if (z > mm) {
-        zs = mm;
-        if (mz == 2) sgn = -sgn;
-      } else if (z == mm && mz == 2) {
-        zero = true;
-      }
-    }
-    const float* row = in + ((size_t)zs * n + ys) * n;
-    const float4 a = *reinterpret_cast<const float4*>(row + 4 * x4);
-    float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (mx) {
-      const float4 b = *reinterpret_cast<const float4*>(row + (n - 4 - 4 * x4));
-      mv[0] = b.w;  // mirror of site 4 x4 + 0 is n - 1 - 4 x4
-      mv[1] = b.z;
-      mv[2] = b.y;
-      mv[3] = b.x;
-    }
-    float o[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int x = 4 * x4 + c, mm = n - 1 - x;
-      double sg = sgn;
-      bool zc = zero;
-      float src = av[c];
-      if (mx) {
-        if (x > mm) {
-          src = mv[c];
-          if (mx == 2) sg = -sg;
-        } else if (x == mm && mx == 2) {
-          zc = true;
-        }
-      }
-      const double val = zc ? 0.0 : sg * ((double)src * scale);
-      o[c] = (float)val;
-    }
-    *reinterpret_cast<float4*>(out + 4 * i) = make_float4(o[0], o[1], o[2], o[3]);
   }
+  if (mz) {
+    const int mm = n - 1 - z;
+    if (z > mm) {
+      zs = mm;
+      neg ^= (mz == 2);
+    } else if (z == mm && mz == 2) {
+      zero = true;
+    }
+  }
+  const float* row = in + ((size_t)zs * n + ys) * n;
+  const float4 a = *reinterpret_cast<const float4*>(row + 4 * x4);
+  float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (mx) {
+    const float4 b = *reinterpret_cast<const float4*>(row + (n - 4 - 4 * x4));
+    mv[0] = b.w;  // mirror of site 4 x4 + 0 is n - 1 - 4 x4
+    mv[1] = b.z;
+    mv[2] = b.y;
+    mv[3] = b.x;
+  }
+  float o[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int x = 4 * x4 + c, mm = n - 1 - x;
+    bool ng = neg, zc = zero;
+    float src = av[c];
+    if (mx) {
+      if (x > mm) {
+        src = mv[c];
+        ng ^= (mx == 2);
+      } else if (x == mm && mx == 2) {
+        zc = true;
+      }
+    }
+    o[c] = scale_site(src, scale, ng, zc);
+  }
+  *reinterpret_cast<float4*>(out + ((size_t)z * n + y) * n + 4 * x4) = make_float4(o[0], o[1], o[2], o[3]);
 }
 
 static int grid_for(size_t total, int threads) {
@@ -473,14 +487,15 @@ static int grid_for(size_t total, int threads) {
 template <typename T>
 void launch_scale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
                          LatState* s_w, cudaStream_t st) {
-  size_t total = (size_t)n * n * n;
   if constexpr (std::is_same_v<T, float>) {
     if (n % 4 == 0) {
-      k_scale_parity_f4<<<grid_for(total / 4, 256), 256, 0, st>>>(in, out, n, mask, s, check_id, out_idx, s_w);
+      launch_pdl(k_scale_parity_f4, dim3((n / 4 + 31) / 32, (n + 7) / 8, n), dim3(32, 8), 0, st, in, out, n, mask, s,
+                 check_id, out_idx, s_w);
       return;
     }
   }
-  k_scale_parity<T><<<grid_for(total, 256), 256, 0, st>>>(in, out, n, mask, s, check_id, out_idx, s_w);
+  launch_pdl(k_scale_parity<T>, dim3((n + 31) / 32, (n + 7) / 8, n), dim3(32, 8), 0, st, in, out, n, mask, s, check_id,
+             out_idx, s_w);
 }
 template void launch_scale_parity<double>(const double*, double*, int, int, const LatState*, int, int, LatState*,
                                           cudaStream_t);
@@ -534,37 +549,53 @@ __device__ __forceinline__ void interp_axis(int x, int& lo, double& wlo, double&
   }
 }
 
+// One fine site per thread on an (x, y, z) grid.  With an FP64 side the
+// eight weighted coarse values are summed in FP64; FP32 / BF16 lattices
+// interpolate separably in FP32 (x, then y, then z): the weights 1/4 and 3/4
+// are exact, so the result differs from the FP64 sum only by the rounding of
+// the seven FP32 operations.
 template <typename Ti, typename To>
 __global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ out) {
   const int nf = 2 * nc;
-  const size_t total = (size_t)nf * nf * nf;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(i % nf), y = (int)((i / nf) % nf), z = (int)(i / ((size_t)nf * nf));
-    int lx, ly, lz;
-    double wx[2], wy[2], wz[2];
-    interp_axis(x, lx, wx[0], wx[1]);
-    interp_axis(y, ly, wy[0], wy[1]);
-    interp_axis(z, lz, wz[0], wz[1]);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= nf) return;
+  const size_t i = ((size_t)z * nf + y) * nf + x;
+  int lx, ly, lz;
+  double wx[2], wy[2], wz[2];
+  interp_axis(x, lx, wx[0], wx[1]);
+  interp_axis(y, ly, wy[0], wy[1]);
+  interp_axis(z, lz, wz[0], wz[1]);
+  auto at = [&](int dx, int dy, int dz) {
+    const int cx = lx + dx, cy = ly + dy, cz = lz + dz;
+    return ((unsigned)cx < (unsigned)nc && (unsigned)cy < (unsigned)nc && (unsigned)cz < (unsigned)nc)
+               ? in[site_index(cx, cy, cz, nc)]
+               : Store<Ti>::from(0.0f);
+  };
+  if constexpr (sizeof(Ti) == 8 || sizeof(To) == 8) {
     double acc = 0.0;
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          int cx = lx + dx, cy = ly + dy, cz = lz + dz;
-          double val = 0.0;
-          if ((unsigned)cx < (unsigned)nc && (unsigned)cy < (unsigned)nc && (unsigned)cz < (unsigned)nc)
-            val = (double)Store<Ti>::to(in[site_index(cx, cy, cz, nc)]);
-          acc += (wx[dx] * wy[dy] * wz[dz]) * val;
-        }
+        for (int dx = 0; dx < 2; ++dx) acc += (wx[dx] * wy[dy] * wz[dz]) * (double)Store<Ti>::to(at(dx, dy, dz));
     if constexpr (sizeof(To) == 8)
       out[i] = acc;
     else
       out[i] = Store<To>::from((float)acc);
+  } else {
+    const float fx0 = (float)wx[0], fx1 = (float)wx[1], fy0 = (float)wy[0], fy1 = (float)wy[1];
+    float row[2][2];
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        row[dz][dy] = __fadd_rn(__fmul_rn(fx0, Store<Ti>::to(at(0, dy, dz))), __fmul_rn(fx1, Store<Ti>::to(at(1, dy, dz))));
+    const float p0 = __fadd_rn(__fmul_rn(fy0, row[0][0]), __fmul_rn(fy1, row[0][1]));
+    const float p1 = __fadd_rn(__fmul_rn(fy0, row[1][0]), __fmul_rn(fy1, row[1][1]));
+    out[i] = Store<To>::from(__fadd_rn(__fmul_rn((float)wz[0], p0), __fmul_rn((float)wz[1], p1)));
   }
 }
 template <typename Ti, typename To>
 void launch_upsample(const Ti* in, int nc, To* out, cudaStream_t st) {
-  size_t total = (size_t)8 * nc * nc * nc;
-  k_upsample<Ti, To><<<grid_for(total, 256), 256, 0, st>>>(in, nc, out);
+  const int nf = 2 * nc;
+  dim3 grid((nf + 127) / 128, nf, nf);
+  k_upsample<Ti, To><<<grid, 128, 0, st>>>(in, nc, out);
 }
 #define INST_UP(Ti, To) template void launch_upsample<Ti, To>(const Ti*, int, To*, cudaStream_t);
 INST_UP(double, double)

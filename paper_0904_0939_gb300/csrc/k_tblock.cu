@@ -3,6 +3,7 @@
 // tile width 64 or 128) and the fused lattice sums of Eq. energysum.
 // Algorithmic HBM traffic of a stencil launch: psi in + psi out + V in,
 // 12 B per site for K steps; of a sums launch: psi + V, 8 B per site.
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -14,20 +15,36 @@ namespace fdtd {
 
 namespace tb {
 
+// The tile columns (TXT x TY sites in x-y, all n planes in z) are laid end
+// to end, column-major with z fastest, into ntiles * n "tile planes"; block
+// b updates the `span` consecutive tile planes from b * span on, split into
+// one item per column it touches.  A span that divides n is a plain z-chunk
+// grid; a span of ceil(ntiles * n / resident blocks) gives every SM the
+// same work in one wave whatever the lattice size.
 template <int K, int TXT>
 __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                     const __grid_constant__ CUtensorMap map_v,
-                                                                    float* __restrict__ out, int n, int zc,
-                                                                    float half_dtau, float one_m6c, float cc,
+                                                                    float* __restrict__ out, int n, int ntx,
+                                                                    long long total, int span, float half_dtau,
+                                                                    float one_m6c, float cc,
                                                                     const int32_t* __restrict__ active,
                                                                     int32_t* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   if (*(volatile const int32_t*)err != 0) return;  // an earlier wait expired: do nothing
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = aligned_smem(smem_raw);
-  const int z0 = blockIdx.z * zc;
-  tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, blockIdx.x * TXT, blockIdx.y * TY, z0, min(z0 + zc, n),
-                        half_dtau, one_m6c, cc, err);
+  long long g = (long long)blockIdx.x * span;
+  const long long gend = min(g + span, total);
+  while (g < gend) {
+    const int t = (int)(g / n), z0 = (int)(g - (long long)t * n);
+    const int z1 = (int)min((long long)n, z0 + (gend - g));
+    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, z0, z1, half_dtau,
+                               one_m6c, cc, err))
+      return;
+    g += z1 - z0;
+  }
 }
 
 constexpr int kSumsTX = 64;
@@ -38,6 +55,8 @@ __global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_sums_tma(const __g
                                                                        double* __restrict__ partials,
                                                                        const int32_t* __restrict__ active,
                                                                        int32_t* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   if (active && *active == 0) return;
   if (*(volatile const int32_t*)err != 0) return;
   extern __shared__ __align__(128) char smem_raw[];
@@ -64,13 +83,31 @@ void set_smem(Kern k, size_t bytes) {
 }
 
 template <int K, int TXT>
-void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int zc,
+long long tile_planes(int n) {
+  return (long long)((n + TXT - 1) / TXT) * ((n + TY - 1) / TY) * n;
+}
+
+template <int K, int TXT>
+void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int span,
               const int32_t* active, int32_t* err, cudaStream_t st) {
   using G = Geo<K, TXT>;
   set_smem(k_step_tma<K, TXT>, G::SMEM);
-  dim3 grid((p.n + TXT - 1) / TXT, (p.n + TY - 1) / TY, (p.n + zc - 1) / zc);
-  k_step_tma<K, TXT><<<grid, G::THREADS, G::SMEM, st>>>(mpsi, mv, out, p.n, zc, p.half_dtau_f, p.one_m6c_f, p.c_f,
-                                                         active, err);
+  const long long total = tile_planes<K, TXT>(p.n);
+  const unsigned blocks = (unsigned)((total + span - 1) / span);
+  launch_pdl(k_step_tma<K, TXT>, dim3(blocks), dim3(G::THREADS), G::SMEM, st, mpsi, mv, out, p.n,
+             (p.n + TXT - 1) / TXT, total, span, p.half_dtau_f, p.one_m6c_f, p.c_f, active, err);
+}
+
+// Blocks of k_step_tma<K, TXT> resident on the whole device at once.
+template <int K, int TXT>
+int resident_blocks() {
+  using G = Geo<K, TXT>;
+  set_smem(k_step_tma<K, TXT>, G::SMEM);
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tma<K, TXT>, G::THREADS, G::SMEM);
+  return std::max(1, sms) * std::max(1, occ);
 }
 
 }  // namespace tb
@@ -84,13 +121,21 @@ int auto_depth(int n, int precision) {
   return n >= 96 ? 3 : 2;
 }
 
+long long tma_tile_planes(int n, int tx) {
+  return tx == 64 ? tb::tile_planes<1, 64>(n) : tb::tile_planes<1, 128>(n);
+}
+
+int tma_resident_blocks(int depth, int tx) {
+  if (tx == 64) return depth == 1 ? tb::resident_blocks<1, 64>()
+                                   : depth == 2 ? tb::resident_blocks<2, 64>() : tb::resident_blocks<3, 64>();
+  return depth == 1 ? tb::resident_blocks<1, 128>()
+                    : depth == 2 ? tb::resident_blocks<2, 128>() : tb::resident_blocks<3, 128>();
+}
+
 int tma_zchunk(int n, int depth, int tx) {
-  // enough blocks for several waves over the 152 SMs, chunks not much
-  // shorter than the 2(K-1) planes of warm-up they repeat
-  int tiles = ((n + tx - 1) / tx) * ((n + tb::TY - 1) / tb::TY);
-  int zc = n;
-  while (zc > 16 * depth && (long long)tiles * ((n + zc - 1) / zc) < 4 * 152) zc = (zc + 1) / 2;
-  return zc;
+  // one wave of equal spans over the resident blocks
+  const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(depth, tx);
+  return (int)std::max(1LL, (total + slots - 1) / slots);
 }
 
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
@@ -120,9 +165,8 @@ int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const 
   using G = tb::Geo<1, tb::kSumsTX>;
   tb::set_smem(tb::k_sums_tma, G::SMEM);
   dim3 grid((p.n + tb::kSumsTX - 1) / tb::kSumsTX, (p.n + tb::TY - 1) / tb::TY, 1);
-  tb::k_sums_tma<<<grid, G::THREADS, G::SMEM, st>>>(map_psi, map_v, p.n, (float)p.a,
-                                                     (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active,
-                                                     err);
+  launch_pdl(tb::k_sums_tma, grid, dim3(G::THREADS), G::SMEM, st, map_psi, map_v, p.n, (float)p.a,
+             (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active, err);
   return (int)(grid.x * grid.y);
 }
 

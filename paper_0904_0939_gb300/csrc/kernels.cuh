@@ -1,5 +1,6 @@
 // Internal launch interface between the C ABI (fdtd_api.cu) and the kernels.
 #pragma once
+#include <utility>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -41,6 +42,23 @@ struct Tiling {
 };
 Tiling tiling_for(int n, int min_blocks);
 
+// Launch with programmatic stream serialisation (the kernel must start with
+// pdl_wait(), see common.cuh).
+template <typename... Exp, typename... Act>
+void launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Act>(args)...);
+}
+
 // ---- launchers (all asynchronous on `st`) -----------------------------------
 // One update step psi_out = M psi_in (Eq. updateeq).
 void launch_step_f64(const double* in, double* out, const double* coefA, const double* coefCB, const Params& p,
@@ -52,10 +70,15 @@ void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const
 // with n % 4 == 0: `depth` update steps per pass over HBM (tile width tx =
 // 64 or 128), bit-identical to `depth` calls of launch_step_f32; and the
 // lattice sums with one partial per 64 x 16 tile column.  *err |= 1 if a
-// bounded wait expired.
+// bounded wait expired.  A stencil launch gives each block `zc` consecutive
+// tile planes of the column-major sequence of tma_tile_planes(n, tx) (a
+// block's span may run on into the next tile column); tma_zchunk is the
+// span that fills the device's resident blocks in one wave.
 bool tma_supported(int n, int precision);
 int blocked_max_depth();
 int auto_depth(int n, int precision);
+long long tma_tile_planes(int n, int tx);
+int tma_resident_blocks(int depth, int tx);
 int tma_zchunk(int n, int depth, int tx);
 void tma_box(int depth, int tx, int* box_w, int* box_h);
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h);

@@ -110,10 +110,12 @@ __device__ __forceinline__ long long wait_budget_ns(const int32_t* err) {
   const int us = *(volatile const int32_t*)(err + 1);
   return us == 0 ? (long long)kWaitLimitNs : (us > 0 ? 1000ll * us : -1);
 }
-// Wait bounded in wall-clock time; gives up early once any block has
-// reported an expired wait in *err.  Returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, const int32_t* err) {
-  const long long budget = wait_budget_ns(err);
+// Wait bounded in wall-clock time (budget from wait_budget_ns, read once per
+// item so that the wait itself touches no global memory on its fast path);
+// gives up early once any block has reported an expired wait in *err.
+// Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, const int32_t* err,
+                                                  long long budget) {
   if (budget < 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
@@ -165,6 +167,7 @@ struct Pipe {
   const CUtensorMap* mv;
   int x0, y0;
   const int32_t* err;
+  long long budget = 0;  // wall-clock wait budget in ns (< 0: do not wait)
   uint64_t* bars;
   float* ring;
   unsigned phase = 0;        // bit s: parity of the next wait on slot s (toggled on success)
@@ -180,7 +183,7 @@ struct Pipe {
     outstanding |= 1u << s;
   }
   __device__ __forceinline__ void wait(int s) {
-    if (mbar_wait_bounded(bars + s, (phase >> s) & 1u, err)) {
+    if (mbar_wait_bounded(bars + s, (phase >> s) & 1u, err, budget)) {
       phase ^= 1u << s;
       outstanding &= ~(1u << s);
     } else {
@@ -191,6 +194,7 @@ struct Pipe {
   __device__ __forceinline__ void begin(int j0, int jlast) {
     bars = (uint64_t*)(smem + G::BAR_OFF);
     ring = (float*)(smem + G::RING_OFF);
+    budget = wait_budget_ns(err);
     if (threadIdx.x == 0) {
       for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

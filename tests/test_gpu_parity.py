@@ -185,20 +185,25 @@ def test_observables_of_a_given_field(fd, orc, prec, tol):
     assert o["norm"] == pytest.approx(ref["S0"] * (L / n) ** 3, rel=tol)
 
 
-@pytest.mark.parametrize("nc,mask", [(5, 0), (8, wl.ODD_Y), (12, wl.SYMMETRIC_ALL)])
-def test_upsample_matches_oracle(fd, orc, nc, mask):
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-14), ("F32", 1e-6)])
+@pytest.mark.parametrize("nc,mask", [(5, 0), (8, wl.ODD_Y), (12, wl.SYMMETRIC_ALL), (68, wl.ODD_Z)])
+def test_upsample_matches_oracle(fd, orc, nc, mask, prec, tol):
+    """Trilinear transfer Nc^3 -> (2 Nc)^3 (Sec. VI), renormalised and with
+    the coarse field's symmetry: FP64 to rounding, FP32 (separable FP32
+    interpolation, FP32 start field) to a few units of FP32 rounding."""
     L = 5.0
-    coarse = solver(fd, nc, L, fd.F64)
+    p = getattr(fd, prec)
+    coarse = solver(fd, nc, L, p)
     coarse.set_potential(wl.harmonic(nc, L))
     coarse.init_symmetric(4, mask)
-    fine = solver(fd, 2 * nc, L, fd.F64)
+    fine = solver(fd, 2 * nc, L, p)
     fine.set_potential(wl.harmonic(2 * nc, L))
     fine.upsample_from(coarse)
     up = orc.upsample(orc.init_symmetric(nc, 4, mask))
     af = L / (2 * nc)
     up = up / math.sqrt(np.sum(up**2) * af**3)
     up = orc.impose_parity(up, mask)
-    assert rel_max(fine.get_psi(), up) <= 1e-14
+    assert rel_max(fine.get_psi(), up) <= tol
 
 
 def test_upsample_shape_mismatch(fd):
@@ -296,20 +301,28 @@ def test_full_size_256_sampled_sites(fd, orc):
 def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
     """The TMA-streamed kernel at depth K reproduces K plain steps bit for
     bit (ragged x/y tiles and z-chunks at n = 132; check cadence not a
-    multiple of K)."""
+    multiple of K), also with short spans that run on into the next tile
+    column or leave a ragged last chunk (down to one plane) and in the
+    configuration the autotuner picks."""
     L = 0.3 * n
     rng = np.random.default_rng(n)
     v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
     outs = {}
-    for name, kw in [("plain", dict(stencil_kernel=1)), ("k1", dict(temporal_depth=1)),
-                     ("k2", dict(temporal_depth=2)), ("k3", dict(temporal_depth=3))]:
+    variants = [("plain", dict(stencil_kernel=1)), ("k1", dict(temporal_depth=1)),
+                ("k2", dict(temporal_depth=2)), ("k3", dict(temporal_depth=3)),
+                ("k1z2", dict(temporal_depth=1, zchunk=2)), ("k1z3", dict(temporal_depth=1, zchunk=3)),
+                ("k2z9", dict(temporal_depth=2, zchunk=9)), ("k3z12", dict(temporal_depth=3, zchunk=12)),
+                ("k2z1", dict(temporal_depth=2, zchunk=1)), ("k3z1", dict(temporal_depth=3, zchunk=1)),
+                ("k3z200", dict(temporal_depth=3, zchunk=200)),
+                ("auto", dict(autotune=1))]
+    for name, kw in variants:
         s = solver(fd, n, L, fd.F32, check_every=50, **kw)
         s.set_potential(v)
         s.init_symmetric(31, wl.ODD_Z)
         s.evolve(100)
         outs[name] = s.get_psi(dtype=np.float32)
         s.close()
-    for name in ("k1", "k2", "k3"):
+    for name, _ in variants[1:]:
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
 
 
