@@ -111,7 +111,12 @@ typedef struct {
                              that is not already complete expires at once; for testing the
                              FDTD_ERR_TIMEOUT path) */
   int32_t snapshots;      /* snapshot slots per lattice (Sec. III excited states); 0 = none */
-  int32_t reserved[3];
+  int32_t graphs;         /* 1 (default): fdtd_evolve on one lattice runs its full pairs of
+                             check_every-step segments as one CUDA graph whose while loop is
+                             ended on the device by the convergence check (no host round trip
+                             per segment); the rest, and every run with profiling on, goes
+                             through the stream.  Results are identical either way. */
+  int32_t reserved[2];
 } fdtd_options;
 
 typedef struct {
@@ -134,6 +139,10 @@ typedef struct {
   double stencil_ms;      /* summed device time of stencil launches (profiling on) */
   int64_t stencil_site_updates;
   double stencil_bytes;   /* algorithmic HBM bytes of those launches */
+  int64_t graph_launches; /* evolve graphs launched (options.graphs) */
+  int64_t stencil_timed_launches; /* stencil launches stencil_ms covers (profiling on: the
+                             launches of the first two segments of each evolve, or all of
+                             them with options.graphs = 0) */
 } fdtd_stats;
 
 typedef struct fdtd_context* fdtd_handle;
@@ -249,7 +258,9 @@ FDTD_API int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double
 /* Launch counters and (when profiling is on) summed stencil device time. */
 FDTD_API int fdtd_get_stats(fdtd_handle h, fdtd_stats* out);
 FDTD_API int fdtd_reset_stats(fdtd_handle h);
-/* on = 1: bracket every stencil launch with CUDA events on the handle's stream. */
+/* on = 1: bracket stencil launches issued through the stream with CUDA events
+ * on the handle's stream (with options.graphs = 1, fdtd_evolve issues its
+ * first two segments through the stream for this and the rest as a graph). */
 FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
 
 /* Allocation-free observables of a caller-held field (no counterpart in

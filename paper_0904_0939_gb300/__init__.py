@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("snapshots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("snapshots", ctypes.c_int32), ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Obs(ctypes.Structure):
@@ -71,7 +71,8 @@ class Obs(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("stencil_launches", ctypes.c_int64),
                 ("stencil_ms", ctypes.c_double), ("stencil_site_updates", ctypes.c_int64),
-                ("stencil_bytes", ctypes.c_double)]
+                ("stencil_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64),
+                ("stencil_timed_launches", ctypes.c_int64)]
 
 
 EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",

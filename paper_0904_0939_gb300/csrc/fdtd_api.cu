@@ -80,7 +80,21 @@ struct Lat {
   // plain = the one-step z-marching kernel (bit-identical) was timed fastest
   int depth = 0, tx = 128, zc = 0;
   bool plain = false;
+  // evolve graph: a while loop over pairs of (check, check_every steps),
+  // built for one start buffer, mask and stencil configuration
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_key[6] = {-1, -1, -1, -1, -1, -1};
+  int64_t graph_kernels = 0;  // kernels per loop iteration
 };
+
+void release_graph(Lat& L) {
+  if (L.graph_exec) cudaGraphExecDestroy(L.graph_exec);
+  if (L.graph) cudaGraphDestroy(L.graph);
+  L.graph_exec = nullptr;
+  L.graph = nullptr;
+  L.graph_key[0] = -1;
+}
 
 struct Carve {
   char* base = nullptr;
@@ -139,6 +153,10 @@ int check_options(const fdtd_options& o, std::string& err) {
   }
   if (o.snapshots < 0 || o.snapshots > 1024) {
     err = "snapshots must be in [0, 1024]";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.graphs != 0 && o.graphs != 1) {
+    err = "graphs must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
   if (o.backward_steps < 0 || !std::isfinite(o.tol)) {
@@ -235,6 +253,7 @@ struct fdtd_context {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   int check_seq = 0;
+  cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured on
   // stencil launches not yet credited to the stats: a launch enqueued past
   // the check at which its lattice converged runs as a no-op and is dropped
   struct Pending {
@@ -289,7 +308,10 @@ void flush_pending(fdtd_context* c, int64_t cutoff) {
     c->stats.stencil_site_updates += p.updates;
     c->stats.stencil_bytes += p.bytes;
     float ms = 0.f;
-    if (p.ev >= 0 && cudaEventElapsedTime(&ms, c->ev[p.ev], c->ev[p.ev + 1]) == cudaSuccess) c->stats.stencil_ms += ms;
+    if (p.ev >= 0 && cudaEventElapsedTime(&ms, c->ev[p.ev], c->ev[p.ev + 1]) == cudaSuccess) {
+      c->stats.stencil_ms += ms;
+      c->stats.stencil_timed_launches += 1;
+    }
   }
   c->pending.clear();
   c->ev_used = 0;
@@ -502,6 +524,99 @@ int read_state(fdtd_context* c, Lat& L) {
   return FDTD_OK;
 }
 
+// The check of enqueue_check in device-sequenced form (inside the graph).
+void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditionalHandle cond) {
+  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  launch_finalize(&L.state[0], L.partials, np, 0, 0, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, (int)ce,
+                  cond, c->flags + 1);
+  c->stats.launches += 1;
+  int mask = c->o.reimpose_parity ? L.mask : 0;
+  scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], -1, 1 - L.cur, &L.state[0]);
+  L.cur ^= 1;
+}
+
+// Stencil launches and algorithmic bytes of one check_every-step segment.
+void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, double* bytes) {
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+  const int depth = tma ? L.depth : 1;
+  *launches = (ce + depth - 1) / depth;
+  *bytes = (double)*launches * L.n3 * (2.0 * L.es + (L.d.precision == FDTD_F64 ? 16.0 : 4.0));
+}
+
+// Build (or reuse) the evolve graph of lattice L for its current start
+// buffer: a while node whose body is two (check, segment) pairs -- a segment
+// flips the ping-pong buffers an odd number of times, a pair an even number,
+// so the body is the same at every iteration.  Returns false if the graph
+// cannot be made (the caller then uses the stream).
+bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
+  choose_config(c, L);  // autotuning synchronises: never inside a capture
+  const int mask = c->o.reimpose_parity ? L.mask : 0;
+  const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain, ce};
+  if (L.graph_exec && std::equal(key, key + 6, L.graph_key)) return true;
+  release_graph(L);
+  if (L.tma_ok && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
+    (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx);  // occupancy query outside the capture
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  cudaGraphNode_t node;
+  if (cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const int cur0 = L.cur;
+  const int64_t launches0 = c->stats.launches;
+  const size_t pending0 = c->pending.size();
+  // capture on the private stream (the handle's stream may be the legacy
+  // one, which cannot be captured); the graph is launched on the handle's
+  if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_st = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  cudaStream_t user_st = c->st;
+  c->st = c->cap_st;
+  bool ok = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess;
+  if (ok) {
+    for (int rep = 0; rep < 2; ++rep) {
+      enqueue_check_seq(c, L, ce, cond);
+      run_steps(c, L, ce, &L.state[0].active, 0);
+    }
+    cudaGraph_t captured = nullptr;
+    ok = cudaStreamEndCapture(c->st, &captured) == cudaSuccess && L.cur == cur0;
+  }
+  c->st = user_st;
+  L.graph_kernels = c->stats.launches - launches0;
+  c->stats.launches = launches0;
+  c->pending.resize(pending0);
+  L.cur = cur0;
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  L.graph = g;
+  L.graph_exec = exec;
+  std::copy(key, key + 6, L.graph_key);
+  return true;
+}
+
 int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
   cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
   launch_state_reset(&L.state[0], 0, c->st);
@@ -511,6 +626,47 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
   int check_id = 0;
   int groups = 2;
   bool done = false;
+  if (c->o.graphs && c->profiling) {
+    // the timed sample: two segments through the stream, every stencil
+    // launch between CUDA events (a graph loop body cannot hold events)
+    for (int i = 0; i < 2 && t + ce <= max_steps; ++i) {
+      enqueue_check(c, L, check_id++, t);
+      run_steps(c, L, ce, &L.state[0].active, t);
+      t += ce;
+    }
+    int rc = cuda_check(c, "evolve launch");
+    if (rc) return rc;
+    if ((rc = read_state(c, L))) return rc;
+    if (!L.host_state.active) done = true;
+  }
+  // full pairs of segments in one graph launch, the convergence check
+  // ending the loop on the device
+  const int64_t pairs = (!done && c->o.graphs) ? std::min<int64_t>((max_steps - t) / (2 * ce), 1 << 28) : 0;
+  if (pairs > 0 && ensure_graph(c, L, ce)) {
+    const int64_t t_end = t + 2 * pairs * ce;
+    launch_state_reset(&L.state[0], 2, c->st, check_id + (int)(2 * pairs));
+    c->stats.launches += 1;
+    cudaGraphLaunch(L.graph_exec, c->st);
+    c->stats.graph_launches += 1;
+    int rc = cuda_check(c, "evolve graph launch");
+    if (rc) return rc;
+    if ((rc = read_state(c, L))) return rc;
+    const LatState& hs = L.host_state;
+    c->stats.launches += (int64_t)((hs.checks - check_id + 1) / 2) * L.graph_kernels;
+    const int64_t advanced = std::max<int64_t>(0, (hs.active ? t_end : hs.step) - t);  // steps taken while active
+    int64_t seg_l;
+    double seg_b;
+    segment_work(c, L, ce, &seg_l, &seg_b);
+    c->stats.stencil_launches += advanced / ce * seg_l;
+    c->stats.stencil_site_updates += advanced * (int64_t)L.n3;
+    c->stats.stencil_bytes += (double)(advanced / ce) * seg_b;
+    if (!hs.active) {
+      done = true;
+    } else {
+      t = t_end;
+      check_id = hs.checks;
+    }
+  }
   int prev_checks = 0;
   double prev_delta = -1.0;
   while (!done) {
@@ -694,6 +850,7 @@ int fdtd_default_options(fdtd_options* o) {
   o->reimpose_parity = 1;
   o->stencil_kernel = 0;
   o->autotune = 1;
+  o->graphs = 1;
   return FDTD_OK;
 }
 
@@ -789,6 +946,8 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
 int fdtd_destroy(fdtd_handle h) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->st);
+  for (auto& L : h->lats) release_graph(L);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
   return FDTD_OK;

@@ -284,10 +284,18 @@ template int launch_sums<__nv_bfloat16>(const __nv_bfloat16*, const void*, const
 // Secs. III-V on thread 0.
 __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __restrict__ parts, int np, int check_id,
                                                   int64_t t, double a3, double v_inf, double tol, int tol_rel,
-                                                  int record) {
+                                                  int record, int seq_ce, cudaGraphConditionalHandle cond,
+                                                  const int32_t* err) {
   pdl_wait();
   pdl_trigger();
-  if (record && s->active == 0) return;
+  const bool seq = seq_ce > 0;
+  if (record && s->active == 0) {
+    if (seq && threadIdx.x == 0) {
+      s->post = 0;
+      cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
   __shared__ double sm[4][256];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < np; i += 256)
@@ -303,15 +311,24 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
+  if (seq) {
+    check_id = s->checks;
+    t = (int64_t)check_id * seq_ce;
+  }
   double s0 = sm[0][0], sh = sm[1][0], sr = sm[2][0], sv = sm[3][0];
   if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(sh) || !isfinite(sr) || !isfinite(sv)) {
     s->status = STATUS_NONFINITE;
     s->active = 0;
     s->scale_seq = -1;
+    if (seq) {
+      s->post = 0;
+      cudaGraphSetConditional(cond, 0u);
+    }
     return;
   }
   s->scale = 1.0 / sqrt(s0 * a3);
   s->scale_seq = check_id;
+  if (seq) s->post = 1;
   if (!record) return;
   double e = sh / s0, eb = e - v_inf;
   s->s0 = s0;
@@ -336,21 +353,33 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
   s->delta_e = d;
   s->e_prev = eb;
   s->has_prev = 1;
+  if (seq) {
+    const bool more = s->active && check_id + 1 < s->seq_limit && *(volatile const int32_t*)err == 0;
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
 }
 
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
-                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st) {
+                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce,
+                     cudaGraphConditionalHandle cond, const int32_t* err) {
   launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol,
-             tol_rel, record);
+             tol_rel, record, seq_ce, cond, err);
 }
 
-__global__ void k_state_reset(LatState* s, int mode) {
+__global__ void k_state_reset(LatState* s, int mode, int seq_limit) {
+  if (mode == 2) {
+    s->post = 0;
+    s->seq_limit = seq_limit;
+    return;
+  }
   if (mode == 1) {
     *s = LatState{};
     s->scale_seq = -1;
     s->delta_e = -1.0;
     return;
   }
+  s->post = 0;
+  s->seq_limit = seq_limit;
   s->has_prev = 0;
   s->active = 1;
   s->converged = 0;
@@ -360,7 +389,9 @@ __global__ void k_state_reset(LatState* s, int mode) {
   s->step = 0;
   s->delta_e = -1.0;
 }
-void launch_state_reset(LatState* s, int mode, cudaStream_t st) { k_state_reset<<<1, 1, 0, st>>>(s, mode); }
+void launch_state_reset(LatState* s, int mode, cudaStream_t st, int seq_limit) {
+  k_state_reset<<<1, 1, 0, st>>>(s, mode, seq_limit);
+}
 
 // ------------------------------------------------------------------ renormalise + symmetry
 // out(site) = sign * scale * in(source): for each masked axis the upper half
@@ -396,7 +427,7 @@ __global__ void __launch_bounds__(256) k_scale_parity(const T* __restrict__ in, 
   using S = typename ScaleT<T>::S;
   S scale = S(1);
   if (s) {
-    if (s->scale_seq != check_id) return;
+    if (check_id < 0 ? s->post != 1 : s->scale_seq != check_id) return;
     scale = (S)s->scale;
   }
   const int x0 = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 8 + threadIdx.y, z0 = blockIdx.z;
@@ -421,7 +452,7 @@ __global__ void __launch_bounds__(256) k_scale_parity_f4(const float* __restrict
   pdl_trigger();
   float scale = 1.0f;
   if (s) {
-    if (s->scale_seq != check_id) return;
+    if (check_id < 0 ? s->post != 1 : s->scale_seq != check_id) return;
     scale = (float)s->scale;
   }
   const int x4 = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;

@@ -98,16 +98,22 @@ void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const 
              (p.n + TXT - 1) / TXT, total, span, p.half_dtau_f, p.one_m6c_f, p.c_f, active, err);
 }
 
-// Blocks of k_step_tma<K, TXT> resident on the whole device at once.
+// Blocks of k_step_tma<K, TXT> resident on the whole device at once
+// (queried once per device).
 template <int K, int TXT>
 int resident_blocks() {
   using G = Geo<K, TXT>;
-  set_smem(k_step_tma<K, TXT>, G::SMEM);
-  int dev = 0, sms = 0, occ = 0;
+  static int cache[64] = {};
+  int dev = 0;
   cudaGetDevice(&dev);
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  set_smem(k_step_tma<K, TXT>, G::SMEM);
+  int sms = 0, occ = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tma<K, TXT>, G::THREADS, G::SMEM);
-  return std::max(1, sms) * std::max(1, occ);
+  const int r = std::max(1, sms) * std::max(1, occ);
+  if (dev < 64) cache[dev] = r;
+  return r;
 }
 
 }  // namespace tb

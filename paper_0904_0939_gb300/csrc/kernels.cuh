@@ -19,7 +19,10 @@ struct LatState {
   double scale;     // 1 / sqrt(S0 a^3) of the last check
   int64_t step;     // t of the last check
   int32_t has_prev, active, converged, status;
-  int32_t checks, scale_seq, cur, pad;
+  int32_t checks, scale_seq, cur;
+  int32_t post;       // device-sequenced checks: 1 if the last finalize posted a factor
+  int32_t seq_limit;  // device-sequenced checks: stop the loop before check seq_limit
+  int32_t pad;
 };
 
 enum : int32_t { STATUS_OK = 0, STATUS_NONFINITE = 1 };
@@ -108,11 +111,19 @@ int sums_blocks(int n);
 
 // Reduce partials, compute E, E_b, <r^2>, the renormalisation factor and
 // the convergence decision.  record = 0: only the scale (for upsample).
+// Device-sequenced mode (seq_ce > 0, inside the evolve graph): the check
+// number is s->checks and its step s->checks * seq_ce, s->post tells the
+// following scale whether a factor was posted, and the graph's while
+// condition `cond` is set to continue only while the lattice is active, no
+// device-side wait has expired (*err == 0) and check + 1 < s->seq_limit.
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
-                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st);
+                     double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce = 0,
+                     cudaGraphConditionalHandle cond = 0, const int32_t* err = nullptr);
 
 // out = P(scale * in): renormalisation and symmetry re-imposition.  With
-// s == nullptr the factor is 1 and the call is unconditional.
+// s == nullptr the factor is 1 and the call is unconditional; otherwise it
+// applies if s->scale_seq == check_id, or, for check_id < 0 (device-
+// sequenced checks), if s->post == 1.
 template <typename T>
 void launch_scale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
                          LatState* s_w, cudaStream_t st);
@@ -133,7 +144,9 @@ template <typename Ti>
 void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, double* vd, double* coefA,
                           double* coefCB, const Params& p, int32_t* flags, cudaStream_t st);
 
-void launch_state_reset(LatState* s, int mode, cudaStream_t st);
+// mode 1: clear everything; mode 0: start of an evolve (keeps the scale);
+// mode 2: only set seq_limit for device-sequenced checks.
+void launch_state_reset(LatState* s, int mode, cudaStream_t st, int seq_limit = 0);
 
 // Snapshot algebra (Sec. III / Sec. VI): block partials of <phi|psi> and
 // <phi|phi> (returns the block count), the ratio on the device, and

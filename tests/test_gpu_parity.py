@@ -326,6 +326,46 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
 
 
+# ------------------------------------------------------------------ evolve graph
+
+@pytest.mark.parametrize("prec,n,kw", [("F32", 64, {}), ("F32", 36, {}), ("F32", 48, dict(temporal_depth=3)),
+                                       ("F64", 24, {}), ("BF16", 32, {})])
+def test_evolve_graph_matches_stream(fd, prec, n, kw):
+    """fdtd_evolve through the CUDA graph whose while loop the convergence
+    check ends on the device gives the stream path's result bit for bit: a
+    run the check stops, a run stopped by max_steps with a remainder after
+    the last full pair of segments, and an evolve continuing from it."""
+    L = 0.3 * n
+    v = wl.harmonic(n, L) + 0.1 * np.cos(wl.radius2(n, L))
+    runs = {}
+    for g in (0, 1):
+        res = []
+        s = solver(fd, n, L, getattr(fd, prec), check_every=50, tol=1e-6, tol_relative=1, graphs=g, **kw)
+        s.set_potential(v)
+        s.init_symmetric(5, wl.ODD_X)
+        res.append(s.evolve(100_000))
+        res.append(s.last_check())
+        res.append(s.get_psi())
+        u = solver(fd, n, L, getattr(fd, prec), check_every=50, tol=0.0, graphs=g, **kw)
+        u.set_potential(v)
+        u.init_symmetric(6, 0)
+        res.append(u.evolve(730))
+        res.append(u.last_check())
+        res.append(u.get_psi())
+        res.append(u.evolve(250))
+        res.append(u.last_check())
+        res.append(u.get_psi())
+        graphs = s.stats()["graph_launches"] + u.stats()["graph_launches"]
+        assert (graphs >= 3) if g else (graphs == 0)
+        runs[g] = res
+    assert runs[0][0][1] and runs[0][0][0] < 100_000  # the first run converged
+    for a, b in zip(runs[0], runs[1]):
+        if isinstance(a, np.ndarray):
+            np.testing.assert_array_equal(a, b)
+        else:
+            assert a == b
+
+
 # ------------------------------------------------------------------ adjoint
 
 @pytest.mark.parametrize("n,mask,T,ce", [(8, 0, 40, 15), (12, wl.ODD_X, 57, 10), (9, wl.SYMMETRIC_ALL, 30, 7)])
