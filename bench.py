@@ -427,6 +427,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="0: every evolve through the stream (for launch lists under ncu)")
     ap.add_argument("--case", default="solve", choices=["solve", "stencil"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=40)
@@ -449,7 +451,7 @@ def main():
     dev = torch.device("cuda", local)
     import paper_0904_0939_gb300 as fd
 
-    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1)
+    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1, graphs=args.graphs)
     seed = SEED + rank
     pots_dev = potentials(True, dev)
     pots_host = potentials(False, dev)
@@ -534,6 +536,7 @@ def main():
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px", "levels": list(LEVELS),
+                   "evolve": "cuda graph (device-side loop)" if args.graphs else "stream",
                    "length": LENGTH, "tol_rel": TOL, "check_every": 100, "precision": "fp32 stencil, fp64 sums",
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

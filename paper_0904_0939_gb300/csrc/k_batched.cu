@@ -27,6 +27,7 @@ namespace fdtd {
 namespace {
 
 constexpr int kTXB = 64;      // tile width of the batched stencil items
+static_assert(kTXB == tb::kSumsTX, "the batched sums use the one-lattice sums partition");
 constexpr int kMaxLat = 256;  // lattices per batched handle
 
 }  // namespace
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const 
       pre_step[l] = b;
       const int n = lats[l].n;
       const int tiles64 = ((n + kTXB - 1) / kTXB) * ((n + tb::TY - 1) / tb::TY);
-      a += tiles64;
+      a += tb::sums_items(n);
       b += tiles64 * ((n + lats[l].step_zc - 1) / lats[l].step_zc);
       s_cur[l] = lats[l].cur;
       s_act[l] = 1;
@@ -221,17 +222,18 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const 
         if (!s_act[l]) continue;
         const BatchLat& L = lats[l];
         const int local = it - pre_sums[l];
-        const int gx = (L.n + kTXB - 1) / kTXB;
+        const int gx = (L.n + kTXB - 1) / kTXB, gy = (L.n + tb::TY - 1) / tb::TY;
+        const int zc = tb::sums_zchunk(L.n), z0 = (local / (gx * gy)) * zc;
         ok = tb::tma_sums_item<kTXB>(smem, &L.sums_map[s_cur[l]], &L.sums_map[2], L.n, (local % gx) * kTXB,
-                                     (local / gx) * tb::TY, 0, L.n, L.a_f, L.kfac_f, L.partials + (size_t)local * 4,
-                                     err);
+                                     ((local / gx) % gy) * tb::TY, z0, min(z0 + zc, L.n), L.a_f, L.kfac_f,
+                                     L.partials + (size_t)local * 4, err);
       }
       if (!ok || !grid_barrier(run, err)) return;
       // ---- FINALIZE
       for (int l = blockIdx.x; l < nlat; l += gridDim.x) {
         if (!s_act[l]) continue;
         const int n = lats[l].n;
-        finalize_lattice(lats[l], ((n + kTXB - 1) / kTXB) * ((n + tb::TY - 1) / tb::TY), check_id, t, *run);
+        finalize_lattice(lats[l], tb::sums_items(n), check_id, t, *run);
       }
       if (!grid_barrier(run, err)) return;
       // ---- SCALE: out = P(scale * in) for lattices checked now (sites dealt grid-wide)

@@ -47,8 +47,6 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   }
 }
 
-constexpr int kSumsTX = 64;
-
 __global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_sums_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                        const __grid_constant__ CUtensorMap map_v,
                                                                        int n, float a, float kfac,
@@ -61,9 +59,10 @@ __global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_sums_tma(const __g
   if (*(volatile const int32_t*)err != 0) return;
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = aligned_smem(smem_raw);
-  const int item = blockIdx.y * gridDim.x + blockIdx.x;
-  tma_sums_item<kSumsTX>(smem, &map_psi, &map_v, n, blockIdx.x * kSumsTX, blockIdx.y * TY, 0, n, a, kfac,
-                         partials + (size_t)item * 4, err);
+  const int item = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int zc = sums_zchunk(n), z0 = blockIdx.z * zc;
+  tma_sums_item<kSumsTX>(smem, &map_psi, &map_v, n, blockIdx.x * kSumsTX, blockIdx.y * TY, z0, min(z0 + zc, n), a,
+                         kfac, partials + (size_t)item * 4, err);
 }
 
 // Opt each kernel in to its dynamic shared memory once per device.
@@ -164,16 +163,17 @@ void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, fl
   }
 }
 
-int tma_sums_blocks(int n) { return ((n + tb::kSumsTX - 1) / tb::kSumsTX) * ((n + tb::TY - 1) / tb::TY); }
+int tma_sums_blocks(int n) { return tb::sums_items(n); }
 
 int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
                     const int32_t* active, int32_t* err, cudaStream_t st) {
   using G = tb::Geo<1, tb::kSumsTX>;
   tb::set_smem(tb::k_sums_tma, G::SMEM);
-  dim3 grid((p.n + tb::kSumsTX - 1) / tb::kSumsTX, (p.n + tb::TY - 1) / tb::TY, 1);
+  const int zc = tb::sums_zchunk(p.n);
+  dim3 grid((p.n + tb::kSumsTX - 1) / tb::kSumsTX, (p.n + tb::TY - 1) / tb::TY, (p.n + zc - 1) / zc);
   launch_pdl(tb::k_sums_tma, grid, dim3(G::THREADS), G::SMEM, st, map_psi, map_v, p.n, (float)p.a,
              (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active, err);
-  return (int)(grid.x * grid.y);
+  return (int)(grid.x * grid.y * grid.z);
 }
 
 void tma_box(int depth, int tx, int* box_w, int* box_h) {
@@ -201,9 +201,11 @@ int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int 
   cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)n * n * 4};
   cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   cuuint32_t estr[3] = {1, 1, 1};
+  // 64 B L2 promotion: a box row (tx + 8 floats) starts 16 B before a tile
+  // boundary, and wider promotion fetches up to twice the row from HBM
   CUresult r = ((Encode)fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -2;
 }
 

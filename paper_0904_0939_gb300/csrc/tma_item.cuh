@@ -386,6 +386,26 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   return true;
 }
 
+// Partition of the lattice sums: 64 x TY tile columns cut along z into
+// chunks of sums_zchunk(n) planes, item (chunk, ty, tx) at index
+// (chunk * gy + ty) * gx + tx.  A function of n only, so every kernel that
+// sums a lattice (one lattice, batched, allocation-free) adds the same
+// partials in the same order: about four items per SM of a 152-SM device,
+// chunks of at least 16 planes, at most 4096 items.
+constexpr int kSumsTX = 64;
+__host__ __device__ inline int sums_zchunk(int n) {
+  const int tiles = ((n + kSumsTX - 1) / kSumsTX) * ((n + TY - 1) / TY);
+  int zs = (608 + tiles - 1) / tiles;
+  const int by_planes = n / 16 > 1 ? n / 16 : 1, by_count = 4096 / tiles > 1 ? 4096 / tiles : 1;
+  zs = zs < by_planes ? zs : by_planes;
+  zs = zs < by_count ? zs : by_count;
+  return (n + zs - 1) / zs;
+}
+__host__ __device__ inline int sums_items(int n) {
+  const int zc = sums_zchunk(n);
+  return ((n + kSumsTX - 1) / kSumsTX) * ((n + TY - 1) / TY) * ((n + zc - 1) / zc);
+}
+
 // Lattice sums over the tile interior, planes [z0, z1); the block's four
 // totals (FP64) go to dst[0..3].  Returns false if a bounded wait expired.
 template <int TXT>
