@@ -83,11 +83,14 @@ struct CoefF {
   float b;      // 1 / (1 + h)
   float alpha;  // 1 - h - 6c
 };
+// Every operation rounds on its own (no contraction), so kernels that
+// evaluate the update with packed two-lane instructions (k_step_tma) agree
+// with the one-site kernels bit for bit.
 __device__ __forceinline__ CoefF coef_f32(float v, float half_dtau, float one_minus_6c) {
-  float h = half_dtau * v;
+  const float h = __fmul_rn(half_dtau, v);
   CoefF k;
-  k.b = rcp_approx(1.0f + h);
-  k.alpha = one_minus_6c - h;
+  k.b = rcp_approx(__fadd_rn(1.0f, h));
+  k.alpha = __fsub_rn(one_minus_6c, h);
   return k;
 }
 __device__ __forceinline__ float nbr_sum(float xm, float xp, float ym, float yp, float zm, float zp) {

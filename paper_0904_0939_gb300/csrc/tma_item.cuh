@@ -146,14 +146,29 @@ __device__ __forceinline__ int slot_add(int sj, int d) {
 __device__ __forceinline__ float4 f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 // One float4 of site updates: c at x..x+3, xl = site x-1, xr = site x+4.
+// The arithmetic of coef_f32 / nbr_sum / update_f32, evaluated on the site
+// pairs (x, x+1) and (x+2, x+3) with packed two-lane FP32 instructions (each
+// lane rounds exactly as the scalar _rn operation); om6c - h is taken as
+// fma(h, -1, om6c), which is the same single rounding.
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float4 update4(float4 c, float xl, float xr, float4 ym, float4 yp, float4 zm, float4 zp,
                                           float4 v, float hd, float om6c, float cc) {
-  float4 o;
-  o.x = update_f32(c.x, nbr_sum(xl, c.y, ym.x, yp.x, zm.x, zp.x), coef_f32(v.x, hd, om6c), cc);
-  o.y = update_f32(c.y, nbr_sum(c.x, c.z, ym.y, yp.y, zm.y, zp.y), coef_f32(v.y, hd, om6c), cc);
-  o.z = update_f32(c.z, nbr_sum(c.y, c.w, ym.z, yp.z, zm.z, zp.z), coef_f32(v.z, hd, om6c), cc);
-  o.w = update_f32(c.w, nbr_sum(c.z, xr, ym.w, yp.w, zm.w, zp.w), coef_f32(v.w, hd, om6c), cc);
-  return o;
+  const float2 hd2 = pr(hd, hd), one2 = pr(1.0f, 1.0f), m1 = pr(-1.0f, -1.0f), om2 = pr(om6c, om6c), cc2 = pr(cc, cc);
+  const float2 c0 = pr(c.x, c.y), c1 = pr(c.z, c.w);
+  // ((xm + xp) + (ym + yp)) + (zm + zp) per site
+  const float2 s0 = __fadd2_rn(__fadd2_rn(__fadd2_rn(pr(xl, c.x), pr(c.y, c.z)), __fadd2_rn(pr(ym.x, ym.y), pr(yp.x, yp.y))),
+                               __fadd2_rn(pr(zm.x, zm.y), pr(zp.x, zp.y)));
+  const float2 s1 = __fadd2_rn(__fadd2_rn(__fadd2_rn(pr(c.y, c.z), pr(c.w, xr)), __fadd2_rn(pr(ym.z, ym.w), pr(yp.z, yp.w))),
+                               __fadd2_rn(pr(zm.z, zm.w), pr(zp.z, zp.w)));
+  // h = hd V, b = 1 / (1 + h), alpha = (1 - 6c) - h
+  const float2 h0 = __fmul2_rn(hd2, pr(v.x, v.y)), h1 = __fmul2_rn(hd2, pr(v.z, v.w));
+  const float2 q0 = __fadd2_rn(one2, h0), q1 = __fadd2_rn(one2, h1);
+  const float2 b0 = pr(rcp_approx(q0.x), rcp_approx(q0.y)), b1 = pr(rcp_approx(q1.x), rcp_approx(q1.y));
+  const float2 a0 = __ffma2_rn(h0, m1, om2), a1 = __ffma2_rn(h1, m1, om2);
+  // psi' = b (c S + alpha psi)
+  const float2 o0 = __fmul2_rn(b0, __ffma2_rn(cc2, s0, __fmul2_rn(a0, c0)));
+  const float2 o1 = __fmul2_rn(b1, __ffma2_rn(cc2, s1, __fmul2_rn(a1, c1)));
+  return make_float4(o0.x, o0.y, o1.x, o1.y);
 }
 
 // The ring pipeline: barriers, prologue, and the bounded waits; the body
