@@ -209,3 +209,82 @@ def test_paper_antisymmetric_z_second_state_by_projection(fd):
     s.project_out([1])
     e2 = s.observables()["binding_energy"]
     assert e2 == pytest.approx(g["E2"], abs=5e-4)
+
+
+def _coulomb_multires(fd, sizes, length, mask, tol):
+    """Multi-resolution bootstrap (Sec. VI) on the Coulomb potential of
+    Eq. coulombpot, FP32, dtau = a^2/4 and V_inf = 1/a on every level."""
+    import torch
+
+    levels = [fd.Lattice(n, length, fd.F32, v_inf=n / length) for n in sizes]
+    pots = [wl.coulomb_paper_device(n, length, "cuda", torch.float32) for n in sizes]
+    opts = fd.default_options(check_every=100, tol=tol, tol_relative=1)
+    out = fd.multires(levels, pots, mask=mask, options=opts, max_steps=400_000)
+    for s, _ in out:
+        s.close()
+    return [o for _, o in out]
+
+
+def test_paper_coulomb_512_ground_and_first_excited(fd):
+    """Sec. VII.C: Coulomb potential of Eq. coulombpot on 512^3, a = 0.05,
+    dtau = a^2/4 = 6.25e-4, m = 1: binding energies E0 = -0.499 (0.2 % from
+    -1/2) and E1 = -0.122 (2.4 % from -1/8).  Reached here by the
+    multi-resolution bootstrap from 128^3 -- the lattice eigenvalue does not
+    depend on the start -- with the A_z sector (Sec. IV) for E1.  The A_z
+    sector gives the lattice 2p level itself, much closer to -1/8 than the
+    printed E1, which the text quotes as 2.4 % off (a snapshot estimate); E1
+    is held to that accuracy bound and E0 to the printed digits."""
+    g = paper("coulomb_512")
+    length = g["n"] * g["a"]
+    obs0 = _coulomb_multires(fd, (128, 256, 512), length, wl.SYMMETRIC_ALL, 1e-6)[-1]
+    obs1 = _coulomb_multires(fd, (128, 256, 512), length, wl.ODD_Z, 1e-6)[-1]
+    print(f"Coulomb 512^3 a=0.05: E0 = {obs0['binding_energy']:.6f}, E1 = {obs1['binding_energy']:.6f}")
+    assert obs0["converged"] and obs1["converged"]
+    assert obs0["binding_energy"] == pytest.approx(g["E0"], abs=1e-3)
+    assert abs(obs1["binding_energy"] + 0.125) <= abs(g["E1"] + 0.125)
+
+
+def test_paper_multires_coulomb_1024(fd):
+    """Sec. VII.G: bootstrapping 128^3 -> 256^3 -> 512^3 -> 1024^3 at fixed
+    L = 25.6 (final a = 0.025) gives E0 = -0.499632; each level stops when
+    E_b changes by less than a part in 10^6 between checks, which leaves the
+    fine level within ~5e-5 of its limit."""
+    g = paper("multires_1024")
+    obs = _coulomb_multires(fd, (128, 256, 512, 1024), g["L"], wl.SYMMETRIC_ALL, 1e-6)
+    print("multires Coulomb: " + ", ".join(f"{n}^3 E = {o['binding_energy']:.6f} ({o['steps']} steps)"
+                                           for n, o in zip((128, 256, 512, 1024), obs)))
+    assert all(o["converged"] for o in obs)
+    assert obs[-1]["binding_energy"] == pytest.approx(g["E0"], abs=1e-4)
+    # the levels approach the continuum -1/2 from above as a shrinks
+    e = [o["binding_energy"] for o in obs]
+    assert e[0] > e[1] > e[2] > e[3] > -0.5
+
+
+def test_paper_dodecahedron_first_excited_128(fd):
+    """Sec. VII.E: ground and first excited levels of the dodecahedral well
+    (128^3, a = 0.1, dtau = 0.001), the excited one from the A_x, A_y and
+    A_z sectors (Sec. IV).  The paper prints E0 = -99.78 and E1 = -99.55;
+    the regular solid the text specifies (circumradius sqrt(3)(N-1)/(2 phi)
+    sites) puts both lower, as if the printed well were ~0.82 of its linear
+    size, so this test checks what does not depend on the size: the ratio of
+    the two levels above the well floor (printed: 0.45 / 0.22 = 2.05) and the
+    threefold degeneracy of the p-like level that the solid's x -> y -> z
+    symmetry gives."""
+    g = paper("dodecahedron_128")
+    n, a = g["n"], g["a"]
+    v = wl.dodecahedron(n).astype(np.float32)
+    e = {}
+    for mask in (0, wl.ODD_X, wl.ODD_Y, wl.ODD_Z):
+        s = fd.Solver(fd.Lattice(n, n * a, fd.F32, dtau=g["dtau"]),
+                      fd.default_options(check_every=100, tol=1e-8, tol_relative=1))
+        s.set_potential(v)
+        s.init_symmetric(3, mask)
+        steps, conv = s.evolve(400_000)
+        assert conv
+        e[mask] = s.last_check()["energy"]
+        s.close()
+    e0, e1 = e[0], e[wl.ODD_X]
+    print(f"dodecahedron 128^3: E0 = {e0:.5f}, E1 = {e1:.5f} / {e[wl.ODD_Y]:.5f} / {e[wl.ODD_Z]:.5f} (A_x/A_y/A_z)")
+    floor = -100.0
+    assert (e1 - floor) / (e0 - floor) == pytest.approx((g["E1"] - floor) / (g["E0"] - floor), rel=0.03)
+    assert e[wl.ODD_Y] == pytest.approx(e1, abs=2e-4) and e[wl.ODD_Z] == pytest.approx(e1, abs=2e-4)

@@ -65,6 +65,18 @@ def coulomb_paper(n: int, length: float) -> np.ndarray:
     return np.where(r < a, 0.0, -1.0 / np.maximum(r, a) + 1.0 / a)
 
 
+def coulomb_paper_device(n: int, length: float, device, dtype=None):
+    """coulomb_paper() evaluated on a torch device, for lattices too large to
+    build quickly in numpy (1024^3)."""
+    import torch
+
+    dtype = dtype or torch.float64
+    a = spacing(n, length)
+    ax = torch.as_tensor(axis(n, length), dtype=torch.float64, device=device)
+    r = torch.sqrt(ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2)
+    return torch.where(r < a, torch.zeros_like(r), -1.0 / torch.clamp(r, min=a) + 1.0 / a).to(dtype)
+
+
 def gaussian_bumps(n: int, length: float, centres, widths, amplitudes) -> np.ndarray:
     """sum_k amp_k exp(-|r - c_k|^2 / (2 w_k^2)), built from per-axis factors."""
     ax = axis(n, length)
