@@ -80,20 +80,25 @@ struct Lat {
   // plain = the one-step z-marching kernel (bit-identical) was timed fastest
   int depth = 0, tx = 128, zc = 0;
   bool plain = false;
-  // evolve graph: a while loop over pairs of (check, check_every steps),
-  // built for one start buffer, mask and stencil configuration
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  int64_t graph_key[6] = {-1, -1, -1, -1, -1, -1};
+  // evolve graphs: a while loop over pairs of (check, check_every steps),
+  // one per start buffer (an evolve ends on either), each built for a mask,
+  // stencil configuration and cadence
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int64_t graph_key[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
   int64_t graph_kernels = 0;  // kernels per loop iteration
 };
 
+void release_graph(Lat& L, int b) {
+  if (L.graph_exec[b]) cudaGraphExecDestroy(L.graph_exec[b]);
+  if (L.graph[b]) cudaGraphDestroy(L.graph[b]);
+  L.graph_exec[b] = nullptr;
+  L.graph[b] = nullptr;
+  L.graph_key[b][0] = -1;
+}
 void release_graph(Lat& L) {
-  if (L.graph_exec) cudaGraphExecDestroy(L.graph_exec);
-  if (L.graph) cudaGraphDestroy(L.graph);
-  L.graph_exec = nullptr;
-  L.graph = nullptr;
-  L.graph_key[0] = -1;
+  release_graph(L, 0);
+  release_graph(L, 1);
 }
 
 struct Carve {
@@ -253,7 +258,8 @@ struct fdtd_context {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   int check_seq = 0;
-  cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured on
+  cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured and launched on
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order cap_st after / before the handle's stream
   // stencil launches not yet credited to the stats: a launch enqueued past
   // the check at which its lattice converged runs as a no-op and is dropped
   struct Pending {
@@ -551,9 +557,10 @@ void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, 
 bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   choose_config(c, L);  // autotuning synchronises: never inside a capture
   const int mask = c->o.reimpose_parity ? L.mask : 0;
+  const int b = L.cur;
   const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain, ce};
-  if (L.graph_exec && std::equal(key, key + 6, L.graph_key)) return true;
-  release_graph(L);
+  if (L.graph_exec[b] && std::equal(key, key + 6, L.graph_key[b])) return true;
+  release_graph(L, b);
   if (L.tma_ok && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
     (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx);  // occupancy query outside the capture
   cudaGraph_t g = nullptr;
@@ -606,14 +613,19 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   L.cur = cur0;
   cudaGraphExec_t exec = nullptr;
   if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (ok && !c->ev_in) {
+    ok = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphUpload(exec, c->cap_st) == cudaSuccess;
   if (!ok) {
     cudaGraphDestroy(g);
     cudaGetLastError();
     return false;
   }
-  L.graph = g;
-  L.graph_exec = exec;
-  std::copy(key, key + 6, L.graph_key);
+  L.graph[b] = g;
+  L.graph_exec[b] = exec;
+  std::copy(key, key + 6, L.graph_key[b]);
   return true;
 }
 
@@ -646,7 +658,14 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
     const int64_t t_end = t + 2 * pairs * ce;
     launch_state_reset(&L.state[0], 2, c->st, check_id + (int)(2 * pairs));
     c->stats.launches += 1;
-    cudaGraphLaunch(L.graph_exec, c->st);
+    // launched on the private stream, ordered after and before the handle's
+    // stream by events (a graph launched into the legacy stream paid about
+    // half a millisecond per launch)
+    cudaEventRecord(c->ev_in, c->st);
+    cudaStreamWaitEvent(c->cap_st, c->ev_in, 0);
+    cudaGraphLaunch(L.graph_exec[L.cur], c->cap_st);
+    cudaEventRecord(c->ev_out, c->cap_st);
+    cudaStreamWaitEvent(c->st, c->ev_out, 0);
     c->stats.graph_launches += 1;
     int rc = cuda_check(c, "evolve graph launch");
     if (rc) return rc;
@@ -948,6 +967,8 @@ int fdtd_destroy(fdtd_handle h) {
   cudaStreamSynchronize(h->st);
   for (auto& L : h->lats) release_graph(L);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
   return FDTD_OK;
