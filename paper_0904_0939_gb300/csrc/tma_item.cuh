@@ -267,6 +267,13 @@ struct StepCtx {
 // windows rotate by renaming instead of moving.  After level l computes
 // its new plane into w[l][ROT], the window reads zm = w[(ROT+1)%3],
 // c = w[(ROT+2)%3], zp = w[ROT].
+//
+// Sites outside the lattice must read as zero at every level.  The level
+// planes and windows start each item at zero, so a site is simply never
+// written when it lies outside the lattice in x or y (the thread does not
+// compute) or below it in z (p < 0 comes first in an item); above it
+// (p >= n, block-uniform) zeros are written.  The last level computes only
+// the planes it stores.
 template <int K, int TXT, int ROT>
 __device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int j, int sj,
                                                float4 (&w)[K > 1 ? K - 1 : 1][3]) {
@@ -281,48 +288,58 @@ __device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K,
     const float* bm = pp.box(slot_add<R>(sj, -1));
     const float* bp = pp.box(slot_add<R>(sj, 1));
     const int p = j;
-    const bool need = x.owner && (x.row >= 1 && x.row < G::BH - 1) && (K > 1 || x.interior_col);
+    const bool need = x.inside && (x.row >= 1 && x.row < G::BH - 1) && (K > 1 || x.interior_col);
     float4 c = x.owner ? f4(b0 + x.ro) : zero4;
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
     if (x.fix_l) xl = b0[x.ro - 1];
     if (x.fix_r) xr = b0[x.ro + 4];
-    if (need) {
-      float4 r = update4(c, xl, xr, f4(b0 + x.ro - BW), f4(b0 + x.ro + BW), f4(bm + x.ro), f4(bp + x.ro),
-                         f4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
-      if (!x.inside || p < 0 || p >= x.n) r = zero4;
-      if constexpr (K == 1) {
-        if (x.interior_row && x.inside && p >= x.z0 && p < x.z1)
-          *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = r;
-      } else {
-        *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = r;
-        w[0][I0] = r;
+    auto upd = [&]() {
+      return update4(c, xl, xr, f4(b0 + x.ro - BW), f4(b0 + x.ro + BW), f4(bm + x.ro), f4(bp + x.ro),
+                     f4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
+    };
+    if constexpr (K == 1) {
+      if (need && x.interior_row && p >= x.z0 && p < x.z1)
+        *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = upd();
+    } else if (p >= x.n) {
+      if (need) {
+        *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = zero4;
+        w[0][I0] = zero4;
       }
+    } else if (p >= 0 && need) {
+      const float4 r = upd();
+      *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = r;
+      w[0][I0] = r;
     }
   }
   // ---- levels 2..K: plane j - l + 1 from level l-1
 #pragma unroll
   for (int l = 2; l <= K; ++l) {
     const int p = j - l + 1;
-    const bool need = x.owner && (x.row >= l && x.row < G::BH - l) && (l < K || x.interior_col);
+    const bool need = x.inside && (x.row >= l && x.row < G::BH - l) && (l < K || x.interior_col);
     const float* lp = x.lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
     const float4 c = w[l - 2][I2];
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
     if (x.fix_l) xl = lp[x.lo - 1];
     if (x.fix_r) xr = lp[x.lo + 4];
-    if (need) {
+    auto upd = [&]() {
       const float4 v = f4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + x.ro);
-      float4 r = update4(c, xl, xr, f4(lp + x.lo - LW), f4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v, x.hd,
-                         x.om6c, x.cc);
-      if (!x.inside || p < 0 || p >= x.n) r = zero4;
-      if (l == K) {
-        if (x.interior_row && x.inside && p >= x.z0 && p < x.z1)
-          *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = r;
-      } else {
-        *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = r;
-        w[l - 1][I0] = r;
+      return update4(c, xl, xr, f4(lp + x.lo - LW), f4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v, x.hd,
+                     x.om6c, x.cc);
+    };
+    if (l == K) {
+      if (need && x.interior_row && p >= x.z0 && p < x.z1)
+        *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = upd();
+    } else if (p >= x.n) {
+      if (need) {
+        *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = zero4;
+        w[l - 1][I0] = zero4;
       }
+    } else if (p >= 0 && need) {
+      const float4 r = upd();
+      *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = r;
+      w[l - 1][I0] = r;
     }
   }
 }
