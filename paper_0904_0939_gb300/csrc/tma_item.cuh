@@ -25,7 +25,7 @@
 //
 // Every mbarrier wait is bounded in wall-clock time; on expiry the item
 // sets *err, waits (bounded) for its copies in flight and returns false in
-// every thread (block-wide vote).
+// every thread (a shared flag read by all after the z-step's barrier).
 #pragma once
 #include <cuda.h>
 
@@ -58,7 +58,8 @@ struct Geo {
   static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;     // bytes the two box loads deliver
   static constexpr size_t LEVEL_OFF = RING_OFF + R * SLOT_BYTES + 128;
   static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)(K > 1 ? K - 1 : 0) * 2 * LPLANE * 4;
-  static constexpr size_t RED_OFF = BAR_OFF + 8 * R;         // block reduction scratch (sums)
+  static constexpr size_t FLAG_OFF = BAR_OFF + 8 * R;        // "a wait expired" word of the item
+  static constexpr size_t RED_OFF = FLAG_OFF + 8;            // block reduction scratch (sums)
   static constexpr size_t SMEM = RED_OFF + 8 * 4 * (THREADS / 32) + 128;  // + base alignment slack
 };
 
@@ -184,6 +185,7 @@ struct Pipe {
   const int32_t* err;
   long long budget = 0;  // wall-clock wait budget in ns (< 0: do not wait)
   uint64_t* bars;
+  int* flag;  // shared: set by any thread whose wait expired, read by all after the barrier
   float* ring;
   unsigned phase = 0;        // bit s: parity of the next wait on slot s (toggled on success)
   unsigned outstanding = 0;  // (thread 0) slots with a copy in flight
@@ -208,9 +210,11 @@ struct Pipe {
   // Set up barriers and issue planes j0-1 .. min(j0+D, jlast) into slots 0, 1, ...
   __device__ __forceinline__ void begin(int j0, int jlast) {
     bars = (uint64_t*)(smem + G::BAR_OFF);
+    flag = (int*)(smem + G::FLAG_OFF);
     ring = (float*)(smem + G::RING_OFF);
     budget = wait_budget_ns(err);
     if (threadIdx.x == 0) {
+      *(volatile int*)flag = 0;
       for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -225,15 +229,24 @@ struct Pipe {
   }
   // Start of iteration j (slot sj): prefetch plane j+1+D, wait for plane j+1.
   __device__ __forceinline__ void advance(int j, int sj, int jlast) {
-    if (threadIdx.x == 0 && j + 1 + D <= jlast) {
+    if (threadIdx.x == 0 && !timeout && j + 1 + D <= jlast) {  // no new copy after an expired wait
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(j + 1 + D, slot_add<R>(sj, 1 + D));
     }
     wait(slot_add<R>(sj, 1));
   }
-  // End of iteration: barrier + vote; on a timeout drain and report.
-  __device__ __forceinline__ bool end_iteration(int32_t* err_w) {
-    if (__syncthreads_or(timeout)) {
+  // End of a z-step: a thread whose wait expired marks the shared flag and
+  // the barrier publishes it.
+  __device__ __forceinline__ void end_step() {
+    if (timeout) *(volatile int*)flag = 1;
+    __syncthreads();
+  }
+  // After a barrier: every thread reads the same flag; on a timeout drain
+  // and report.  Step items read it once per three z-steps (the steps run
+  // in between on whatever the ring holds, in bounds, and the item's output
+  // is discarded), which keeps the unrolled loop free of exits.
+  __device__ __forceinline__ bool ok(int32_t* err_w) {
+    if (*(volatile const int*)flag) {
       if (threadIdx.x == 0) {
         atomicOr(err_w, 1);
         for (int s = 0; s < R; ++s) {
@@ -398,24 +411,26 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
 
   int sj = 1;  // slot of plane j (plane j0 sits in slot 1)
   int j = j0;
-  auto one = [&](auto rot) -> bool {
+  auto one = [&](auto rot) {
     constexpr int ROT = decltype(rot)::value;
     pp.advance(j, sj, j1 + 1);
     step_iteration<K, TXT, ROT>(x, pp, j, sj, w);
-    if (!pp.end_iteration(err)) return false;
+    pp.end_step();
     sj = slot_add<R>(sj, 1);
     ++j;
-    return true;
   };
   using R0 = std::integral_constant<int, 0>;
   using R1 = std::integral_constant<int, 1>;
   using R2 = std::integral_constant<int, 2>;
   while (j + 2 <= j1) {
-    if (!one(R0{}) || !one(R1{}) || !one(R2{})) return false;
+    one(R0{});
+    one(R1{});
+    one(R2{});
+    if (!pp.ok(err)) return false;
   }
-  if (j <= j1 && !one(R0{})) return false;
-  if (j <= j1 && !one(R1{})) return false;
-  return true;
+  if (j <= j1) one(R0{});
+  if (j <= j1) one(R1{});
+  return pp.ok(err);
 }
 
 // Partition of the lattice sums: 64 x TY tile columns cut along z into
@@ -506,7 +521,8 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
         sv.add(vs[i] * c2);
       }
     }
-    if (!pp.end_iteration(err)) return false;
+    pp.end_step();
+    if (!pp.ok(err)) return false;
     sj = slot_add<R>(sj, 1);
   }
   // fixed-order block reduction
