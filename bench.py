@@ -261,25 +261,38 @@ def batched_run(fd, dev, seed):
     lats = wl.config_batch()
     opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1, batched=1)
     s = fd.Solver([fd.Lattice(l.n, l.length, fd.F32) for l in lats], opts)
-    for i, l in enumerate(lats):
-        s.set_potential(torch.from_numpy(l.potential().astype(np.float32)).to(dev), lat=i)
-        s.init_symmetric(seed, l.mask, lat=i)
+    pots = [torch.from_numpy(l.potential().astype(np.float32)).to(dev) for l in lats]
+
+    def start():
+        for i, l in enumerate(lats):
+            s.set_potential(pots[i], lat=i)
+            s.init_symmetric(seed, l.mask, lat=i)
+
+    # first solve: the autotuner times its candidates on slices of the run
+    # and keeps the fastest; the timed solve uses it in one launch
+    start()
+    s.evolve(200_000)
+    start()
+    s.reset_stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     steps, conv = s.evolve(200_000)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    graph_launches = s.stats()["graph_launches"]
     upd = 0
     worst = 0
     for i, l in enumerate(lats):
         o = s.last_check(lat=i)
         upd += l.n**3 * o["steps"]
         worst = max(worst, o["steps"])
+    tuned = s.tuned_config()
     s.close()
     return {"lattices": len(lats), "sites": int(sum(l.n**3 for l in lats)), "site_updates": upd, "ms": ms,
             "gsite_per_s": upd / (ms * 1e-3) / 1e9, "max_steps_taken": worst, "all_converged": bool(conv),
-            "launches": 1}
+            "launches": graph_launches, "launch": "cooperative kernel in a CUDA graph",
+            "tuned": tuned}
 
 
 class Clocks:

@@ -94,7 +94,12 @@ typedef struct {
   double tol;             /* convergence tolerance; <= 0 never converges */
   int32_t temporal_depth; /* FP32/BF16 steps fused per stencil launch; 0 = auto */
   int32_t backward_steps; /* largest T that fdtd_backward may be asked for; 0 = none */
-  int32_t batched;        /* 1: all lattices of the handle advance in one persistent launch */
+  int32_t batched;        /* 1: all lattices of the handle advance in one persistent launch (a
+                             cooperative kernel in a CUDA graph); with autotune and no
+                             temporal_depth, the first evolve of a set of lattice sizes times
+                             (depth 1..3) x (16/32/64 z-planes per item) on slices of
+                             2 x check_every steps of the run itself and finishes with the
+                             fastest (cached; identical results for every choice) */
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
   int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
                              (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
@@ -233,7 +238,8 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
 /* Stencil configuration in use for lattice `lat` (after autotuning, if on):
  * temporal depth (steps per launch) and the span (tile planes per block,
  * options.zchunk) of the TMA kernel; zchunk = 0 (depth 1) when the one-step
- * z-marching kernel is in use. */
+ * z-marching kernel is in use.  For a batched handle after an evolve: the
+ * depth and z-planes per item of its persistent launch. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
 /* Snapshots (Sec. III): full copies of psi kept in the workspace, in

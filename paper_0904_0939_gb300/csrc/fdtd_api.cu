@@ -258,6 +258,8 @@ struct fdtd_context {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   int check_seq = 0;
+  BatchedGraphs batch_graphs;     // graphs of the batched persistent launch
+  int batch_depth = 0, batch_zc = 0;  // configuration of the last batched evolve
   cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured and launched on
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order cap_st after / before the handle's stream
   // stencil launches not yet credited to the stats: a launch enqueued past
@@ -794,47 +796,125 @@ int export_field(fdtd_context* c, const void* src, int prec, void* dst, int dt, 
 }
 
 // All lattices in one persistent launch (k_batched.cu).
+// Batched configurations already chosen, by device and lattice sizes.
+std::mutex g_btune_mu;
+std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_btune;
+
+// All lattices of the handle in persistent launches.  With autotuning on
+// (and no depth given) the first launches of a new set of lattice sizes are
+// slices of 2 x check_every steps, one per (depth 1..3, z-chunk 16/32/64)
+// candidate, timed with CUDA events; the fastest runs the rest in one
+// launch.  Every candidate computes the same bits, so tuning costs no extra
+// work, only launch boundaries.
 int evolve_batched(fdtd_context* c, int64_t max_steps) {
   const int count = (int)c->lats.size();
   if (count > batched_max_lattices()) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: too many lattices for batched mode");
   for (auto& L : c->lats)
     if (!L.tma_ok) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: batched mode needs FP32 lattices with n % 4 == 0");
-  int depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : 2;
-  std::vector<char> table(batched_entry_bytes() * count + 64);
-  char* base = table.data() + ((64 - ((uintptr_t)table.data() & 63)) & 63);
-  for (int l = 0; l < count; ++l) {
-    Lat& L = c->lats[l];
-    if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
-                     (const float*)L.v, L.partials, &L.state[0], L.p, L.mask, L.cur, L.d.v_inf, depth))
-      return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
+  const int64_t ce = c->o.check_every;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> sizes;
+  for (auto& L : c->lats) sizes.push_back(L.d.n);
+  const auto key = std::make_pair(dev, sizes);
+  std::vector<std::pair<int, int>> cands;  // (depth, z-chunk)
+  if (c->o.temporal_depth > 0 || !c->o.autotune) {
+    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, c->o.zchunk > 0 ? c->o.zchunk : 32});
+  } else {
+    std::lock_guard<std::mutex> lock(g_btune_mu);
+    auto it = g_btune.find(key);
+    if (it != g_btune.end()) {
+      cands.push_back(it->second);
+    } else {
+      for (int d = 1; d <= 3; ++d)
+        for (int zc : {16, 32, 64}) cands.push_back({d, zc});
+    }
+  }
+  const bool tuning = cands.size() > 1;
+  for (auto& L : c->lats) {
     launch_state_reset(&L.state[0], 0, c->st);
     c->stats.launches += 1;
   }
   cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
-  cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
-  int64_t steps = 0;
-  int grid = 0;
-  const long bev = prof_begin(c);
-  int e = batched_launch(c->batch_ws, count, max_steps, c->o.check_every, c->o.tol, c->o.tol_relative,
-                         c->o.reimpose_parity, depth, c->flags + 1, c->st, &steps, &grid);
-  prof_end(c);
-  if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
-  c->stats.launches += 1;
-  int rc = cuda_check(c, "evolve (batched)");
-  if (rc) return rc;
-  for (auto& L : c->lats) {
-    if ((rc = read_state(c, L))) return rc;
-    if (L.host_state.status == STATUS_NONFINITE)
-      return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
-    L.cur = L.host_state.cur;
-    L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
-    c->pending.push_back({0, (int64_t)L.n3 * L.last_steps, (double)L.n3 * 12.0 * ((L.last_steps + depth - 1) / depth),
-                          -1});
+  std::vector<char> table(batched_entry_bytes() * count + 64);
+  char* base = table.data() + ((64 - ((uintptr_t)table.data() & 63)) & 63);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int64_t t = 0, steps = 0, slices = 0;
+  double best_rate = -1.0;
+  std::pair<int, int> best = cands[0];
+  std::vector<int64_t> step_at(count, 0);  // steps each lattice advanced while active
+  int rc = FDTD_OK;
+  auto slice = [&](std::pair<int, int> cd, int64_t t_end) -> int {
+    for (int l = 0; l < count; ++l) {
+      Lat& L = c->lats[l];
+      if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
+                       (const float*)L.v, L.partials, &L.state[0], L.p, L.mask, L.cur, L.d.v_inf, cd.second))
+        return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
+    }
+    cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
+    int grid = 0;
+    cudaEventRecord(e0, c->st);
+    int e = batched_launch(c->batch_ws, count, max_steps, t, t_end, t > 0, 0, (int)ce, c->o.tol, c->o.tol_relative,
+                           c->o.reimpose_parity, cd.first, c->flags + 1, c->st, &c->batch_graphs, &steps, &grid);
+    cudaEventRecord(e1, c->st);
+    if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
+    c->stats.launches += 1;
+    c->stats.graph_launches += 1;
+    ++slices;
+    int r = cuda_check(c, "evolve (batched)");
+    if (r) return r;
+    double upd = 0.0;
+    for (int l = 0; l < count; ++l) {
+      Lat& L = c->lats[l];
+      const bool was_active = L.host_state.active || t == 0;
+      if ((r = read_state(c, L))) return r;
+      if (L.host_state.status == STATUS_NONFINITE)
+        return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+      L.cur = L.host_state.cur;
+      if (was_active) {
+        const int64_t upto = L.host_state.active ? steps : L.host_state.step;
+        upd += (double)L.n3 * (double)std::max<int64_t>(0, upto - t);
+        step_at[l] = std::max(step_at[l], upto);
+      }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c->profiling) c->stats.stencil_ms += ms;
+    const double rate = ms > 0.f ? upd / ms : 0.0;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = cd;
+    }
+    t = steps;
+    return FDTD_OK;
+  };
+  bool any = true;
+  for (size_t i = 0; tuning && i < cands.size() && any && t < max_steps; ++i) {
+    if ((rc = slice(cands[i], std::min<int64_t>(max_steps, t + 2 * ce)))) break;
+    any = false;
+    for (auto& L : c->lats) any |= L.host_state.active != 0;
   }
-  // the persistent launch is one timed unit: credit its time once
-  if (!c->pending.empty()) c->pending[0].ev = bev;
-  flush_pending(c, INT64_MAX);
-  c->stats.stencil_launches += 1 - (int64_t)c->lats.size();
+  if (!rc && tuning && best_rate > 0.0) {
+    std::lock_guard<std::mutex> lock(g_btune_mu);
+    g_btune[key] = best;
+  }
+  if (!rc && any && t < max_steps) rc = slice(best, max_steps);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  // the persistent launches are the stencil launches of a batched evolve
+  for (int l = 0; l < count; ++l) {
+    Lat& L = c->lats[l];
+    L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+    c->stats.stencil_site_updates += (int64_t)L.n3 * step_at[l];
+    c->stats.stencil_bytes += (double)L.n3 * 12.0 * ((step_at[l] + best.first - 1) / best.first);
+  }
+  c->stats.stencil_launches += slices;
+  if (c->profiling) c->stats.stencil_timed_launches += slices;
+  c->batch_depth = best.first;
+  c->batch_zc = best.second;
   return FDTD_OK;
 }
 
@@ -966,6 +1046,7 @@ int fdtd_destroy(fdtd_handle h) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->st);
   for (auto& L : h->lats) release_graph(L);
+  h->batch_graphs.release();
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -1371,6 +1452,11 @@ int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
   if (rc) return rc;
   if (!depth || !zchunk) return fail(h, FDTD_ERR_INVALID_ARG, "tuned_config: null output");
   Lat& L = h->lats[lat];
+  if (h->o.batched && h->batch_depth) {  // the persistent launch's choice
+    *depth = h->batch_depth;
+    *zchunk = h->batch_zc;
+    return FDTD_OK;
+  }
   if (L.has_v && L.has_psi) choose_config(h, L);
   *depth = L.depth;
   *zchunk = L.plain ? 0 : L.zc;

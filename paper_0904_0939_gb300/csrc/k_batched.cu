@@ -46,9 +46,9 @@ struct alignas(64) BatchLat {
 };
 
 struct BatchRun {
-  int64_t max_steps;
+  int64_t max_steps, t_start, t_end;
   double tol;
-  int check_every, tol_rel, reimpose, depth, nlat, pad;
+  int check_every, tol_rel, reimpose, depth, nlat, skip_first, check0, pad;
   unsigned bar_count, bar_gen;
   int64_t steps_done;
 };
@@ -205,17 +205,18 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const 
       a += tb::sums_items(n);
       b += tiles64 * ((n + lats[l].step_zc - 1) / lats[l].step_zc);
       s_cur[l] = lats[l].cur;
-      s_act[l] = 1;
+      s_act[l] = lats[l].state->active;  // a lattice that converged in an earlier slice stays retired
     }
     pre_sums[nlat] = a;
     pre_step[nlat] = b;
   }
   __syncthreads();
   bool ok = true;
-  int64_t t = 0;
-  int check_id = 0;
+  const int64_t t_start = run->t_start, t_end = run->t_end;
+  int64_t t = t_start;
+  int check_id = run->check0;
   for (;;) {
-    if (t % ce == 0 || t == max_steps) {
+    if ((t % ce == 0 || t == max_steps) && !(run->skip_first && t == t_start)) {
       // ---- SUMS
       for (int it = blockIdx.x; it < pre_sums[nlat] && ok; it += gridDim.x) {
         const int l = find_lattice(pre_sums, nlat, it);
@@ -284,11 +285,11 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const 
       ++check_id;
       int any = 0;
       for (int l = 0; l < nlat; ++l) any |= s_act[l];
-      if (t >= max_steps || !any) break;
+      if (t >= t_end || !any) break;
     }
     // ---- STEP: up to the next check, KMAX steps per phase
     const int64_t nc = (t / ce + 1) * ce;
-    const int64_t next = nc < max_steps ? nc : max_steps;
+    const int64_t next = nc < t_end ? nc : t_end;
     while (t < next) {
       const int k = (int)((next - t) < KMAX ? (next - t) : KMAX);
       for (int it = blockIdx.x; it < pre_step[nlat] && ok; it += gridDim.x) {
@@ -330,7 +331,7 @@ size_t batched_smem() {
 int batched_max_lattices() { return kMaxLat; }
 
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
-                 LatState* state, const Params& p, int mask, int cur, double v_inf, int depth) {
+                 LatState* state, const Params& p, int mask, int cur, double v_inf, int zc) {
   BatchLat& B = *(BatchLat*)host_entry;
   int bw, bh;
   const float* bufs[3] = {psi0, psi1, v};
@@ -348,8 +349,7 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
   B.state = state;
   B.n = p.n;
   B.mask = mask;
-  B.step_zc = p.n < 32 ? p.n : 32;
-  (void)depth;
+  B.step_zc = zc < p.n ? zc : p.n;
   B.cur = cur;
   B.hd = p.half_dtau_f;
   B.om6c = p.one_m6c_f;
@@ -364,10 +364,23 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
 size_t batched_entry_bytes() { return sizeof(BatchLat); }
 size_t batched_run_offset(int count) { return (size_t)count * sizeof(BatchLat); }
 
-int batched_launch(void* dev_table, int count, int64_t max_steps, int check_every, double tol, int tol_rel,
-                   int reimpose, int depth, int32_t* err, cudaStream_t st, int64_t* steps_done, int* grid_out) {
+void BatchedGraphs::release() {
+  for (int d = 0; d < 4; ++d) {
+    if (exec[d]) cudaGraphExecDestroy(exec[d]);
+    exec[d] = nullptr;
+    grid[d] = 0;
+  }
+}
+
+int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_start, int64_t t_end, int skip_first,
+                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int32_t* err,
+                   cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done, int* grid_out) {
   BatchRun run{};
   run.max_steps = max_steps;
+  run.t_start = t_start;
+  run.t_end = t_end;
+  run.skip_first = skip_first;
+  run.check0 = check0;
   run.tol = tol;
   run.check_every = check_every;
   run.tol_rel = tol_rel;
@@ -376,29 +389,53 @@ int batched_launch(void* dev_table, int count, int64_t max_steps, int check_ever
   run.nlat = count;
   BatchRun* drun = (BatchRun*)((char*)dev_table + batched_run_offset(count));
   cudaMemcpyAsync(drun, &run, sizeof(run), cudaMemcpyHostToDevice, st);
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  void* args[3];
-  const BatchLat* tab = (const BatchLat*)dev_table;
-  args[0] = (void*)&tab;
-  args[1] = (void*)&drun;
-  args[2] = (void*)&err;
-  cudaError_t e;
-  auto go = [&](auto kern, int threads, size_t smem) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = per_sm * sms;
-    *grid_out = grid;
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem, st);
-  };
-  if (depth <= 1)
-    e = go(k_batched<1>, tb::Geo<1, kTXB>::THREADS, batched_smem<1>());
-  else if (depth == 2)
-    e = go(k_batched<2>, tb::Geo<2, kTXB>::THREADS, batched_smem<2>());
-  else
-    e = go(k_batched<3>, tb::Geo<3, kTXB>::THREADS, batched_smem<3>());
+  depth = depth < 1 ? 1 : (depth > 3 ? 3 : depth);
+  if (!graphs->exec[depth]) {
+    // capture the cooperative launch once: grid = resident blocks of the whole device
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const BatchLat* tab = (const BatchLat*)dev_table;
+    void* args[3] = {(void*)&tab, (void*)&drun, (void*)&err};
+    auto capture = [&](auto kern, int threads, size_t smem) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      const int grid = per_sm * sms;
+      cudaStream_t cs;
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t el = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = el;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs->exec[depth], g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) {
+        graphs->exec[depth] = nullptr;
+        return e;
+      }
+      graphs->grid[depth] = grid;
+      return cudaSuccess;
+    };
+    cudaError_t e;
+    if (depth == 1)
+      e = capture(k_batched<1>, tb::Geo<1, kTXB>::THREADS, batched_smem<1>());
+    else if (depth == 2)
+      e = capture(k_batched<2>, tb::Geo<2, kTXB>::THREADS, batched_smem<2>());
+    else
+      e = capture(k_batched<3>, tb::Geo<3, kTXB>::THREADS, batched_smem<3>());
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return (int)e;
+    }
+  }
+  *grid_out = graphs->grid[depth];
+  cudaError_t e = cudaGraphLaunch(graphs->exec[depth], st);
   if (e != cudaSuccess) return (int)e;
   cudaMemcpyAsync(steps_done, &drun->steps_done, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   return 0;

@@ -68,6 +68,35 @@ def test_batched_bit_identical_to_separate_runs(fd, depth):
         np.testing.assert_array_equal(pa, pb)
 
 
+def test_batched_autotuned_slices_match_one_launch(fd):
+    """With autotuning the first batched evolve runs its (depth, z-chunk)
+    candidates on slices of 2 x check_every steps of the run itself and
+    finishes with the fastest, each launch a cooperative kernel in a CUDA
+    graph: the result equals one launch at a fixed configuration bit for
+    bit, lattices that converge during the tuning slices stay retired, and
+    the second evolve of the same sizes launches once with the cached
+    choice."""
+    lats, pots, masks, seeds = small_batch()
+    fixed = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=2, zchunk=32, check_every=50)
+    kw = dict(check_every=50, tol=1e-6, tol_relative=1, batched=1)
+    s = fd.Solver([fd.Lattice(l.n, l.length, fd.F32) for l in lats], fd.default_options(**kw))
+    for rep in range(2):
+        for i, (v, m, sd) in enumerate(zip(pots, masks, seeds)):
+            s.set_potential(v.astype(np.float32), lat=i)
+            s.init_symmetric(sd, m, lat=i)
+        s.reset_stats()
+        s.evolve(3000)
+        launches = s.stats()["graph_launches"]
+        assert launches == (1 if rep else 10) or (rep == 0 and 1 < launches <= 10)
+        for i, (pf, of) in enumerate(fixed):
+            o = s.last_check(lat=i)
+            assert o["steps"] == of["steps"] and o["energy"] == of["energy"], (rep, i)
+            np.testing.assert_array_equal(s.get_psi(lat=i, dtype=np.float32), pf)
+    depth, zc = s.tuned_config()
+    assert depth in (1, 2, 3) and zc in (16, 32, 64)
+    s.close()
+
+
 def test_batched_fixed_steps_match_oracle(fd, orc):
     lats = [wl.Lattice(8, 4.0), wl.Lattice(12, 5.0), wl.Lattice(20, 6.0)]
     pots = [wl.harmonic(8, 4.0), wl.anisotropic(12, 5.0), wl.harmonic(20, 6.0)]
