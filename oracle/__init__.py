@@ -22,6 +22,9 @@ Every function cites the passage of the paper it follows:
                        adjoint of Eq. updateeq (gradients w.r.t. V)
   project_out          Sec. III snapshot projection of lower states
   combine              Sec. VI linear combination of states as a start
+  set_boundary /
+  periodic_boundary    Sec. III remark on other boundary conditions:
+                       periodic ones (default: the zero shell)
 """
 from __future__ import annotations
 
@@ -47,6 +50,8 @@ def _load():
     lib = ctypes.CDLL(LIB_PATH)
     d, i, i64, u64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
     P = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_set_boundary.argtypes = [i]
+    lib.oracle_set_boundary.restype = None
     lib.oracle_splitmix64_mix.argtypes = [u64]
     lib.oracle_splitmix64_mix.restype = u64
     lib.oracle_splitmix64_output.argtypes = [u64, u64]
@@ -103,6 +108,25 @@ def _n_of(psi: np.ndarray) -> int:
     n = psi.shape[0]
     assert psi.shape == (n, n, n), psi.shape
     return n
+
+
+# --- boundary ---------------------------------------------------------------
+
+def set_boundary(periodic: bool) -> None:
+    """Zero shell (default, Sec. III) or periodic boundaries for every later call."""
+    _load().oracle_set_boundary(int(bool(periodic)))
+
+
+class periodic_boundary:
+    """Context manager: periodic boundaries inside the block."""
+
+    def __enter__(self):
+        set_boundary(True)
+        return self
+
+    def __exit__(self, *exc):
+        set_boundary(False)
+        return False
 
 
 # --- random numbers -------------------------------------------------------

@@ -13,6 +13,9 @@
  * lattice of (N+2)^3 sites, index (i, j, k) with x = i fastest, and the
  * padding shell i, j, k in {0, N+1} holds the boundary value psi = 0
  * (Sec. III: "The boundary values of the wavefunction are set to zero").
+ * The paper notes that other boundary conditions are easily implemented
+ * (Sec. III); oracle_set_boundary(1) selects periodic ones, under which a
+ * neighbour index 0 stands for N and N+1 for 1 (the shell is not read).
  * The potential V is passed densely on the N^3 interior sites, x fastest.
  * Interior site (i, j, k), 1 <= i, j, k <= N, sits at
  *     x = (i - (N+1)/2) a,   y = (j - (N+1)/2) a,   z = (k - (N+1)/2) a,
@@ -165,11 +168,22 @@ int oracle_impose_parity_adjoint(int n, int mask, double* lam) {
 /* psi_in and psi_out are distinct padded fields (Jacobi update); the         */
 /* padding of psi_out is set to zero.                                          */
 /* ------------------------------------------------------------------------ */
+/* Boundary: 0 = the zero shell of Sec. III, 1 = periodic (index 0 is N,
+ * index N+1 is 1 along every axis). */
+static int g_periodic = 0;
+void oracle_set_boundary(int periodic) { g_periodic = periodic ? 1 : 0; }
+
+/* neighbour index along one axis: i in [0, N+1] */
+static int nb(int n, int i) {
+  if (!g_periodic) return i;
+  return i < 1 ? i + n : (i > n ? i - n : i);
+}
+
 static double second_differences(int n, double a, const double* p, int i, int j, int k) {
   double c = p[PIDX(n, i, j, k)];
-  double dxx = (p[PIDX(n, i - 1, j, k)] - 2.0 * c + p[PIDX(n, i + 1, j, k)]) / (a * a);
-  double dyy = (p[PIDX(n, i, j - 1, k)] - 2.0 * c + p[PIDX(n, i, j + 1, k)]) / (a * a);
-  double dzz = (p[PIDX(n, i, j, k - 1)] - 2.0 * c + p[PIDX(n, i, j, k + 1)]) / (a * a);
+  double dxx = (p[PIDX(n, nb(n, i - 1), j, k)] - 2.0 * c + p[PIDX(n, nb(n, i + 1), j, k)]) / (a * a);
+  double dyy = (p[PIDX(n, i, nb(n, j - 1), k)] - 2.0 * c + p[PIDX(n, i, nb(n, j + 1), k)]) / (a * a);
+  double dzz = (p[PIDX(n, i, j, nb(n, k - 1))] - 2.0 * c + p[PIDX(n, i, j, nb(n, k + 1))]) / (a * a);
   return dxx + dyy + dzz;
 }
 
@@ -316,7 +330,8 @@ int64_t oracle_evolve(int n, double a, double dtau, double mass, const double* v
 /* Fine site j sits at x = (j - (2Nc+1)/2) a/2 with a the coarse spacing; in  */
 /* coarse index units that is xi = x/a + (Nc+1)/2 = j/2 + 1/4.  The value is   */
 /* interpolated linearly along each axis between coarse indices floor(xi) and */
-/* floor(xi)+1, where the coarse padding (index 0 and Nc+1) holds zero.        */
+/* floor(xi)+1, where the coarse padding (index 0 and Nc+1) holds zero, or,  */
+/* with periodic boundaries, index 0 stands for Nc and Nc+1 for 1.             */
 /* ------------------------------------------------------------------------ */
 void oracle_upsample(int nc, const double* psi_c, double* psi_f) {
   int nf = 2 * nc;
@@ -337,7 +352,7 @@ void oracle_upsample(int nc, const double* psi_c, double* psi_f) {
             for (int dx = 0; dx < 2; ++dx) {
               double w = (dx ? w1[0] : 1.0 - w1[0]) * (dy ? w1[1] : 1.0 - w1[1]) *
                          (dz ? w1[2] : 1.0 - w1[2]);
-              acc += w * psi_c[PIDX(nc, lo[0] + dx, lo[1] + dy, lo[2] + dz)];
+              acc += w * psi_c[PIDX(nc, nb(nc, lo[0] + dx), nb(nc, lo[1] + dy), nb(nc, lo[2] + dz))];
             }
         psi_f[PIDX(nf, i, j, k)] = acc;
       }
@@ -346,7 +361,8 @@ void oracle_upsample(int nc, const double* psi_c, double* psi_f) {
 /* ------------------------------------------------------------------------ */
 /* Adjoint of one update step.  The update is linear in Psi:                   */
 /*   Psi' = M Psi,   M = diag(A) + (dtau / 2m) diag(B) Lap,                    */
-/* with Lap the sum of second differences (symmetric, zero boundary), so       */
+/* with Lap the sum of second differences (symmetric for zero and for        */
+/* periodic boundaries), so                                                    */
 /*   M^T lambda = A lambda + (dtau / 2m) Lap (B lambda).                       */
 /* ------------------------------------------------------------------------ */
 void oracle_adjoint_step(int n, double a, double dtau, double mass, const double* v,
