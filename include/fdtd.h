@@ -121,7 +121,13 @@ typedef struct {
                              ended on the device by the convergence check (no host round trip
                              per segment); the rest, and every run with profiling on, goes
                              through the stream.  Results are identical either way. */
-  int32_t reserved[2];
+  int32_t boundary;       /* 0 (default): psi = 0 beyond the lattice (Sec. III); 1: periodic
+                             (neighbour index -1 is N-1 and N is 0 along every axis; the
+                             paper notes that other boundary conditions are easily
+                             implemented).  Periodic lattices use the z-marching kernels
+                             (the TMA boxes zero-fill), not batched mode and not
+                             fdtd_observables_noalloc */
+  int32_t reserved[1];
 } fdtd_options;
 
 typedef struct {

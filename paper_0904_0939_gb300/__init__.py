@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
                 ("batched", ctypes.c_int32), ("reimpose_parity", ctypes.c_int32),
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("snapshots", ctypes.c_int32), ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("snapshots", ctypes.c_int32), ("graphs", ctypes.c_int32), ("boundary", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Obs(ctypes.Structure):

@@ -164,6 +164,14 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "graphs must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
+  if (o.boundary != 0 && o.boundary != 1) {
+    err = "boundary must be 0 (zero) or 1 (periodic)";
+    return FDTD_ERR_INVALID_ARG;
+  }
+  if (o.boundary == 1 && o.batched) {
+    err = "batched mode needs zero boundaries";
+    return FDTD_ERR_INVALID_ARG;
+  }
   if (o.backward_steps < 0 || !std::isfinite(o.tol)) {
     err = "backward_steps must be >= 0 and tol finite";
     return FDTD_ERR_INVALID_ARG;
@@ -171,8 +179,9 @@ int check_options(const fdtd_options& o, std::string& err) {
   return FDTD_OK;
 }
 
-Params make_params(const fdtd_lattice_desc& d) {
+Params make_params(const fdtd_lattice_desc& d, int periodic) {
   Params p{};
+  p.periodic = periodic ? 1 : 0;
   p.n = d.n;
   p.a = d.length / d.n;
   p.dtau = d.dtau > 0.0 ? d.dtau : p.a * p.a / 4.0;
@@ -192,7 +201,7 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
   for (int l = 0; l < count; ++l) {
     Lat L;
     L.d = d[l];
-    L.p = make_params(d[l]);
+    L.p = make_params(d[l], o.boundary);
     L.n3 = (size_t)d[l].n * d[l].n * d[l].n;
     L.es = (int)elem_bytes(d[l].precision);
     L.psi[0] = cv.take(L.n3 * L.es);
@@ -1019,7 +1028,7 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
     launch_state_reset(&L.state[0], 1, c->st);
     launch_state_reset(&L.state[1], 1, c->st);
     c->stats.launches += 2;
-    if (tma_supported(L.d.n, L.d.precision)) {
+    if (tma_supported(L.d.n, L.d.precision) && !L.p.periodic) {  // TMA boxes zero-fill
       const float* bufs[3] = {(const float*)L.psi[0], (const float*)L.psi[1], (const float*)L.v};
       bool ok = true;
       int bw, bh;
@@ -1213,6 +1222,7 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
   if (D.d.n != 2 * S.d.n || std::fabs(D.d.length - S.d.length) > 1e-12 * S.d.length)
     return fail(dst, FDTD_ERR_SHAPE, "upsample: need n_dst = 2 n_src and equal box lengths");
   if (!S.has_psi) return fail(dst, FDTD_ERR_STATE, "upsample: source has no wavefunction");
+  if (S.p.periodic != D.p.periodic) return fail(dst, FDTD_ERR_INVALID_ARG, "upsample: boundaries differ");
   if (!D.has_v) return fail(dst, FDTD_ERR_STATE, "upsample: set the destination potential first");
   if (src->st != dst->st) {
     cudaEvent_t ev;
@@ -1226,7 +1236,7 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
     using Ti = std::remove_pointer_t<decltype(tin)>;
     with_type(D.d.precision, [&](auto* tout) {
       using To = std::remove_pointer_t<decltype(tout)>;
-      launch_upsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, dst->st);
+      launch_upsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, D.p.periodic, dst->st);
     });
   });
   dst->stats.launches += 1;

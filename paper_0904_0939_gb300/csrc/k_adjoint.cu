@@ -24,8 +24,14 @@ static int grid_1d(size_t total) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// neighbour value: zero beyond the lattice, or wrapped with periodic boundaries
 template <typename T>
-__device__ __forceinline__ double ldz(const T* p, int x, int y, int z, int n) {
+__device__ __forceinline__ double ldz(const T* p, int x, int y, int z, int n, int periodic) {
+  if (periodic) {
+    x = x < 0 ? x + n : (x >= n ? x - n : x);
+    y = y < 0 ? y + n : (y >= n ? y - n : y);
+    z = z < 0 ? z + n : (z >= n ? z - n : z);
+  }
   if ((unsigned)x < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)z < (unsigned)n)
     return (double)Store<T>::to(p[site_index(x, y, z, n)]);
   return 0.0;
@@ -85,8 +91,9 @@ __global__ void k_adjoint_seed(const T* __restrict__ psi, const void* __restrict
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
     double c = (double)Store<T>::to(psi[i]);
-    double nb = ldz(psi, x - 1, y, z, n) + ldz(psi, x + 1, y, z, n) + ldz(psi, x, y - 1, z, n) +
-                ldz(psi, x, y + 1, z, n) + ldz(psi, x, y, z - 1, n) + ldz(psi, x, y, z + 1, n);
+    const int pr = p.periodic;
+    double nb = ldz(psi, x - 1, y, z, n, pr) + ldz(psi, x + 1, y, z, n, pr) + ldz(psi, x, y - 1, z, n, pr) +
+                ldz(psi, x, y + 1, z, n, pr) + ldz(psi, x, y, z - 1, n, pr) + ldz(psi, x, y, z + 1, n, pr);
     double vv = (sizeof(T) == 8) ? ((const double*)v)[i] : (double)((const float*)v)[i];
     double hpsi = -kfac * (nb - 6.0 * c) + vv * c;
     double px = coord_f64(x, n, p.a), py = coord_f64(y, n, p.a), pz = coord_f64(z, n, p.a);

@@ -36,7 +36,10 @@ struct RowTile {
   C r[2][TY + 2][TX];
 };
 
-template <typename T, typename Body>
+// P: periodic boundaries (every load wraps modulo n, so the tile's rim and
+// the z-neighbours of the first and last planes come from the opposite side);
+// otherwise sites beyond the lattice read as zero.
+template <typename T, bool P, typename Body>
 __device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, RowTile<typename Store<T>::C>& tile,
                                        Body&& body) {
   using C = typename Store<T>::C;
@@ -46,9 +49,17 @@ __device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, 
   const int z1 = min(z0 + zc, n);
   const bool act = (x < n) && (y < n);
   auto ld = [&](int xx, int yy, int zz) -> C {
-    if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n)
-      return Store<T>::ld(in + site_index(xx, yy, zz, n));
-    return C(0);
+    if constexpr (P) {
+      auto wrap = [n](int q) {
+        q %= n;
+        return q < 0 ? q + n : q;
+      };
+      return Store<T>::ld(in + site_index(wrap(xx), wrap(yy), wrap(zz), n));
+    } else {
+      if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n)
+        return Store<T>::ld(in + site_index(xx, yy, zz, n));
+      return C(0);
+    }
   };
   const bool hy_lo = (ty == 0), hy_hi = (ty == TY - 1), hx_lo = (tx == 0), hx_hi = (tx == TX - 1);
   const int hy = hy_lo ? y - 1 : y + 1;
@@ -82,6 +93,7 @@ __device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, 
 }
 
 // ------------------------------------------------------------------ update
+template <bool P>
 __global__ void __launch_bounds__(TX* TY) k_step_f64(const double* __restrict__ in, double* __restrict__ out,
                                                      const double* __restrict__ coefA,
                                                      const double* __restrict__ coefCB, int n, int zc,
@@ -90,9 +102,9 @@ __global__ void __launch_bounds__(TX* TY) k_step_f64(const double* __restrict__ 
   pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<double> tile;
-  zmarch<double>(in, n, zc, tile,
-                 [&](int x, int y, int z, bool act, double c, double xm, double xp, double ym, double yp, double zm,
-                     double zp) {
+  zmarch<double, P>(in, n, zc, tile,
+                    [&](int x, int y, int z, bool act, double c, double xm, double xp, double ym, double yp, double zm,
+                        double zp) {
                    if (!act) return;
                    size_t i = site_index(x, y, z, n);
                    double s = nbr_sum(xm, xp, ym, yp, zm, zp);
@@ -100,7 +112,7 @@ __global__ void __launch_bounds__(TX* TY) k_step_f64(const double* __restrict__ 
                  });
 }
 
-template <typename T>
+template <typename T, bool P>
 __global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T* __restrict__ out,
                                                      const float* __restrict__ v, int n, int zc, float half_dtau,
                                                      float one_m6c, float cc, const int32_t* __restrict__ active) {
@@ -108,7 +120,7 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T
   pdl_trigger();
   if (active && *active == 0) return;
   __shared__ RowTile<float> tile;
-  zmarch<T>(in, n, zc, tile,
+  zmarch<T, P>(in, n, zc, tile,
             [&](int x, int y, int z, bool act, float c, float xm, float xp, float ym, float yp, float zm, float zp) {
               if (!act) return;
               size_t i = site_index(x, y, z, n);
@@ -121,14 +133,15 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const T* __restrict__ in, T
 void launch_step_f64(const double* in, double* out, const double* coefA, const double* coefCB, const Params& p,
                      const int32_t* active, cudaStream_t st) {
   Tiling t = tiling_for(p.n, 1216);
-  launch_pdl(k_step_f64, t.grid, dim3(TX, TY), 0, st, in, out, coefA, coefCB, p.n, t.zc, active);
+  launch_pdl(p.periodic ? k_step_f64<true> : k_step_f64<false>, t.grid, dim3(TX, TY), 0, st, in, out, coefA, coefCB,
+             p.n, t.zc, active);
 }
 
 template <typename T>
 void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st) {
   Tiling t = tiling_for(p.n, 1216);
-  launch_pdl(k_step_f32<T>, t.grid, dim3(TX, TY), 0, st, in, out, v, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f,
-             active);
+  launch_pdl(p.periodic ? k_step_f32<T, true> : k_step_f32<T, false>, t.grid, dim3(TX, TY), 0, st, in, out, v, p.n,
+             t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
 }
 template void launch_step_f32<float>(const float*, float*, const float*, const Params&, const int32_t*, cudaStream_t);
 template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
@@ -137,14 +150,14 @@ template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16
 // ------------------------------------------------------------------ adjoint stencil
 // lam_out = A lam + c (sum of the 6 neighbours of u - 6 u), u = B lam given;
 // the transpose of the update with the symmetric lattice Laplacian.
-template <typename T>
+template <typename T, bool P>
 __global__ void __launch_bounds__(TX* TY) k_adjoint_stencil(const T* __restrict__ u, const T* __restrict__ lam,
                                                             T* __restrict__ lam_out, const void* __restrict__ v,
                                                             const double* __restrict__ coefA, int n, int zc,
                                                             float half_dtau, float one_m6c, float cc, double c64) {
   using C = typename Store<T>::C;
   __shared__ RowTile<C> tile;
-  zmarch<T>(u, n, zc, tile, [&](int x, int y, int z, bool act, C cu, C xm, C xp, C ym, C yp, C zm, C zp) {
+  zmarch<T, P>(u, n, zc, tile, [&](int x, int y, int z, bool act, C cu, C xm, C xp, C ym, C yp, C zm, C zp) {
     if (!act) return;
     size_t i = site_index(x, y, z, n);
     if constexpr (sizeof(T) == 8) {
@@ -163,8 +176,8 @@ template <typename T>
 void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v, const double* coefA, const Params& p,
                             cudaStream_t st) {
   Tiling t = tiling_for(p.n, 1216);
-  k_adjoint_stencil<T><<<t.grid, dim3(TX, TY), 0, st>>>(u, lam, lam_out, v, coefA, p.n, t.zc, p.half_dtau_f,
-                                                         p.one_m6c_f, p.c_f, p.c);
+  auto k = p.periodic ? k_adjoint_stencil<T, true> : k_adjoint_stencil<T, false>;
+  k<<<t.grid, dim3(TX, TY), 0, st>>>(u, lam, lam_out, v, coefA, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f, p.c);
 }
 template void launch_adjoint_stencil<double>(const double*, const double*, double*, const void*, const double*,
                                              const Params&, cudaStream_t);
@@ -197,6 +210,7 @@ __device__ __forceinline__ void block_sum4_store(double v0, double v1, double v2
 }
 
 // FP64: every term and sum in FP64.
+template <bool P>
 __global__ void __launch_bounds__(TX* TY) k_sums_f64(const double* __restrict__ psi, const double* __restrict__ v,
                                                      int n, int zc, double a, double kfac, double* partials,
                                                      const int32_t* __restrict__ active) {
@@ -205,7 +219,7 @@ __global__ void __launch_bounds__(TX* TY) k_sums_f64(const double* __restrict__ 
   if (active && *active == 0) return;
   __shared__ RowTile<double> tile;
   double s0 = 0, sh = 0, sr = 0, sv = 0;
-  zmarch<double>(psi, n, zc, tile,
+  zmarch<double, P>(psi, n, zc, tile,
                  [&](int x, int y, int z, bool act, double c, double xm, double xp, double ym, double yp, double zm,
                      double zp) {
                    if (!act) return;
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(TX* TY) k_sums_f64(const double* __restrict__ 
 
 // FP32 / BF16 storage: per-site terms in FP32, Kahan-compensated FP32 runs
 // per thread, FP64 across threads and blocks.
-template <typename T>
+template <typename T, bool P>
 __global__ void __launch_bounds__(TX* TY) k_sums_f32(const T* __restrict__ psi, const float* __restrict__ v, int n,
                                                      int zc, float a, float kfac, double* partials,
                                                      const int32_t* __restrict__ active) {
@@ -233,7 +247,7 @@ __global__ void __launch_bounds__(TX* TY) k_sums_f32(const T* __restrict__ psi, 
   if (active && *active == 0) return;
   __shared__ RowTile<float> tile;
   Kahan s0, sh, sr, sv;
-  zmarch<T>(psi, n, zc, tile,
+  zmarch<T, P>(psi, n, zc, tile,
             [&](int x, int y, int z, bool act, float c, float xm, float xp, float ym, float yp, float zm, float zp) {
               if (!act) return;
               size_t i = site_index(x, y, z, n);
@@ -263,7 +277,8 @@ template <>
 int launch_sums<double>(const double* psi, const void* v, const Params& p, double* partials, const int32_t* active,
                         cudaStream_t st) {
   Tiling t = sums_tiling(p.n);
-  launch_pdl(k_sums_f64, t.grid, dim3(TX, TY), 0, st, psi, (const double*)v, p.n, t.zc, p.a,
+  launch_pdl(p.periodic ? k_sums_f64<true> : k_sums_f64<false>, t.grid, dim3(TX, TY), 0, st, psi, (const double*)v,
+             p.n, t.zc, p.a,
              1.0 / (2.0 * p.mass * p.a * p.a), partials, active);
   return (int)(t.grid.x * t.grid.y * t.grid.z);
 }
@@ -271,7 +286,8 @@ template <typename T>
 int launch_sums(const T* psi, const void* v, const Params& p, double* partials, const int32_t* active,
                 cudaStream_t st) {
   Tiling t = sums_tiling(p.n);
-  launch_pdl(k_sums_f32<T>, t.grid, dim3(TX, TY), 0, st, psi, (const float*)v, p.n, t.zc, (float)p.a,
+  launch_pdl(p.periodic ? k_sums_f32<T, true> : k_sums_f32<T, false>, t.grid, dim3(TX, TY), 0, st, psi,
+             (const float*)v, p.n, t.zc, (float)p.a,
              (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active);
   return (int)(t.grid.x * t.grid.y * t.grid.z);
 }
@@ -586,7 +602,7 @@ __device__ __forceinline__ void interp_axis(int x, int& lo, double& wlo, double&
 // are exact, so the result differs from the FP64 sum only by the rounding of
 // the seven FP32 operations.
 template <typename Ti, typename To>
-__global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ out) {
+__global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ out, int periodic) {
   const int nf = 2 * nc;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= nf) return;
@@ -597,7 +613,12 @@ __global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ o
   interp_axis(y, ly, wy[0], wy[1]);
   interp_axis(z, lz, wz[0], wz[1]);
   auto at = [&](int dx, int dy, int dz) {
-    const int cx = lx + dx, cy = ly + dy, cz = lz + dz;
+    int cx = lx + dx, cy = ly + dy, cz = lz + dz;
+    if (periodic) {  // coarse index -1 is nc-1 and nc is 0
+      cx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+      cy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+      cz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+    }
     return ((unsigned)cx < (unsigned)nc && (unsigned)cy < (unsigned)nc && (unsigned)cz < (unsigned)nc)
                ? in[site_index(cx, cy, cz, nc)]
                : Store<Ti>::from(0.0f);
@@ -623,12 +644,12 @@ __global__ void k_upsample(const Ti* __restrict__ in, int nc, To* __restrict__ o
   }
 }
 template <typename Ti, typename To>
-void launch_upsample(const Ti* in, int nc, To* out, cudaStream_t st) {
+void launch_upsample(const Ti* in, int nc, To* out, int periodic, cudaStream_t st) {
   const int nf = 2 * nc;
   dim3 grid((nf + 127) / 128, nf, nf);
-  k_upsample<Ti, To><<<grid, 128, 0, st>>>(in, nc, out);
+  k_upsample<Ti, To><<<grid, 128, 0, st>>>(in, nc, out, periodic);
 }
-#define INST_UP(Ti, To) template void launch_upsample<Ti, To>(const Ti*, int, To*, cudaStream_t);
+#define INST_UP(Ti, To) template void launch_upsample<Ti, To>(const Ti*, int, To*, int, cudaStream_t);
 INST_UP(double, double)
 INST_UP(double, float)
 INST_UP(double, __nv_bfloat16)

@@ -35,6 +35,7 @@ struct Params {
   float half_dtau_f;   // dtau / 2 (FP32)
   float one_m6c_f;     // 1 - 6c (FP32)
   float c_f;           // c (FP32)
+  int periodic;        // 1: periodic boundaries, 0: psi = 0 beyond the lattice
 };
 
 // Tiling of the z-marching kernels: 32 x 8 threads per block, one site per
@@ -145,7 +146,7 @@ template <typename T>
 void launch_init_random(T* out, int n, uint64_t seed, uint64_t lat, int dist, cudaStream_t st);
 
 template <typename Ti, typename To>
-void launch_upsample(const Ti* in, int nc, To* out, cudaStream_t st);
+void launch_upsample(const Ti* in, int nc, To* out, int periodic, cudaStream_t st);
 
 template <typename Ti, typename To>
 void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t st);
