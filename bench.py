@@ -40,7 +40,7 @@ SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 TOL = 1e-6
 SEED = 904939
 # dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
-# from an ncu capture of the current kernel, by (depth, z-chunk); a tuned
+# from an ncu capture of the current kernel, by (depth, span); a tuned
 # configuration without a capture reports traffic null
 TRAFFIC_256 = {(3, 54): 238_210_048}
 
@@ -554,7 +554,7 @@ def main():
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc)),
-                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, z-chunk {zc})" if zc
+                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, span {zc})" if zc
                                 else "k_step_f32 (256^3 level, one-step z-marching)"),
                      "launches": fine_launches, "timed_launches": fine_timed, "ms_per_launch": ms_launch,
                      "bytes_per_launch": bytes_launch, "peak_kind": peak_note,
