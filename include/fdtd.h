@@ -27,7 +27,7 @@
  *   that return results to host memory synchronise that stream.
  * - Errors: every call returns an int status (FDTD_OK = 0; negative = error;
  *   FDTD_NOT_CONVERGED is a positive, soft status).  Nothing aborts, exits or
- *   throws across the ABI.  fdtd_last_error() gives a message for the last
+ *   throws across the ABI.  fdtd_last_error() copies a message for the last
  *   failure on a handle.
  * - Threads: a handle must not be used by two host threads at once.
  */
@@ -179,8 +179,12 @@ FDTD_API int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_optio
 /* Release the host-side context (the caller frees the workspace). */
 FDTD_API int fdtd_destroy(fdtd_handle h);
 
-/* Message for the last error on h (or on handle creation when h is NULL). */
-FDTD_API const char* fdtd_last_error(fdtd_handle h);
+/* Message for the last error on h (or on handle creation and the
+ * handle-free calls when h is NULL), copied into the caller's buf of n bytes
+ * (truncated, always NUL-terminated when n > 0; buf may be NULL when n is 0).
+ * Returns the full length of the message, so a caller can size buf; never
+ * negative. */
+FDTD_API int fdtd_last_error(fdtd_handle h, char* buf, size_t n);
 
 /* Load V (n^3 values, dense x-fastest, dtype FDTD_F64 or FDTD_F32) for
  * lattice `lat` (Sec. II: static real potential).  The coefficients

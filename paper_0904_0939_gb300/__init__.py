@@ -119,8 +119,8 @@ def _load():
         f.restype = ctypes.c_int
     lib.fdtd_observables_noalloc.argtypes = [vp, vp, i32, i32, d, d, vp, vp]
     lib.fdtd_observables_noalloc.restype = ctypes.c_int
-    lib.fdtd_last_error.argtypes = [vp]
-    lib.fdtd_last_error.restype = ctypes.c_char_p
+    lib.fdtd_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.fdtd_last_error.restype = i32
     return lib
 
 
@@ -157,10 +157,17 @@ class Lattice:
         return self.dtau if self.dtau > 0 else self.a * self.a / 4.0
 
 
+def last_error(handle=None) -> str:
+    """The library's message for the last error on `handle` (None: handle creation)."""
+    size = lib.fdtd_last_error(handle, None, 0)
+    buf = ctypes.create_string_buffer(size + 1)
+    lib.fdtd_last_error(handle, buf, size + 1)
+    return buf.value.decode(errors="replace")
+
+
 def _check(rc: int, handle=None, allow_soft: bool = False) -> int:
     if rc < 0 or (rc > 0 and not allow_soft):
-        msg = lib.fdtd_last_error(handle)
-        raise FdtdError(rc, msg.decode() if msg else "")
+        raise FdtdError(rc, last_error(handle))
     return rc
 
 

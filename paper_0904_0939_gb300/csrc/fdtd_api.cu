@@ -1064,7 +1064,15 @@ int fdtd_destroy(fdtd_handle h) {
   return FDTD_OK;
 }
 
-const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+int fdtd_last_error(fdtd_handle h, char* buf, size_t n) {
+  const std::string& m = h ? h->err : g_create_err;
+  if (buf && n > 0) {
+    const size_t k = std::min(n - 1, m.size());
+    std::memcpy(buf, m.data(), k);
+    buf[k] = '\0';
+  }
+  return (int)std::min<size_t>(m.size(), 0x7fffffff);
+}
 
 int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
   int rc = lat_check(h, lat);

@@ -39,6 +39,23 @@ def test_library_exports_every_declared_symbol(fd):
     assert set(fd.EXPORTED) | {"fdtd_last_error"} >= set(declared_symbols())
 
 
+def test_last_error_copies_into_the_callers_buffer(fd):
+    """fdtd_last_error(h, buf, n): full length returned, the copy truncated
+    and NUL-terminated (checked after a failed create, no GPU needed)."""
+    o = fd.default_options(check_every=0)
+    h = ctypes.c_void_p()
+    desc = fd.Lattice(8, 4.0, fd.F32).desc()
+    rc = fd.lib.fdtd_create(ctypes.byref(desc), 1, ctypes.byref(o), None, 0, None, ctypes.byref(h))
+    assert rc < 0
+    full = fd.lib.fdtd_last_error(None, None, 0)
+    assert full > 0
+    msg = fd.last_error(None)
+    assert len(msg) == full
+    small = ctypes.create_string_buffer(8)
+    assert fd.lib.fdtd_last_error(None, small, 8) == full
+    assert small.value == msg.encode()[:7]
+
+
 def test_default_options(fd):
     o = fd.default_options()
     assert o.check_every == 100 and o.tol == pytest.approx(1e-6) and o.tol_relative == 1
@@ -78,7 +95,9 @@ def test_host_side_validation(fd):
     assert rc == fd.ERR_INVALID_ARG
     rc, _ = _size(fd, [fd.Lattice(8, 1.0, fd.F32)], check_every=0)
     assert rc == fd.ERR_INVALID_ARG
-    assert b"von Neumann" in fd.lib.fdtd_last_error(None) or True
+    assert "check_every" in fd.last_error(None)
+    rc, _ = _size(fd, [fd.Lattice(32, 10.0, fd.F32, dtau=a * a / 3 * 1.0001)])
+    assert "von Neumann" in fd.last_error(None)
 
 
 def test_create_rejects_bad_workspace(fd):

@@ -49,7 +49,7 @@ def noalloc(fd, psi, v, length, prec):
     rc = fd.lib.fdtd_observables_noalloc(ctypes.c_void_p(tp.data_ptr()), ctypes.c_void_p(tv.data_ptr()), prec,
                                          psi.shape[0], length, 1.0, ctypes.c_void_p(out.data_ptr()),
                                          ctypes.c_void_p(stream.cuda_stream))
-    assert rc == fd.OK, fd.lib.fdtd_last_error(None)
+    assert rc == fd.OK, fd.last_error(None)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -81,4 +81,4 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(fd):
     rc = fd.lib.fdtd_observables_noalloc(ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(t.data_ptr()), fd.F32, 1025,
                                          10.0, 1.0, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == fd.ERR_SHAPE
-    assert b"1024" in fd.lib.fdtd_last_error(None)
+    assert "1024" in fd.last_error(None)
