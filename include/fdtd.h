@@ -252,6 +252,14 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
  * depth and z-planes per item of its persistent launch. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
+/* Per-check record of the last fdtd_evolve on lattice `lat` (Secs. III-V):
+ * 8 doubles per check {t, E, E_b, norm = sum psi^2 a^3 before the
+ * renormalisation, <r^2>, <V>, |dE_b| (-1 at the first check), S0}, oldest
+ * first.  The device keeps the last 4096 checks of an evolve; the most
+ * recent min(checks, 4096, cap) are copied to the host array out (cap
+ * records of 8 doubles) and *count receives the number of checks made. */
+FDTD_API int fdtd_check_history(fdtd_handle h, int lat, double* out, int cap, int* count);
+
 /* Snapshots (Sec. III): full copies of psi kept in the workspace, in
  * options.snapshots slots per lattice.  save: psi -> slot; load: slot -> psi
  * (also recorded as the start of fdtd_backward; the symmetry mask is kept). */

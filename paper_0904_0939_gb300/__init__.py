@@ -80,6 +80,7 @@ EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
             "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
+            "fdtd_check_history",
             "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine"]
 
 
@@ -108,6 +109,7 @@ def _load():
         "fdtd_reset_stats": [vp],
         "fdtd_set_profiling": [vp, i32],
         "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
+        "fdtd_check_history": [vp, i32, P(d), i32, P(ctypes.c_int)],
         "fdtd_snapshot_save": [vp, i32, i32],
         "fdtd_snapshot_load": [vp, i32, i32],
         "fdtd_project_out": [vp, i32, P(ctypes.c_int), i32],
@@ -324,6 +326,18 @@ class Solver:
         w = (ctypes.c_double * len(weights))(*weights)
         with self._ctx():
             _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
+
+    HISTORY_FIELDS = ("t", "E", "E_b", "norm", "r2", "V", "delta_e", "S0")
+
+    def history(self, lat: int = 0, cap: int = 4096) -> np.ndarray:
+        """Per-check records of the last evolve, oldest first: an array of
+        shape (k, 8) with columns HISTORY_FIELDS."""
+        buf = np.zeros((cap, 8), dtype=np.float64)
+        count = ctypes.c_int()
+        with self._ctx():
+            _check(lib.fdtd_check_history(self.handle, lat, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap,
+                                          ctypes.byref(count)), self.handle)
+        return buf[: min(count.value, cap, 4096)].copy()
 
     def tuned_config(self, lat: int = 0) -> tuple[int, int]:
         """(temporal depth, span in tile planes per block) the stencil uses for

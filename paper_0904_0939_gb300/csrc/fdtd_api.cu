@@ -22,6 +22,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fdtd.h"
 #include "kernels.cuh"
 
@@ -48,6 +50,7 @@ struct Lat {
   double* partials = nullptr;
   int nparts = 0;
   LatState* state = nullptr;    // [0] evolve record, [1] scratch
+  double* hist = nullptr;       // check history ring of the evolve (kHistCap records)
   int mask = 0;
   bool has_v = false, has_psi = false, has_psi0 = false;
   // backward storage
@@ -216,6 +219,7 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
     L.nparts = std::max(sums_blocks(d[l].n), tma_sums_blocks(d[l].n));
     L.partials = (double*)cv.take((size_t)L.nparts * 4 * sizeof(double));
     L.state = (LatState*)cv.take(2 * sizeof(LatState));
+    L.hist = (double*)cv.take((size_t)kHistCap * kHistFields * sizeof(double));
     if (o.backward_steps > 0 && d[l].precision != FDTD_BF16) {
       L.bw_T = o.backward_steps;
       L.bw_K = (int)std::ceil(std::sqrt((double)o.backward_steps));
@@ -282,6 +286,12 @@ struct fdtd_context {
 };
 
 namespace {
+
+// NVTX range for profilers (header-only NVTX3: no cost without a tool attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 int fail(fdtd_context* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -379,6 +389,7 @@ void choose_config(fdtd_context* c, Lat& L) {
       return;
     }
   }
+  Range r("stencil autotune");
   // time each candidate (every one of them is bit-identical):
   // psi[cur] -> psi[1-cur], psi[cur] is only read
   cudaEvent_t e0, e1;
@@ -523,7 +534,8 @@ void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int ma
 // One check of Secs. III-V on psi[cur]: sums, finalize, renormalise + mask.
 void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
   int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
-  launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st);
+  launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, 0,
+                  0, nullptr, L.hist);
   c->stats.launches += 1;
   int mask = c->o.reimpose_parity ? L.mask : 0;
   scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], check_id, 1 - L.cur, &L.state[0]);
@@ -545,7 +557,7 @@ int read_state(fdtd_context* c, Lat& L) {
 void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditionalHandle cond) {
   int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
   launch_finalize(&L.state[0], L.partials, np, 0, 0, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, (int)ce,
-                  cond, c->flags + 1);
+                  cond, c->flags + 1, L.hist);
   c->stats.launches += 1;
   int mask = c->o.reimpose_parity ? L.mask : 0;
   scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], -1, 1 - L.cur, &L.state[0]);
@@ -572,6 +584,7 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain, ce};
   if (L.graph_exec[b] && std::equal(key, key + 6, L.graph_key[b])) return true;
   release_graph(L, b);
+  Range r("evolve graph build");
   if (L.tma_ok && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
     (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx);  // occupancy query outside the capture
   cudaGraph_t g = nullptr;
@@ -859,7 +872,8 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
     for (int l = 0; l < count; ++l) {
       Lat& L = c->lats[l];
       if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
-                       (const float*)L.v, L.partials, &L.state[0], L.p, L.mask, L.cur, L.d.v_inf, cd.second))
+                       (const float*)L.v, L.partials, &L.state[0], L.hist, L.p, L.mask, L.cur, L.d.v_inf,
+                       cd.second))
         return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
     }
     cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
@@ -1159,6 +1173,7 @@ int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_kind) {
 }
 
 int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
+  Range r("fdtd_evolve");
   if (!h) return FDTD_ERR_INVALID_ARG;
   if (max_steps < 0) return fail(h, FDTD_ERR_INVALID_ARG, "evolve: max_steps < 0");
   for (auto& L : h->lats)
@@ -1198,7 +1213,31 @@ int fdtd_last_check(fdtd_handle h, int lat, fdtd_obs* out) {
   return FDTD_OK;
 }
 
+int fdtd_check_history(fdtd_handle h, int lat, double* out, int cap, int* count) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!count || cap < 0 || (cap > 0 && !out)) return fail(h, FDTD_ERR_INVALID_ARG, "check_history: bad output");
+  Lat& L = h->lats[lat];
+  cudaMemcpyAsync(&L.host_state, &L.state[0], sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("check_history: ") + cudaGetErrorString(e));
+  const int total = L.host_state.checks;
+  *count = total;
+  // the most recent min(total, kHistCap, cap) records, oldest first
+  const int keep = std::min(std::min(total, kHistCap), cap);
+  const size_t rec = (size_t)kHistFields * sizeof(double);
+  for (int q = 0; q < keep; ++q) {
+    const int k = total - keep + q;  // check number, 0-based
+    cudaMemcpyAsync(out + (size_t)q * kHistFields, L.hist + (size_t)(k % kHistCap) * kHistFields, rec,
+                    cudaMemcpyDeviceToHost, h->st);
+  }
+  e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("check_history: ") + cudaGetErrorString(e));
+  return FDTD_OK;
+}
+
 int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out) {
+  Range r("fdtd_observables");
   int rc = lat_check(h, lat);
   if (rc) return rc;
   if (!out) return fail(h, FDTD_ERR_INVALID_ARG, "observables: null output");
@@ -1222,6 +1261,7 @@ int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out) {
 }
 
 int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
+  Range r("fdtd_upsample");
   int rc = lat_check(src, lat_src);
   if (rc) return rc;
   if ((rc = lat_check(dst, lat_dst))) return rc;
@@ -1268,6 +1308,7 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
 
 int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, void* gv_out, int dtype, int mem_kind,
                   fdtd_obs* obs) {
+  Range r("fdtd_backward");
   int rc = lat_check(h, lat);
   if (rc) return rc;
   Lat& L = h->lats[lat];

@@ -39,6 +39,7 @@ struct alignas(64) BatchLat {
   float* psi[2];
   double* partials;
   LatState* state;
+  double* hist;  // check history ring (kHistCap records)
   int n, mask, step_zc, cur;
   float hd, om6c, cc, a_f, kfac_f;
   int pad;
@@ -171,6 +172,17 @@ __device__ void finalize_lattice(const BatchLat& L, int nparts, int check_id, in
       s->delta_e = d;
       s->e_prev = eb;
       s->has_prev = 1;
+      if (L.hist) {
+        double* h = L.hist + (size_t)((s->checks - 1) % kHistCap) * kHistFields;
+        h[0] = (double)t;
+        h[1] = e;
+        h[2] = eb;
+        h[3] = s0 * L.a3;
+        h[4] = sr / s0;
+        h[5] = sv / s0;
+        h[6] = d;
+        h[7] = s0;
+      }
     }
   }
   __syncthreads();
@@ -331,7 +343,7 @@ size_t batched_smem() {
 int batched_max_lattices() { return kMaxLat; }
 
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
-                 LatState* state, const Params& p, int mask, int cur, double v_inf, int zc) {
+                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf, int zc) {
   BatchLat& B = *(BatchLat*)host_entry;
   int bw, bh;
   const float* bufs[3] = {psi0, psi1, v};
@@ -347,6 +359,7 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
   B.psi[1] = (float*)psi1;
   B.partials = partials;
   B.state = state;
+  B.hist = hist;
   B.n = p.n;
   B.mask = mask;
   B.step_zc = zc < p.n ? zc : p.n;

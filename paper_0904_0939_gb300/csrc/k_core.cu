@@ -301,7 +301,7 @@ template int launch_sums<__nv_bfloat16>(const __nv_bfloat16*, const void*, const
 __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __restrict__ parts, int np, int check_id,
                                                   int64_t t, double a3, double v_inf, double tol, int tol_rel,
                                                   int record, int seq_ce, cudaGraphConditionalHandle cond,
-                                                  const int32_t* err) {
+                                                  const int32_t* err, double* hist) {
   pdl_wait();
   pdl_trigger();
   const bool seq = seq_ce > 0;
@@ -369,6 +369,17 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
   s->delta_e = d;
   s->e_prev = eb;
   s->has_prev = 1;
+  if (hist) {
+    double* h = hist + (size_t)((s->checks - 1) % kHistCap) * kHistFields;
+    h[0] = (double)t;
+    h[1] = e;
+    h[2] = eb;
+    h[3] = s0 * a3;
+    h[4] = sr / s0;
+    h[5] = sv / s0;
+    h[6] = d;
+    h[7] = s0;
+  }
   if (seq) {
     const bool more = s->active && check_id + 1 < s->seq_limit && *(volatile const int32_t*)err == 0;
     cudaGraphSetConditional(cond, more ? 1u : 0u);
@@ -377,9 +388,9 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
 
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
                      double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce,
-                     cudaGraphConditionalHandle cond, const int32_t* err) {
+                     cudaGraphConditionalHandle cond, const int32_t* err, double* hist) {
   launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol,
-             tol_rel, record, seq_ce, cond, err);
+             tol_rel, record, seq_ce, cond, err, hist);
 }
 
 __global__ void k_state_reset(LatState* s, int mode, int seq_limit) {

@@ -99,7 +99,7 @@ int batched_max_lattices();
 size_t batched_entry_bytes();
 // zc: z-planes per step item (the tile is 64 x 16 sites in x-y).
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
-                 LatState* state, const Params& p, int mask, int cur, double v_inf, int zc);
+                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf, int zc);
 // Instantiated CUDA graphs of the persistent launch, one per depth, owned
 // by the handle (the kernel's arguments are the fixed table, run record and
 // error flag, so a graph is reused by every evolve of the handle).
@@ -130,9 +130,14 @@ int sums_blocks(int n);
 // following scale whether a factor was posted, and the graph's while
 // condition `cond` is set to continue only while the lattice is active, no
 // device-side wait has expired (*err == 0) and check + 1 < s->seq_limit.
+// With hist, a recording check also writes its record {t, E, E_b, norm,
+// <r^2>, <V>, |dE_b|, S0} to slot (checks - 1) % kHistCap of the lattice's
+// history ring.
+constexpr int kHistCap = 4096;
+constexpr int kHistFields = 8;
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
                      double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce = 0,
-                     cudaGraphConditionalHandle cond = 0, const int32_t* err = nullptr);
+                     cudaGraphConditionalHandle cond = 0, const int32_t* err = nullptr, double* hist = nullptr);
 
 // out = P(scale * in): renormalisation and symmetry re-imposition.  With
 // s == nullptr the factor is 1 and the call is unconditional; otherwise it

@@ -92,6 +92,9 @@ def test_batched_autotuned_slices_match_one_launch(fd):
             o = s.last_check(lat=i)
             assert o["steps"] == of["steps"] and o["energy"] == of["energy"], (rep, i)
             np.testing.assert_array_equal(s.get_psi(lat=i, dtype=np.float32), pf)
+            h = s.history(lat=i)  # the check records of the persistent launch, across its slices
+            assert len(h) == o["checks"] and h[-1, 0] == o["steps"] and h[-1, 1] == o["energy"]
+            assert np.all(np.diff(h[:, 0]) > 0)
     depth, zc = s.tuned_config()
     assert depth in (1, 2, 3) and zc in (16, 32, 64)
     s.close()

@@ -90,6 +90,30 @@ def test_fp64_100_steps_match_oracle(fd, orc, n):
     assert o["norm"] == pytest.approx(rec["S0"] * a**3, rel=1e-12)
 
 
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_check_history_matches_oracle(fd, orc, graphs):
+    """The per-check records of an FP64 evolve (t, E, <r^2>, S0 before the
+    renormalisation) against the oracle's check history, through the stream
+    and through the evolve graph."""
+    n, L = 12, 6.0
+    a = L / n
+    v = wl.harmonic(n, L)
+    s = solver(fd, n, L, fd.F64, check_every=20, graphs=graphs)
+    s.set_potential(v)
+    s.init_symmetric(8, 0)
+    s.evolve(270)
+    h = s.history()
+    _, rec, hist = orc.evolve(orc.init_random(n, 8), v, a, a * a / 4, 270, 20)
+    assert h.shape == (len(hist), 8) == (15, 8)
+    np.testing.assert_array_equal(h[:, 0], hist[:, 0])
+    np.testing.assert_allclose(h[:, 1], hist[:, 1], rtol=1e-12)
+    np.testing.assert_allclose(h[:, 4], hist[:, 2], rtol=1e-12)
+    np.testing.assert_allclose(h[:, 7], hist[:, 3], rtol=1e-12)
+    np.testing.assert_allclose(h[:, 3], hist[:, 3] * a**3, rtol=1e-12)
+    assert h[0, 6] == -1.0 and np.all(h[1:, 6] >= 0.0)
+    np.testing.assert_allclose(h[1:, 6], np.abs(np.diff(h[:, 2])), rtol=1e-9, atol=1e-15)
+
+
 @pytest.mark.parametrize("mask", [wl.ODD_X, wl.ODD_Z | wl.ODD_Y, wl.SYMMETRIC_ALL])
 @pytest.mark.parametrize("n", [9, 16])
 def test_fp64_sector_evolution_matches_oracle(fd, orc, n, mask):
