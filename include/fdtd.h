@@ -58,6 +58,7 @@ extern "C" {
 #define FDTD_ERR_SHAPE (-6)        /* lattice sizes or boxes do not match */
 #define FDTD_ERR_WORKSPACE (-7)    /* workspace missing, misaligned or too small */
 #define FDTD_ERR_STATE (-8)        /* call out of order (e.g. evolve before set_potential) */
+#define FDTD_ERR_IO (-9)           /* a file cannot be opened, read or written, or is malformed */
 
 /* ---- enums ---------------------------------------------------------------- */
 #define FDTD_F64 0   /* psi and V in FP64 ("plain FP64 form") */
@@ -251,6 +252,25 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
  * z-marching kernel is in use.  For a batched handle after an evolve: the
  * depth and z-planes per item of its persistent launch. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
+
+/* Checkpoint files (Sec. VII.G: a run saves its wavefunction, and a later
+ * run reads it back as its initial condition, adjusting the resolution).
+ * File layout, little-endian: a 64-byte header {char magic[8] = "FDTDPSI1";
+ * uint32 version = 1; int32 n; int32 dtype (FDTD_F64 for FP64 lattices,
+ * FDTD_F32 otherwise); int32 symmetry mask; double box length, mass, dtau;
+ * int64 steps of the last evolve; uint64 FNV-1a hash of the data bytes}
+ * followed by the n^3 values, x fastest.
+ * fdtd_save_psi writes psi of lattice `lat` (FDTD_ERR_STATE before any
+ * psi, FDTD_ERR_IO if the file cannot be written).
+ * fdtd_load_psi reads it into lattice `lat`: the box length must match
+ * (FDTD_ERR_SHAPE) and the lattice's n must be the file's n times 2^k.  For
+ * k = 0 psi is taken as stored (as fdtd_set_psi); for k > 0 it is
+ * transferred k times by the trilinear map of fdtd_upsample, then
+ * renormalised and given the file's symmetry mask.  A file that is
+ * truncated, too long, of another format or whose data do not match the
+ * stored hash is rejected with FDTD_ERR_IO before the lattice is touched. */
+FDTD_API int fdtd_save_psi(fdtd_handle h, int lat, const char* path);
+FDTD_API int fdtd_load_psi(fdtd_handle h, int lat, const char* path);
 
 /* Per-check record of the last fdtd_evolve on lattice `lat` (Secs. III-V):
  * 8 doubles per check {t, E, E_b, norm = sum psi^2 a^3 before the

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libfdtd.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_UNSTABLE_DT, ERR_NONFINITE, ERR_CUDA = -1, -2, -3, -4
-ERR_TIMEOUT, ERR_SHAPE, ERR_WORKSPACE, ERR_STATE = -5, -6, -7, -8
+ERR_TIMEOUT, ERR_SHAPE, ERR_WORKSPACE, ERR_STATE, ERR_IO = -5, -6, -7, -8, -9
 F64, F32, BF16 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 DIST_UNIFORM, DIST_GAUSSIAN = 0, 1
@@ -80,7 +80,7 @@ EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
             "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
-            "fdtd_check_history",
+            "fdtd_check_history", "fdtd_save_psi", "fdtd_load_psi",
             "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine"]
 
 
@@ -110,6 +110,8 @@ def _load():
         "fdtd_set_profiling": [vp, i32],
         "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
         "fdtd_check_history": [vp, i32, P(d), i32, P(ctypes.c_int)],
+        "fdtd_save_psi": [vp, i32, ctypes.c_char_p],
+        "fdtd_load_psi": [vp, i32, ctypes.c_char_p],
         "fdtd_snapshot_save": [vp, i32, i32],
         "fdtd_snapshot_load": [vp, i32, i32],
         "fdtd_project_out": [vp, i32, P(ctypes.c_int), i32],
@@ -326,6 +328,17 @@ class Solver:
         w = (ctypes.c_double * len(weights))(*weights)
         with self._ctx():
             _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
+
+    def save(self, path, lat: int = 0):
+        """Write psi of lattice `lat` to a checkpoint file (fdtd_save_psi)."""
+        with self._ctx():
+            _check(lib.fdtd_save_psi(self.handle, lat, os.fsencode(path)), self.handle)
+
+    def load(self, path, lat: int = 0):
+        """Start lattice `lat` from a checkpoint file, at the same or a
+        2^k-times coarser resolution (fdtd_load_psi)."""
+        with self._ctx():
+            _check(lib.fdtd_load_psi(self.handle, lat, os.fsencode(path)), self.handle)
 
     HISTORY_FIELDS = ("t", "E", "E_b", "norm", "r2", "V", "delta_e", "S0")
 

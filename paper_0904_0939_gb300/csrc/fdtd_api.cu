@@ -817,7 +817,6 @@ int export_field(fdtd_context* c, const void* src, int prec, void* dst, int dt, 
   return cuda_check(c, "export");
 }
 
-// All lattices in one persistent launch (k_batched.cu).
 // Batched configurations already chosen, by device and lattice sizes.
 std::mutex g_btune_mu;
 std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_btune;
@@ -946,6 +945,31 @@ int valid_mask(int mask) {
   for (int ax = 0; ax < 3; ++ax)
     if (((mask >> (2 * ax)) & 3) == 3) return 0;
   return 1;
+}
+
+// ---- checkpoint files ---------------------------------------------------------
+// 64-byte little-endian header followed by n^3 values (x fastest) of dtype.
+struct PsiFileHeader {
+  char magic[8];       // "FDTDPSI1"
+  uint32_t version;    // 1
+  int32_t n;
+  int32_t dtype;       // FDTD_F64 or FDTD_F32
+  int32_t mask;        // symmetry mask of the field
+  double length, mass, dtau;
+  int64_t step;        // steps of the evolve that produced it
+  uint64_t checksum;   // FNV-1a (64 bit) of the data bytes
+};
+static_assert(sizeof(PsiFileHeader) == 64, "checkpoint header layout");
+constexpr char kPsiMagic[8] = {'F', 'D', 'T', 'D', 'P', 'S', 'I', '1'};
+
+// FNV-1a, 64-bit: offset basis 14695981039346656037, prime 1099511628211.
+uint64_t fnv1a64(const unsigned char* p, size_t len) {
+  uint64_t h = 14695981039346656037ull;
+  for (size_t i = 0; i < len; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
 }
 
 void record_start(fdtd_context* c, Lat& L) {
@@ -1170,6 +1194,116 @@ int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_kind) {
   Lat& L = h->lats[lat];
   if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "get_psi: no wavefunction yet");
   return export_field(h, L.psi[L.cur], L.d.precision, psi, dtype, mem_kind, L.n3);
+}
+
+int fdtd_save_psi(fdtd_handle h, int lat, const char* path) {
+  Range r("fdtd_save_psi");
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!path) return fail(h, FDTD_ERR_INVALID_ARG, "save_psi: null path");
+  Lat& L = h->lats[lat];
+  if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "save_psi: no wavefunction yet");
+  PsiFileHeader hd{};
+  std::memcpy(hd.magic, kPsiMagic, 8);
+  hd.version = 1;
+  hd.n = L.d.n;
+  hd.dtype = L.d.precision == FDTD_F64 ? FDTD_F64 : FDTD_F32;
+  hd.mask = L.mask;
+  hd.length = L.d.length;
+  hd.mass = L.p.mass;
+  hd.dtau = L.p.dtau;
+  hd.step = L.last_steps;
+  const size_t bytes = L.n3 * (hd.dtype == FDTD_F64 ? 8 : 4);
+  std::vector<unsigned char> data(bytes);
+  if ((rc = export_field(h, L.psi[L.cur], L.d.precision, data.data(), hd.dtype, FDTD_MEM_HOST, L.n3))) return rc;
+  hd.checksum = fnv1a64(data.data(), bytes);
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, FDTD_ERR_IO, std::string("save_psi: cannot open ") + path);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(data.data(), 1, bytes, f) == bytes;
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(h, FDTD_ERR_IO, std::string("save_psi: write failed for ") + path);
+  return FDTD_OK;
+}
+
+int fdtd_load_psi(fdtd_handle h, int lat, const char* path) {
+  Range r("fdtd_load_psi");
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!path) return fail(h, FDTD_ERR_INVALID_ARG, "load_psi: null path");
+  Lat& L = h->lats[lat];
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, FDTD_ERR_IO, std::string("load_psi: cannot open ") + path);
+  PsiFileHeader hd{};
+  std::vector<unsigned char> data;
+  std::string why;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1) {
+    why = "shorter than its header";
+  } else if (std::memcmp(hd.magic, kPsiMagic, 8) != 0 || hd.version != 1) {
+    why = "not a wavefunction file of this format";
+  } else if (hd.n < 1 || hd.n > 2048 || (hd.dtype != FDTD_F64 && hd.dtype != FDTD_F32) || !valid_mask(hd.mask) ||
+             !(hd.length > 0.0) || !std::isfinite(hd.length)) {
+    why = "header fields out of range";
+  } else {
+    const size_t bytes = (size_t)hd.n * hd.n * hd.n * (hd.dtype == FDTD_F64 ? 8 : 4);
+    data.resize(bytes + 1);
+    const size_t got = std::fread(data.data(), 1, bytes + 1, f);
+    if (got != bytes)
+      why = got < bytes ? "truncated" : "longer than its header says";
+    else if (fnv1a64(data.data(), bytes) != hd.checksum)
+      why = "checksum mismatch (corrupted data)";
+    data.resize(bytes);
+  }
+  std::fclose(f);
+  if (!why.empty()) return fail(h, FDTD_ERR_IO, std::string("load_psi: ") + path + ": " + why);
+  if (std::fabs(hd.length - L.d.length) > 1e-12 * L.d.length)
+    return fail(h, FDTD_ERR_SHAPE, "load_psi: the file's box length differs from the lattice's");
+  int levels = 0;
+  while ((hd.n << levels) < L.d.n) ++levels;
+  if ((hd.n << levels) != L.d.n)
+    return fail(h, FDTD_ERR_SHAPE, "load_psi: the lattice must have the file's n times a power of two");
+  if (levels == 0) {  // same resolution: as fdtd_set_psi
+    if ((rc = import_field(h, data.data(), hd.dtype, FDTD_MEM_HOST, L.psi[L.cur], L.d.precision, L.n3))) return rc;
+  } else {
+    // Sec. VII.G: the saved field is the start at a finer resolution.  Stage
+    // it and every intermediate level in the spare buffer, transfer level by
+    // level (the last into psi[cur]), then renormalise and re-impose its
+    // symmetry as fdtd_upsample does.
+    char* spare = (char*)L.psi[1 - L.cur];
+    size_t off = 0;
+    int nc = hd.n;
+    const size_t n3c = (size_t)nc * nc * nc;
+    if ((rc = import_field(h, data.data(), hd.dtype, FDTD_MEM_HOST, spare, L.d.precision, n3c))) return rc;
+    for (int k = 0; k < levels; ++k) {
+      const size_t in_off = off;
+      const bool last = k == levels - 1;
+      const size_t out_off = in_off + (size_t)nc * nc * nc;
+      with_type(L.d.precision, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        T* out = last ? (T*)L.psi[L.cur] : (T*)(spare + out_off * L.es);
+        launch_upsample<T, T>((const T*)(spare + in_off * L.es), nc, out, L.p.periodic, h->st);
+      });
+      h->stats.launches += 1;
+      off = out_off;
+      nc *= 2;
+    }
+    const int id = 1000000 + (h->check_seq++);
+    const int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
+    launch_state_reset(&L.state[1], 0, h->st);
+    launch_finalize(&L.state[1], L.partials, np, id, 0, L.p, L.d.v_inf, 0.0, 0, 0, h->st);
+    scale_parity_any(h, L, L.psi[L.cur], L.psi[1 - L.cur], h->o.reimpose_parity ? hd.mask : 0, &L.state[1], id,
+                     1 - L.cur, nullptr);
+    h->stats.launches += 2;
+    L.cur ^= 1;
+    LatState st;
+    cudaMemcpyAsync(&st, &L.state[1], sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("load_psi: ") + cudaGetErrorString(e));
+    if (st.status == STATUS_NONFINITE) return fail(h, FDTD_ERR_NONFINITE, "load_psi: non-finite or zero norm");
+  }
+  L.mask = hd.mask;
+  L.has_psi = true;
+  record_start(h, L);
+  return cuda_check(h, "load_psi");
 }
 
 int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
