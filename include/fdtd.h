@@ -272,6 +272,13 @@ FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 FDTD_API int fdtd_save_psi(fdtd_handle h, int lat, const char* path);
 FDTD_API int fdtd_load_psi(fdtd_handle h, int lat, const char* path);
 
+/* Bounds-checking builds (compiled with -DFDTD_CHECK_BOUNDS, e.g.
+ * `python paper_0904_0939_gb300/_build.py --checked`): the number of
+ * shared-memory and output accesses of the TMA tile pipelines that fell
+ * outside their allocation since the handle was created (each was skipped,
+ * not performed).  Other builds return FDTD_ERR_STATE. */
+FDTD_API int fdtd_bounds_violations(fdtd_handle h, int64_t* count);
+
 /* Per-check record of the last fdtd_evolve on lattice `lat` (Secs. III-V):
  * 8 doubles per check {t, E, E_b, norm = sum psi^2 a^3 before the
  * renormalisation, <r^2>, <V>, |dE_b| (-1 at the first check), S0}, oldest

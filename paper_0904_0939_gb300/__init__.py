@@ -22,7 +22,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfdtd.so")
+# FDTD_LIB selects another build of the library, e.g. the bounds-checking
+# libfdtd_checked.so (python paper_0904_0939_gb300/_build.py --checked)
+LIB_PATH = os.environ.get("FDTD_LIB") or os.path.join(_HERE, "libfdtd.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_UNSTABLE_DT, ERR_NONFINITE, ERR_CUDA = -1, -2, -3, -4
@@ -80,7 +82,7 @@ EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
             "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
-            "fdtd_check_history", "fdtd_save_psi", "fdtd_load_psi",
+            "fdtd_check_history", "fdtd_save_psi", "fdtd_load_psi", "fdtd_bounds_violations",
             "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine"]
 
 
@@ -111,6 +113,7 @@ def _load():
         "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
         "fdtd_check_history": [vp, i32, P(d), i32, P(ctypes.c_int)],
         "fdtd_save_psi": [vp, i32, ctypes.c_char_p],
+        "fdtd_bounds_violations": [vp, P(i64)],
         "fdtd_load_psi": [vp, i32, ctypes.c_char_p],
         "fdtd_snapshot_save": [vp, i32, i32],
         "fdtd_snapshot_load": [vp, i32, i32],
@@ -328,6 +331,12 @@ class Solver:
         w = (ctypes.c_double * len(weights))(*weights)
         with self._ctx():
             _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
+
+    def bounds_violations(self) -> int:
+        """Out-of-allocation accesses counted by a bounds-checking build."""
+        c = ctypes.c_int64()
+        _check(lib.fdtd_bounds_violations(self.handle, ctypes.byref(c)), self.handle)
+        return c.value
 
     def save(self, path, lat: int = 0):
         """Write psi of lattice `lat` to a checkpoint file (fdtd_save_psi)."""

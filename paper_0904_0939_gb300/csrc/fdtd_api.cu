@@ -1347,6 +1347,21 @@ int fdtd_last_check(fdtd_handle h, int lat, fdtd_obs* out) {
   return FDTD_OK;
 }
 
+int fdtd_bounds_violations(fdtd_handle h, int64_t* count) {
+  if (!h || !count) return FDTD_ERR_INVALID_ARG;
+#ifdef FDTD_CHECK_BOUNDS
+  int32_t v = 0;
+  cudaMemcpyAsync(&v, h->flags + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("bounds_violations: ") + cudaGetErrorString(e));
+  *count = v;
+  return FDTD_OK;
+#else
+  *count = 0;
+  return fail(h, FDTD_ERR_STATE, "bounds_violations: not a bounds-checking build (-DFDTD_CHECK_BOUNDS)");
+#endif
+}
+
 int fdtd_check_history(fdtd_handle h, int lat, double* out, int cap, int* count) {
   int rc = lat_check(h, lat);
   if (rc) return rc;

@@ -146,6 +146,54 @@ __device__ __forceinline__ int slot_add(int sj, int d) {
 
 __device__ __forceinline__ float4 f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
+// Bounds-checking build (nvcc -DFDTD_CHECK_BOUNDS): every shared-memory
+// load and store of the tile pipelines and every store to the output field
+// goes through Chk, which tests the address against its allocation; an
+// access outside is skipped (a load gives 0) and counted in *bad (the word
+// after the wait budget), so a debug run reports index errors without
+// faulting the GPU.  In the normal build Chk is empty and the accessors are
+// plain loads and stores.
+struct Chk {
+#ifdef FDTD_CHECK_BOUNDS
+  const char* lo = nullptr;
+  const char* hi = nullptr;
+  int32_t* bad = nullptr;
+  __device__ __forceinline__ bool ok(const void* p, int bytes) const {
+    const char* q = (const char*)p;
+    if (q >= lo && q + bytes <= hi) return true;
+    atomicAdd(bad, 1);
+    return false;
+  }
+#endif
+  __device__ __forceinline__ void set(const void* l, const void* h, int32_t* err) {
+#ifdef FDTD_CHECK_BOUNDS
+    lo = (const char*)l;
+    hi = (const char*)h;
+    bad = err + 2;
+#else
+    (void)l, (void)h, (void)err;
+#endif
+  }
+  __device__ __forceinline__ float4 ld4(const float* p) const {
+#ifdef FDTD_CHECK_BOUNDS
+    if (!ok(p, 16)) return make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
+    return f4(p);
+  }
+  __device__ __forceinline__ float ld1(const float* p) const {
+#ifdef FDTD_CHECK_BOUNDS
+    if (!ok(p, 4)) return 0.f;
+#endif
+    return *p;
+  }
+  __device__ __forceinline__ void st4(float* p, float4 v) const {
+#ifdef FDTD_CHECK_BOUNDS
+    if (!ok(p, 16)) return;
+#endif
+    *reinterpret_cast<float4*>(p) = v;
+  }
+};
+
 // One float4 of site updates: c at x..x+3, xl = site x-1, xr = site x+4.
 // The arithmetic of coef_f32 / nbr_sum / update_f32, evaluated on the site
 // pairs (x, x+1) and (x+2, x+3) with packed two-lane FP32 instructions (each
@@ -273,6 +321,7 @@ struct StepCtx {
   bool owner, inside, interior_col, interior_row, fix_l, fix_r;
   int row;
   float hd, om6c, cc;
+  Chk sm, gl;  // shared memory of the item, the output field
 };
 
 // One z-step of a step item.  ROT (compile time, 0..2) names which of the
@@ -302,26 +351,25 @@ __device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K,
     const float* bp = pp.box(slot_add<R>(sj, 1));
     const int p = j;
     const bool need = x.inside && (x.row >= 1 && x.row < G::BH - 1) && (K > 1 || x.interior_col);
-    float4 c = x.owner ? f4(b0 + x.ro) : zero4;
+    float4 c = x.owner ? x.sm.ld4(b0 + x.ro) : zero4;
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (x.fix_l) xl = b0[x.ro - 1];
-    if (x.fix_r) xr = b0[x.ro + 4];
+    if (x.fix_l) xl = x.sm.ld1(b0 + x.ro - 1);
+    if (x.fix_r) xr = x.sm.ld1(b0 + x.ro + 4);
     auto upd = [&]() {
-      return update4(c, xl, xr, f4(b0 + x.ro - BW), f4(b0 + x.ro + BW), f4(bm + x.ro), f4(bp + x.ro),
-                     f4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
+      return update4(c, xl, xr, x.sm.ld4(b0 + x.ro - BW), x.sm.ld4(b0 + x.ro + BW), x.sm.ld4(bm + x.ro),
+                     x.sm.ld4(bp + x.ro), x.sm.ld4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
     };
     if constexpr (K == 1) {
-      if (need && x.interior_row && p >= x.z0 && p < x.z1)
-        *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = upd();
+      if (need && x.interior_row && p >= x.z0 && p < x.z1) x.gl.st4(x.out_col + (size_t)p * x.n * x.n, upd());
     } else if (p >= x.n) {
       if (need) {
-        *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = zero4;
+        x.sm.st4(x.lev + (p & 1) * G::LPLANE + x.lo, zero4);
         w[0][I0] = zero4;
       }
     } else if (p >= 0 && need) {
       const float4 r = upd();
-      *reinterpret_cast<float4*>(x.lev + (p & 1) * G::LPLANE + x.lo) = r;
+      x.sm.st4(x.lev + (p & 1) * G::LPLANE + x.lo, r);
       w[0][I0] = r;
     }
   }
@@ -334,24 +382,23 @@ __device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K,
     const float4 c = w[l - 2][I2];
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (x.fix_l) xl = lp[x.lo - 1];
-    if (x.fix_r) xr = lp[x.lo + 4];
+    if (x.fix_l) xl = x.sm.ld1(lp + x.lo - 1);
+    if (x.fix_r) xr = x.sm.ld1(lp + x.lo + 4);
     auto upd = [&]() {
-      const float4 v = f4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + x.ro);
-      return update4(c, xl, xr, f4(lp + x.lo - LW), f4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v, x.hd,
-                     x.om6c, x.cc);
+      const float4 v = x.sm.ld4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + x.ro);
+      return update4(c, xl, xr, x.sm.ld4(lp + x.lo - LW), x.sm.ld4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v,
+                     x.hd, x.om6c, x.cc);
     };
     if (l == K) {
-      if (need && x.interior_row && p >= x.z0 && p < x.z1)
-        *reinterpret_cast<float4*>(x.out_col + (size_t)p * x.n * x.n) = upd();
+      if (need && x.interior_row && p >= x.z0 && p < x.z1) x.gl.st4(x.out_col + (size_t)p * x.n * x.n, upd());
     } else if (p >= x.n) {
       if (need) {
-        *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = zero4;
+        x.sm.st4(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo, zero4);
         w[l - 1][I0] = zero4;
       }
     } else if (p >= 0 && need) {
       const float4 r = upd();
-      *reinterpret_cast<float4*>(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo) = r;
+      x.sm.st4(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo, r);
       w[l - 1][I0] = r;
     }
   }
@@ -392,6 +439,8 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.hd = half_dtau;
   x.om6c = one_m6c;
   x.cc = cc;
+  x.sm.set(smem, smem + (G::SMEM - 128), err);
+  x.gl.set(out, out + (size_t)n * n * n, err);
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
 
   for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) x.lev[i] = 0.f;
@@ -472,6 +521,8 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
   const bool fix_l = owner && lane == 0 && col > 0;
   const bool fix_r = owner && lane == 31 && col < C4 - 1;
   const int ro = row * BW + 4 * col;
+  Chk sm;
+  sm.set(smem, smem + (G::SMEM - 128), err);
   const float py = coord_f32(yg, n, a);
   float px[4];
 #pragma unroll
@@ -492,14 +543,14 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
     const float* b0 = pp.box(sj);
     const float* bm = pp.box(slot_add<R>(sj, -1));
     const float* bp = pp.box(slot_add<R>(sj, 1));
-    float4 c = owner ? f4(b0 + ro) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 c = owner ? sm.ld4(b0 + ro) : make_float4(0.f, 0.f, 0.f, 0.f);
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (fix_l) xl = b0[ro - 1];
-    if (fix_r) xr = b0[ro + 4];
+    if (fix_l) xl = sm.ld1(b0 + ro - 1);
+    if (fix_r) xr = sm.ld1(b0 + ro + 4);
     if (use) {
-      const float4 ym = f4(b0 + ro - BW), yp = f4(b0 + ro + BW), zm = f4(bm + ro), zp = f4(bp + ro);
-      const float4 v = f4(b0 + G::PLANE + ro);
+      const float4 ym = sm.ld4(b0 + ro - BW), yp = sm.ld4(b0 + ro + BW), zm = sm.ld4(bm + ro), zp = sm.ld4(bp + ro);
+      const float4 v = sm.ld4(b0 + G::PLANE + ro);
       const float pz = coord_f32(j, n, a);
       const float cs[4] = {c.x, c.y, c.z, c.w};
       const float xls[4] = {xl, c.x, c.y, c.z};

@@ -1,0 +1,51 @@
+"""Run by tests/test_gpu_bounds.py with FDTD_LIB pointing at the
+bounds-checking build: every TMA tile-pipeline configuration on small,
+ragged lattices, then the total of out-of-allocation accesses as JSON."""
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import numpy as np  # noqa: E402
+
+import paper_0904_0939_gb300 as fd  # noqa: E402
+import workloads as wl  # noqa: E402
+
+assert fd.LIB_PATH.endswith("libfdtd_checked.so"), fd.LIB_PATH
+bad, cases = 0, 0
+
+
+def run(s):
+    global bad, cases
+    bad += s.bounds_violations()
+    cases += 1
+    s.close()
+
+
+for n in (8, 12, 20, 36, 44, 68, 132):
+    L = 0.4 * n
+    v = wl.harmonic(n, L).astype(np.float32)
+    for depth in (1, 2, 3):
+        for zc in (0, 1, 3, 9, n + 5):
+            s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=5, tol=0.0, temporal_depth=depth,
+                                                                         zchunk=zc))
+            s.set_potential(v)
+            s.init_symmetric(1, wl.ODD_Y)
+            s.evolve(13)
+            s.observables()
+            run(s)
+    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=10, tol=1e-5, tol_relative=1))
+    s.set_potential(v)
+    s.init_symmetric(2, 0)
+    s.evolve(60)  # autotuned: every candidate runs once
+    run(s)
+lats = [fd.Lattice(n, 0.4 * n, fd.F32) for n in (8, 12, 20, 36, 68)]
+s = fd.Solver(lats, fd.default_options(check_every=10, tol=1e-4, tol_relative=1, batched=1))
+for i, l in enumerate(lats):
+    s.set_potential(wl.harmonic(l.n, l.length).astype(np.float32), lat=i)
+    s.init_symmetric(3, wl.ODD_X, lat=i)
+s.evolve(200)  # batched, with its tuning slices
+run(s)
+print(json.dumps({"violations": bad, "cases": cases}))
