@@ -1,0 +1,561 @@
+// Evolution (Secs. III-V): the stencil autotuner, the steps and checks of one
+// lattice on the stream or as a CUDA graph with a device-side loop, and the
+// batched persistent driver.
+#include "api_internal.cuh"
+
+using namespace fdtd;
+using namespace fdtd::api;
+
+namespace fdtd {
+namespace api {
+
+// ---- autotuning of the stencil configuration ---------------------------------
+// Fastest (depth, z-chunk) per (n, precision, device), shared by all handles.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int, bool>> g_tune;
+
+void choose_config(fdtd_context* c, Lat& L) {
+  if (L.depth) return;
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
+  L.plain = false;
+  if (!tma) {
+    L.depth = 1;
+    L.tx = 128;
+    L.zc = 0;
+    L.plain = true;
+    return;
+  }
+  if (c->o.temporal_depth > 0 || !c->o.autotune) {
+    L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
+    L.tx = L.d.n > 64 ? 128 : 64;
+    L.zc = c->o.zchunk > 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
+    return;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto key = std::make_tuple(L.d.n, L.d.precision, dev);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      std::tie(L.depth, L.tx, L.zc, L.plain) = it->second;
+      return;
+    }
+  }
+  Range r("stencil autotune");
+  // time each candidate (every one of them is bit-identical):
+  // psi[cur] -> psi[1-cur], psi[cur] is only read
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int n = L.d.n;
+  double best = 0.0;
+  int bd = auto_depth(n, L.d.precision), bt = n > 64 ? 128 : 64, bz = tma_zchunk(n, bd, bt);
+  bool bp = false;
+  auto time_it = [&](auto&& launch, int depth) {
+    launch();
+    const int reps = 3;
+    cudaEventRecord(e0, c->st);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->stats.launches += reps + 1;
+    return (double)L.n3 * depth * reps / (ms > 0.f ? ms : 1e-6);
+  };
+  // the plain one-step kernel
+  {
+    double rate = time_it(
+        [&]() {
+          launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p,
+                                 nullptr, c->st);
+        },
+        1);
+    best = rate;
+    bd = 1;
+    bp = true;
+  }
+  for (int ti = 0; ti < 2; ++ti) {
+    const int tx = ti ? 128 : 64;
+    if (tx == 128 && n <= 64) continue;
+    for (int d = 1; d <= blocked_max_depth(); ++d) {
+      // spans: z-chunks n / 2^i (depth 1 repeats no planes, deeper levels
+      // repeat 2(d-1) per item, so short chunks only for depth 1) and the
+      // spans that fill the resident blocks in one, two or three waves
+      std::vector<int> spans;
+      for (int div = 1; div <= 128; div *= 2) {
+        const int zc = (n + div - 1) / div;
+        if (zc >= (d == 1 ? 2 : std::max(8, 4 * d))) spans.push_back(zc);
+      }
+      const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx);
+      for (int m = 1; m <= 3; ++m) spans.push_back((int)std::max(1LL, (total + m * slots - 1) / (m * slots)));
+      std::sort(spans.begin(), spans.end());
+      spans.erase(std::unique(spans.begin(), spans.end()), spans.end());
+      for (int zc : spans) {
+        double rate = time_it(
+            [&]() {
+              launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx,
+                              zc, nullptr, c->flags + 1, c->st);
+            },
+            d);
+        if (rate > best) {
+          best = rate;
+          bd = d;
+          bt = tx;
+          bz = zc;
+          bp = false;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int32_t err = 0;
+  cudaMemcpy(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (err) {  // the timed launches did no work: keep the heuristic, cache nothing
+    L.depth = auto_depth(n, L.d.precision);
+    L.tx = n > 64 ? 128 : 64;
+    L.zc = tma_zchunk(n, L.depth, L.tx);
+    return;
+  }
+  L.depth = bd;
+  L.tx = bt;
+  L.zc = bz;
+  L.plain = bp;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = std::make_tuple(bd, bt, bz, bp);
+}
+
+// Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows),
+// the first of them being step t0 of the current evolve.
+void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0) {
+  const int prec = L.d.precision;
+  choose_config(c, L);
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+  const int depth = tma ? L.depth : 1;
+  while (count > 0) {
+    int k = (int)std::min<int64_t>(count, depth);
+    const long ev = prof_begin(c);
+    if (prec == FDTD_F64) {
+      launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
+    } else if (prec == FDTD_F32) {
+      if (tma)
+        launch_step_tma(L.maps[L.tx == 128][k - 1][L.cur], L.maps[L.tx == 128][k - 1][2], (float*)L.psi[1 - L.cur],
+                        L.p, k, L.tx, k == depth ? L.zc : 0, active, c->flags + 1, c->st);
+      else
+        launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
+                               c->st);
+    } else {
+      launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
+                                     (const float*)L.v, L.p, active, c->st);
+    }
+    prof_end(c);
+    c->stats.launches += 1;
+    // algorithmic bytes: psi read + psi write + V (FP64: A and cB) read once per launch
+    c->pending.push_back({t0, (int64_t)L.n3 * k, (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0)), ev});
+    L.cur ^= 1;
+    count -= k;
+    t0 += k;
+  }
+}
+
+int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* active) {
+  int np = 0;
+  if (L.tma_ok && (psi == L.psi[0] || psi == L.psi[1])) {
+    np = launch_sums_tma(L.sums_maps[psi == L.psi[1]], L.sums_maps[2], L.p, L.partials, active, c->flags + 1, c->st);
+    c->stats.launches += 1;
+    return np;
+  }
+  with_type(L.d.precision, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    np = launch_sums<T>((const T*)psi, L.v, L.p, L.partials, active, c->st);
+  });
+  c->stats.launches += 1;
+  return np;
+}
+
+void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int mask, const LatState* s, int id,
+                      int out_idx, LatState* sw) {
+  with_type(L.d.precision, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    launch_scale_parity<T>((const T*)in, (T*)out, L.d.n, mask, s, id, out_idx, sw, c->st);
+  });
+  c->stats.launches += 1;
+}
+
+// One check of Secs. III-V on psi[cur]: sums, finalize, renormalise + mask.
+void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
+  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, 0,
+                  0, nullptr, L.hist);
+  c->stats.launches += 1;
+  int mask = c->o.reimpose_parity ? L.mask : 0;
+  scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], check_id, 1 - L.cur, &L.state[0]);
+  L.cur ^= 1;
+}
+
+int read_state(fdtd_context* c, Lat& L) {
+  int32_t err = 0;
+  cudaMemcpyAsync(&L.host_state, &L.state[0], sizeof(LatState), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("evolve: ") + cudaGetErrorString(e));
+  flush_pending(c, L.host_state.converged ? L.host_state.step : INT64_MAX);
+  if (err) return fail(c, FDTD_ERR_TIMEOUT, "evolve: a bounded device-side wait expired in the stencil kernel");
+  return FDTD_OK;
+}
+
+// The check of enqueue_check in device-sequenced form (inside the graph).
+void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditionalHandle cond) {
+  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  launch_finalize(&L.state[0], L.partials, np, 0, 0, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, (int)ce,
+                  cond, c->flags + 1, L.hist);
+  c->stats.launches += 1;
+  int mask = c->o.reimpose_parity ? L.mask : 0;
+  scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], -1, 1 - L.cur, &L.state[0]);
+  L.cur ^= 1;
+}
+
+// Stencil launches and algorithmic bytes of one check_every-step segment.
+void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, double* bytes) {
+  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+  const int depth = tma ? L.depth : 1;
+  *launches = (ce + depth - 1) / depth;
+  *bytes = (double)*launches * L.n3 * (2.0 * L.es + (L.d.precision == FDTD_F64 ? 16.0 : 4.0));
+}
+
+// Build (or reuse) the evolve graph of lattice L for its current start
+// buffer: a while node whose body is two (check, segment) pairs -- a segment
+// flips the ping-pong buffers an odd number of times, a pair an even number,
+// so the body is the same at every iteration.  Returns false if the graph
+// cannot be made (the caller then uses the stream).
+bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
+  choose_config(c, L);  // autotuning synchronises: never inside a capture
+  const int mask = c->o.reimpose_parity ? L.mask : 0;
+  const int b = L.cur;
+  const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain, ce};
+  if (L.graph_exec[b] && std::equal(key, key + 6, L.graph_key[b])) return true;
+  release_graph(L, b);
+  Range r("evolve graph build");
+  if (L.tma_ok && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
+    (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx);  // occupancy query outside the capture
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  cudaGraphNode_t node;
+  if (cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const int cur0 = L.cur;
+  const int64_t launches0 = c->stats.launches;
+  const size_t pending0 = c->pending.size();
+  // capture on the private stream (the handle's stream may be the legacy
+  // one, which cannot be captured); the graph is launched on the handle's
+  if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_st = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  cudaStream_t user_st = c->st;
+  c->st = c->cap_st;
+  bool ok = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess;
+  if (ok) {
+    for (int rep = 0; rep < 2; ++rep) {
+      enqueue_check_seq(c, L, ce, cond);
+      run_steps(c, L, ce, &L.state[0].active, 0);
+    }
+    cudaGraph_t captured = nullptr;
+    ok = cudaStreamEndCapture(c->st, &captured) == cudaSuccess && L.cur == cur0;
+  }
+  c->st = user_st;
+  L.graph_kernels = c->stats.launches - launches0;
+  c->stats.launches = launches0;
+  c->pending.resize(pending0);
+  L.cur = cur0;
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (ok && !c->ev_in) {
+    ok = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphUpload(exec, c->cap_st) == cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  L.graph[b] = g;
+  L.graph_exec[b] = exec;
+  std::copy(key, key + 6, L.graph_key[b]);
+  return true;
+}
+
+int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
+  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
+  launch_state_reset(&L.state[0], 0, c->st);
+  c->stats.launches += 1;
+  const int64_t ce = c->o.check_every;
+  int64_t t = 0;
+  int check_id = 0;
+  int groups = 2;
+  bool done = false;
+  if (c->o.graphs && c->profiling) {
+    // the timed sample: two segments through the stream, every stencil
+    // launch between CUDA events (a graph loop body cannot hold events)
+    for (int i = 0; i < 2 && t + ce <= max_steps; ++i) {
+      enqueue_check(c, L, check_id++, t);
+      run_steps(c, L, ce, &L.state[0].active, t);
+      t += ce;
+    }
+    int rc = cuda_check(c, "evolve launch");
+    if (rc) return rc;
+    if ((rc = read_state(c, L))) return rc;
+    if (!L.host_state.active) done = true;
+  }
+  // full pairs of segments in one graph launch, the convergence check
+  // ending the loop on the device
+  const int64_t pairs = (!done && c->o.graphs) ? std::min<int64_t>((max_steps - t) / (2 * ce), 1 << 28) : 0;
+  if (pairs > 0 && ensure_graph(c, L, ce)) {
+    const int64_t t_end = t + 2 * pairs * ce;
+    launch_state_reset(&L.state[0], 2, c->st, check_id + (int)(2 * pairs));
+    c->stats.launches += 1;
+    // launched on the private stream, ordered after and before the handle's
+    // stream by events (a graph launched into the legacy stream paid about
+    // half a millisecond per launch)
+    cudaEventRecord(c->ev_in, c->st);
+    cudaStreamWaitEvent(c->cap_st, c->ev_in, 0);
+    cudaGraphLaunch(L.graph_exec[L.cur], c->cap_st);
+    cudaEventRecord(c->ev_out, c->cap_st);
+    cudaStreamWaitEvent(c->st, c->ev_out, 0);
+    c->stats.graph_launches += 1;
+    int rc = cuda_check(c, "evolve graph launch");
+    if (rc) return rc;
+    if ((rc = read_state(c, L))) return rc;
+    const LatState& hs = L.host_state;
+    c->stats.launches += (int64_t)((hs.checks - check_id + 1) / 2) * L.graph_kernels;
+    const int64_t advanced = std::max<int64_t>(0, (hs.active ? t_end : hs.step) - t);  // steps taken while active
+    int64_t seg_l;
+    double seg_b;
+    segment_work(c, L, ce, &seg_l, &seg_b);
+    c->stats.stencil_launches += advanced / ce * seg_l;
+    c->stats.stencil_site_updates += advanced * (int64_t)L.n3;
+    c->stats.stencil_bytes += (double)(advanced / ce) * seg_b;
+    if (!hs.active) {
+      done = true;
+    } else {
+      t = t_end;
+      check_id = hs.checks;
+    }
+  }
+  int prev_checks = 0;
+  double prev_delta = -1.0;
+  while (!done) {
+    for (int g = 0; g < groups && !done; ++g) {
+      enqueue_check(c, L, check_id++, t);
+      if (t >= max_steps) {
+        done = true;
+        break;
+      }
+      int64_t nst = std::min<int64_t>(ce, max_steps - t);
+      run_steps(c, L, nst, &L.state[0].active, t);
+      t += nst;
+    }
+    int rc = cuda_check(c, "evolve launch");
+    if (rc) return rc;
+    rc = read_state(c, L);
+    if (rc) return rc;
+    if (!L.host_state.active) done = true;
+    // segments to enqueue before the next look: predicted from the decay of
+    // |dE_b| per check, so that little work is queued past convergence
+    const LatState& hs = L.host_state;
+    int next = std::min(groups * 2, 32);
+    if (c->o.tol > 0.0 && hs.delta_e > 0.0 && prev_delta > 0.0 && hs.checks > prev_checks) {
+      const double rate = std::pow(hs.delta_e / prev_delta, 1.0 / (hs.checks - prev_checks));
+      const double thr = c->o.tol * (c->o.tol_relative ? std::fabs(hs.ebind) : 1.0);
+      if (rate < 0.999 && thr > 0.0) {
+        double m = std::log(thr / hs.delta_e) / std::log(rate);
+        next = (int)std::max(1.0, std::min(32.0, std::ceil(m)));
+      }
+    }
+    prev_checks = hs.checks;
+    prev_delta = hs.delta_e;
+    groups = next;
+  }
+  if (L.host_state.status == STATUS_NONFINITE)
+    return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+  L.cur = L.host_state.cur;
+  L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+  return FDTD_OK;
+}
+
+// Batched configurations already chosen, by device and lattice sizes.
+std::mutex g_btune_mu;
+std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_btune;
+
+// All lattices of the handle in persistent launches.  With autotuning on
+// (and no depth given) the first launches of a new set of lattice sizes are
+// slices of 2 x check_every steps, one per (depth 1..3, z-chunk 16/32/64)
+// candidate, timed with CUDA events; the fastest runs the rest in one
+// launch.  Every candidate computes the same bits, so tuning costs no extra
+// work, only launch boundaries.
+int evolve_batched(fdtd_context* c, int64_t max_steps) {
+  const int count = (int)c->lats.size();
+  if (count > batched_max_lattices()) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: too many lattices for batched mode");
+  for (auto& L : c->lats)
+    if (!L.tma_ok) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: batched mode needs FP32 lattices with n % 4 == 0");
+  const int64_t ce = c->o.check_every;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> sizes;
+  for (auto& L : c->lats) sizes.push_back(L.d.n);
+  const auto key = std::make_pair(dev, sizes);
+  std::vector<std::pair<int, int>> cands;  // (depth, z-chunk)
+  if (c->o.temporal_depth > 0 || !c->o.autotune) {
+    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, c->o.zchunk > 0 ? c->o.zchunk : 32});
+  } else {
+    std::lock_guard<std::mutex> lock(g_btune_mu);
+    auto it = g_btune.find(key);
+    if (it != g_btune.end()) {
+      cands.push_back(it->second);
+    } else {
+      for (int d = 1; d <= 3; ++d)
+        for (int zc : {16, 32, 64}) cands.push_back({d, zc});
+    }
+  }
+  const bool tuning = cands.size() > 1;
+  for (auto& L : c->lats) {
+    launch_state_reset(&L.state[0], 0, c->st);
+    c->stats.launches += 1;
+  }
+  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
+  std::vector<char> table(batched_entry_bytes() * count + 64);
+  char* base = table.data() + ((64 - ((uintptr_t)table.data() & 63)) & 63);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int64_t t = 0, steps = 0, slices = 0;
+  double best_rate = -1.0;
+  std::pair<int, int> best = cands[0];
+  std::vector<int64_t> step_at(count, 0);  // steps each lattice advanced while active
+  int rc = FDTD_OK;
+  auto slice = [&](std::pair<int, int> cd, int64_t t_end) -> int {
+    for (int l = 0; l < count; ++l) {
+      Lat& L = c->lats[l];
+      if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
+                       (const float*)L.v, L.partials, &L.state[0], L.hist, L.p, L.mask, L.cur, L.d.v_inf,
+                       cd.second))
+        return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
+    }
+    cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
+    int grid = 0;
+    cudaEventRecord(e0, c->st);
+    int e = batched_launch(c->batch_ws, count, max_steps, t, t_end, t > 0, 0, (int)ce, c->o.tol, c->o.tol_relative,
+                           c->o.reimpose_parity, cd.first, c->flags + 1, c->st, &c->batch_graphs, &steps, &grid);
+    cudaEventRecord(e1, c->st);
+    if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
+    c->stats.launches += 1;
+    c->stats.graph_launches += 1;
+    ++slices;
+    int r = cuda_check(c, "evolve (batched)");
+    if (r) return r;
+    double upd = 0.0;
+    for (int l = 0; l < count; ++l) {
+      Lat& L = c->lats[l];
+      const bool was_active = L.host_state.active || t == 0;
+      if ((r = read_state(c, L))) return r;
+      if (L.host_state.status == STATUS_NONFINITE)
+        return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+      L.cur = L.host_state.cur;
+      if (was_active) {
+        const int64_t upto = L.host_state.active ? steps : L.host_state.step;
+        upd += (double)L.n3 * (double)std::max<int64_t>(0, upto - t);
+        step_at[l] = std::max(step_at[l], upto);
+      }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c->profiling) c->stats.stencil_ms += ms;
+    const double rate = ms > 0.f ? upd / ms : 0.0;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = cd;
+    }
+    t = steps;
+    return FDTD_OK;
+  };
+  bool any = true;
+  for (size_t i = 0; tuning && i < cands.size() && any && t < max_steps; ++i) {
+    if ((rc = slice(cands[i], std::min<int64_t>(max_steps, t + 2 * ce)))) break;
+    any = false;
+    for (auto& L : c->lats) any |= L.host_state.active != 0;
+  }
+  if (!rc && tuning && best_rate > 0.0) {
+    std::lock_guard<std::mutex> lock(g_btune_mu);
+    g_btune[key] = best;
+  }
+  if (!rc && any && t < max_steps) rc = slice(best, max_steps);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  // the persistent launches are the stencil launches of a batched evolve
+  for (int l = 0; l < count; ++l) {
+    Lat& L = c->lats[l];
+    L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+    c->stats.stencil_site_updates += (int64_t)L.n3 * step_at[l];
+    c->stats.stencil_bytes += (double)L.n3 * 12.0 * ((step_at[l] + best.first - 1) / best.first);
+  }
+  c->stats.stencil_launches += slices;
+  if (c->profiling) c->stats.stencil_timed_launches += slices;
+  c->batch_depth = best.first;
+  c->batch_zc = best.second;
+  return FDTD_OK;
+}
+
+}  // namespace api
+}  // namespace fdtd
+
+extern "C" {
+
+int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
+  Range r("fdtd_evolve");
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (max_steps < 0) return fail(h, FDTD_ERR_INVALID_ARG, "evolve: max_steps < 0");
+  for (auto& L : h->lats)
+    if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "evolve: set_potential and init/set_psi first");
+  int rc = FDTD_OK;
+  if (h->o.batched) {
+    rc = evolve_batched(h, max_steps);
+  } else {
+    for (auto& L : h->lats) {
+      rc = evolve_one(h, L, max_steps);
+      if (rc) return rc;
+    }
+  }
+  if (rc) return rc;
+  int64_t mx = 0;
+  bool all_conv = true;
+  for (auto& L : h->lats) {
+    mx = std::max(mx, L.last_steps);
+    all_conv = all_conv && L.host_state.converged;
+  }
+  if (steps_done) *steps_done = mx;
+  return (h->o.tol > 0.0 && !all_conv) ? FDTD_NOT_CONVERGED : FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,4 +1,4 @@
-// Internal launch interface between the C ABI (fdtd_api.cu) and the kernels.
+// Internal launch interface between the C ABI (api_*.cu) and the kernels.
 #pragma once
 #include <utility>
 #include <cuda.h>
