@@ -40,9 +40,9 @@ SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 TOL = 1e-6
 SEED = 904939
 # dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
-# from an ncu capture of the current kernel, by (depth, span); a tuned
-# configuration without a capture reports traffic null
-TRAFFIC_256 = {(3, 54): 238_210_048}
+# from an ncu capture of the current kernel, by (depth, span, tile width,
+# tile height); a tuned configuration without a capture reports traffic null
+TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048}
 
 
 def dist_env():
@@ -96,7 +96,7 @@ def run_step(fd, pots, seed, opts):
                 tot["fine_updates"] += st["stencil_site_updates"]
                 tot["fine_launches"] += st["stencil_launches"]
                 tot["fine_timed"] += st["stencil_timed_launches"]
-                tot["config"] = s.tuned_config()
+                tot["config"] = s.tuned_config() + s.tuned_kernel()
             ev1.record()
             ev1.synchronize()
             tot["level_ms"][f"{name}_{n}"] = ev0.elapsed_time(ev1)
@@ -542,7 +542,7 @@ def main():
     bytes_launch = fine_bytes / max(1, fine_launches)
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9 if ms_launch else None
     eff = fine_upd / max(1, fine_launches) * 12.0 / (ms_launch * 1e-3) / 1e9 / hbm if ms_launch else None
-    depth, zc = tot["config"] if tot and tot["config"] else (None, None)
+    depth, zc, tx, ty = tot["config"] if tot and tot["config"] else (None, None, None, None)
     h2d = sum(n**3 * 4 for n in LEVELS) * len(SECTORS)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -553,8 +553,8 @@ def main():
                    "length": LENGTH, "tol_rel": TOL, "check_every": 100, "precision": "fp32 stencil, fp64 sums",
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc)),
-                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, span {zc})" if zc
+                     "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc, tx, ty)),
+                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, span {zc}, tile {tx}x{ty})" if zc
                                 else "k_step_f32 (256^3 level, one-step z-marching)"),
                      "launches": fine_launches, "timed_launches": fine_timed, "ms_per_launch": ms_launch,
                      "bytes_per_launch": bytes_launch, "peak_kind": peak_note,

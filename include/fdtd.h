@@ -253,6 +253,12 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
  * depth and z-planes per item of its persistent launch. */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
+/* The tile of that TMA stencil: tile_x x tile_y output sites of one z-plane
+ * per block and step (tile_x 64 or 128, tile_y 16).  Both are 0 when the
+ * one-step z-marching kernel is in use (FP64, BF16, periodic lattices,
+ * stencil_kernel = 1, or the autotuner's choice) and for a batched handle. */
+FDTD_API int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y);
+
 /* Checkpoint files (Sec. VII.G: a run saves its wavefunction, and a later
  * run reads it back as its initial condition, adjusting the resolution).
  * File layout, little-endian: a 64-byte header {char magic[8] = "FDTDPSI1";

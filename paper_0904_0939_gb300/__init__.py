@@ -82,6 +82,7 @@ EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_
             "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
             "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
+            "fdtd_tuned_kernel",
             "fdtd_check_history", "fdtd_save_psi", "fdtd_load_psi", "fdtd_bounds_violations",
             "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine"]
 
@@ -111,6 +112,7 @@ def _load():
         "fdtd_reset_stats": [vp],
         "fdtd_set_profiling": [vp, i32],
         "fdtd_tuned_config": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
+        "fdtd_tuned_kernel": [vp, i32, P(ctypes.c_int), P(ctypes.c_int)],
         "fdtd_check_history": [vp, i32, P(d), i32, P(ctypes.c_int)],
         "fdtd_save_psi": [vp, i32, ctypes.c_char_p],
         "fdtd_bounds_violations": [vp, P(i64)],
@@ -368,6 +370,14 @@ class Solver:
         with self._ctx():
             _check(lib.fdtd_tuned_config(self.handle, lat, ctypes.byref(d), ctypes.byref(z)), self.handle)
         return d.value, z.value
+
+    def tuned_kernel(self, lat: int = 0) -> tuple[int, int]:
+        """(tile width in x, tile height in y) of the TMA stencil for lattice
+        `lat`; (0, 0) when the one-step kernel is in use."""
+        t, r = ctypes.c_int(), ctypes.c_int()
+        with self._ctx():
+            _check(lib.fdtd_tuned_kernel(self.handle, lat, ctypes.byref(t), ctypes.byref(r)), self.handle)
+        return t.value, r.value
 
     def stats(self) -> dict:
         s = Stats()

@@ -669,6 +669,23 @@ int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
   return cuda_check(h, "tuned_config");
 }
 
+int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y) {
+  int rc = lat_check(h, lat);
+  if (rc) return rc;
+  if (!tile_x || !tile_y) return fail(h, FDTD_ERR_INVALID_ARG, "tuned_kernel: null output");
+  Lat& L = h->lats[lat];
+  *tile_x = *tile_y = 0;
+  if (h->o.batched) return FDTD_OK;
+  if (L.has_v && L.has_psi) choose_config(h, L);
+  if (L.tma_ok && h->o.stencil_kernel == 0 && !L.plain && L.depth > 0) {
+    int bw = 0, bh = 0;
+    tma_box(L.depth, L.tx, &bw, &bh);
+    *tile_x = L.tx;
+    *tile_y = bh - 2 * L.depth;
+  }
+  return cuda_check(h, "tuned_kernel");
+}
+
 int fdtd_get_stats(fdtd_handle h, fdtd_stats* out) {
   if (!h || !out) return FDTD_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->st);

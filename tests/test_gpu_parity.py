@@ -345,6 +345,10 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         s.init_symmetric(31, wl.ODD_Z)
         s.evolve(100)
         outs[name] = s.get_psi(dtype=np.float32)
+        if name == "plain":
+            assert s.tuned_kernel() == (0, 0)
+        elif name.startswith("k"):
+            assert s.tuned_kernel() == (128 if n > 64 else 64, 16), name
         s.close()
     for name, _ in variants[1:]:
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
