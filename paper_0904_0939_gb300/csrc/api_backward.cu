@@ -1,5 +1,6 @@
 // Gradients through the unrolled evolution: fdtd_backward (sqrt(T)
-// checkpoints, segment recompute, the split adjoint step).
+// checkpoints, segment recompute, the adjoint step: one fused pass for FP32
+// lattices, a pointwise and a stencil pass for FP64).
 #include "api_internal.cuh"
 
 using namespace fdtd;
@@ -33,7 +34,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
   // forward pass from the recorded start, saving every K-th field
   L.cur = 0;
   cudaMemcpyAsync(L.psi[0], L.psi0, fb, cudaMemcpyDeviceToDevice, h->st);
-  for (int64_t t = 0; t < T; ++t) {
+  for (int64_t t = 0; t < T;) {
     if (t % ce == 0) {
       int id = 2000000 + (h->check_seq++);
       int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
@@ -45,7 +46,10 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
     }
     if (t % K == 0)
       cudaMemcpyAsync(field(L.pool, t / K), L.psi[L.cur], fb, cudaMemcpyDeviceToDevice, h->st);
-    run_steps(h, L, 1, nullptr);
+    // the steps up to the next check or checkpoint, temporally blocked
+    const int64_t next = std::min(std::min((t / ce + 1) * ce, (t / K + 1) * K), T);
+    run_steps(h, L, next - t, nullptr, t);
+    t = next;
   }
   // seed the adjoint with the derivative of the loss at psi_T
   int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
@@ -88,16 +92,21 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
     for (int64_t t = t1; t > t0; --t) {
       with_type(L.d.precision, [&](auto* tag) {
         using T_ = std::remove_pointer_t<decltype(tag)>;
-        if constexpr (!std::is_same_v<T_, __nv_bfloat16>) {
+        if constexpr (std::is_same_v<T_, float>) {
+          launch_adjoint_step_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
+                                  (const float*)raw_of(t), (const float*)L.v, (float*)L.lam[1 - lc], L.gv, L.p, h->st);
+        } else if constexpr (std::is_same_v<T_, double>) {
           launch_adjoint_pointwise<T_>((const T_*)L.lam[lc], (const T_*)field(L.seg, t - 1 - t0), (const T_*)raw_of(t),
                                        L.v, L.coefCB, (T_*)L.bw_u, L.gv, L.p, h->st);
           launch_adjoint_stencil<T_>((const T_*)L.bw_u, (const T_*)L.lam[lc], (T_*)L.lam[1 - lc], L.v, L.coefA, L.p,
                                      h->st);
+        }
+        if constexpr (!std::is_same_v<T_, __nv_bfloat16>) {
           if ((t - 1) % ce == 0)
             launch_parity_adjoint_scale<T_>((T_*)L.lam[1 - lc], L.d.n, mask, L.scales + (t - 1) / ce, h->st);
         }
       });
-      h->stats.launches += ((t - 1) % ce == 0) ? 3 : 2;
+      h->stats.launches += ((t - 1) % ce == 0 ? 1 : 0) + (L.d.precision == FDTD_F64 ? 2 : 1);
       lc ^= 1;
     }
   }

@@ -9,10 +9,11 @@
 // at one site gives  d psi'(s)/d V(s) = -(dtau/2) B(s) (psi'(s) + psi(s)),
 // with psi' the step's raw output (before any check).
 //
-// One adjoint step is split in two passes: a pointwise pass (u = B lam and
-// the g_V accumulation, one thread per site) and a z-marching stencil pass
-// over u (launch_adjoint_stencil in k_core.cu).  The seed and the transpose
-// of the checks are one thread per site.
+// An FP64 adjoint step is split in two passes: a pointwise pass (u = B lam
+// and the g_V accumulation, one thread per site) and a z-marching stencil
+// pass over u (launch_adjoint_stencil in k_core.cu); an FP32 step is one
+// fused z-marching pass (launch_adjoint_step_f32 in k_core.cu).  The seed and
+// the transpose of the checks are one thread per site.
 #include "common.cuh"
 #include "kernels.cuh"
 

@@ -38,11 +38,11 @@ struct RowTile {
 
 // P: periodic boundaries (every load wraps modulo n, so the tile's rim and
 // the z-neighbours of the first and last planes come from the opposite side);
-// otherwise sites beyond the lattice read as zero.
-template <typename T, bool P, typename Body>
-__device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, RowTile<typename Store<T>::C>& tile,
-                                       Body&& body) {
-  using C = typename Store<T>::C;
+// otherwise sites beyond the lattice read as zero.  The marched field is
+// get(i) at the site of linear index i: a stored field, or one computed from
+// stored fields as it is loaded.
+template <typename C, bool P, typename Get, typename Body>
+__device__ __forceinline__ void zmarch_fn(int n, int zc, RowTile<C>& tile, Get&& get, Body&& body) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
   const int z0 = blockIdx.z * zc;
@@ -54,10 +54,10 @@ __device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, 
         q %= n;
         return q < 0 ? q + n : q;
       };
-      return Store<T>::ld(in + site_index(wrap(xx), wrap(yy), wrap(zz), n));
+      return get(site_index(wrap(xx), wrap(yy), wrap(zz), n));
     } else {
       if ((unsigned)xx < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)zz < (unsigned)n)
-        return Store<T>::ld(in + site_index(xx, yy, zz, n));
+        return get(site_index(xx, yy, zz, n));
       return C(0);
     }
   };
@@ -90,6 +90,13 @@ __device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, 
     hxm = hxm_n;
     hxp = hxp_n;
   }
+}
+
+template <typename T, bool P, typename Body>
+__device__ __forceinline__ void zmarch(const T* __restrict__ in, int n, int zc, RowTile<typename Store<T>::C>& tile,
+                                       Body&& body) {
+  zmarch_fn<typename Store<T>::C, P>(
+      n, zc, tile, [in](size_t i) { return Store<T>::ld(in + i); }, body);
 }
 
 // ------------------------------------------------------------------ update
@@ -183,6 +190,44 @@ template void launch_adjoint_stencil<double>(const double*, const double*, doubl
                                              const Params&, cudaStream_t);
 template void launch_adjoint_stencil<float>(const float*, const float*, float*, const void*, const double*,
                                             const Params&, cudaStream_t);
+
+// One whole FP32 adjoint step in one pass.  The FP32 update is
+// psi' = B (c Adj psi + alpha psi), i.e. M = diag(B) (c Adj + diag(alpha)),
+// so with u = B lam
+//   M^T lam = c Adj(u) + alpha u,
+// and the site derivative d psi'(s)/dV(s) = -(dtau/2) B (psi' + psi) gives
+//   g_V += -(dtau/2) u (psi_next + psi_prev).
+// u is formed as the z-march loads it (B from V as the forward computes it),
+// the per-site terms are FP32 and g_V accumulates in FP64.
+template <bool P>
+__global__ void __launch_bounds__(TX* TY) k_adjoint_step_f32(const float* __restrict__ lam,
+                                                             const float* __restrict__ psi_prev,
+                                                             const float* __restrict__ psi_next,
+                                                             const float* __restrict__ v, float* __restrict__ lam_out,
+                                                             double* __restrict__ gv, int n, int zc, float half_dtau,
+                                                             float one_m6c, float cc) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ RowTile<float> tile;
+  zmarch_fn<float, P>(
+      n, zc, tile,
+      [&](size_t i) { return __fmul_rn(coef_f32(__ldg(v + i), half_dtau, one_m6c).b, __ldg(lam + i)); },
+      [&](int x, int y, int z, bool act, float cu, float xm, float xp, float ym, float yp, float zm, float zp) {
+        if (!act) return;
+        const size_t i = site_index(x, y, z, n);
+        const float alpha = __fsub_rn(one_m6c, __fmul_rn(half_dtau, __ldg(v + i)));
+        lam_out[i] = __fmaf_rn(cc, nbr_sum(xm, xp, ym, yp, zm, zp), __fmul_rn(alpha, cu));
+        const float d = __fmul_rn(__fmul_rn(-half_dtau, cu), __fadd_rn(__ldg(psi_next + i), __ldg(psi_prev + i)));
+        gv[i] = __dadd_rn(gv[i], (double)d);
+      });
+}
+
+void launch_adjoint_step_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v,
+                             float* lam_out, double* gv, const Params& p, cudaStream_t st) {
+  Tiling t = tiling_for(p.n, 1216);
+  launch_pdl(p.periodic ? k_adjoint_step_f32<true> : k_adjoint_step_f32<false>, t.grid, dim3(TX, TY), 0, st, lam,
+             psi_prev, psi_next, v, lam_out, gv, p.n, t.zc, p.half_dtau_f, p.one_m6c_f, p.c_f);
+}
 
 // ------------------------------------------------------------------ sums
 __device__ __forceinline__ void block_sum4_store(double v0, double v1, double v2, double v3, double* dst) {

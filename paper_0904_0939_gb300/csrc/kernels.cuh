@@ -185,6 +185,9 @@ void launch_adjoint_pointwise(const T* lam, const T* psi_prev, const T* psi_next
 template <typename T>
 void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v, const double* coefA, const Params& p,
                             cudaStream_t st);
+// one fused FP32 adjoint step (u = B lam, g_V accumulation, lam_out = M^T lam)
+void launch_adjoint_step_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v,
+                             float* lam_out, double* gv, const Params& p, cudaStream_t st);
 template <typename T>
 void launch_adjoint_seed(const T* psi, const void* v, const LatState* s, double w_e, double w_r, T* lam, double* gv,
                          const Params& p, cudaStream_t st);
