@@ -66,46 +66,49 @@ def potentials(resident: bool, device):
 
 
 def run_step(fd, pots, seed, opts):
-    """Both sectors, three levels each.  Returns a dict of totals: site
-    updates, kernel launches, and the stencil time / algorithmic bytes of the
-    finest level (the dominant kernel), plus per-level results."""
+    """Both sectors, three levels each: one handle per level holding the two
+    sectors' lattices (their evolve loops run concurrently, each lattice
+    upsampled from its own sector's coarser level).  Returns a dict of
+    totals: site updates, kernel launches, and the stencil time / algorithmic
+    bytes of the finest level (the dominant kernel), plus per-level results."""
     import torch
 
     tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0,
            "fine_launches": 0, "fine_timed": 0, "results": {}, "config": None, "level_ms": {}}
-    for name, mask in SECTORS:
-        prev = None
-        for lvl, n in enumerate(LEVELS):
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record()
-            s = fd.Solver(fd.Lattice(n, LENGTH, fd.F32), opts)
-            s.set_profiling(n == LEVELS[-1])
-            s.set_potential(pots[lvl])
+    prev = None
+    for lvl, n in enumerate(LEVELS):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        s = fd.Solver([fd.Lattice(n, LENGTH, fd.F32) for _ in SECTORS], opts)
+        s.set_profiling(n == LEVELS[-1])
+        for i, (name, mask) in enumerate(SECTORS):
+            s.set_potential(pots[lvl], lat=i)
             if prev is None:
-                s.init_symmetric(seed, mask)
+                s.init_symmetric(seed, mask, lat=i)
             else:
-                s.upsample_from(prev)
-            steps, conv = s.evolve(2_000_000)
-            o = s.last_check()
-            st = s.stats()
-            tot["updates"] += n**3 * steps
-            tot["launches"] += st["launches"]
-            if n == LEVELS[-1]:
-                tot["fine_ms"] += st["stencil_ms"]
-                tot["fine_bytes"] += st["stencil_bytes"]
-                tot["fine_updates"] += st["stencil_site_updates"]
-                tot["fine_launches"] += st["stencil_launches"]
-                tot["fine_timed"] += st["stencil_timed_launches"]
-                tot["config"] = s.tuned_config() + s.tuned_kernel()
-            ev1.record()
-            ev1.synchronize()
-            tot["level_ms"][f"{name}_{n}"] = ev0.elapsed_time(ev1)
-            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": steps, "converged": conv,
-                                             "ms": ev0.elapsed_time(ev1)}
-            if prev is not None:
-                prev.close()
-            prev = s
-        prev.close()
+                s.upsample_from(prev, lat_src=i, lat=i)
+        _, conv = s.evolve(2_000_000)
+        st = s.stats()
+        tot["launches"] += st["launches"]
+        if n == LEVELS[-1]:
+            tot["fine_ms"] += st["stencil_ms"]
+            tot["fine_bytes"] += st["stencil_bytes"]
+            tot["fine_updates"] += st["stencil_site_updates"]
+            tot["fine_launches"] += st["stencil_launches"]
+            tot["fine_timed"] += st["stencil_timed_launches"]
+            tot["config"] = s.tuned_config() + s.tuned_kernel()
+        ev1.record()
+        ev1.synchronize()
+        tot["level_ms"][str(n)] = ev0.elapsed_time(ev1)
+        for i, (name, _) in enumerate(SECTORS):
+            o = s.last_check(lat=i)
+            tot["updates"] += n**3 * o["steps"]
+            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": o["steps"],
+                                             "converged": bool(o["converged"]), "level_ms": ev0.elapsed_time(ev1)}
+        if prev is not None:
+            prev.close()
+        prev = s
+    prev.close()
     return tot
 
 

@@ -103,7 +103,10 @@ typedef struct {
                              fastest (cached; identical results for every choice) */
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
   int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
-                             (FP32, n % 4 == 0); 1: the plain one-step kernel everywhere */
+                             (FP32, n % 4 == 0); 1: the plain one-step z-marching kernel
+                             everywhere; 2: the one-step kernel with four x sites per thread
+                             and no z-march where it applies (FP32, n % 4 == 0), else 1.
+                             Results are identical for all. */
   int32_t autotune;       /* 1 (default): time every (depth, tile width, span) candidate and the
                              one-step kernel on first use of a lattice size and keep the
                              fastest (results are identical for all) */
@@ -117,11 +120,13 @@ typedef struct {
                              that is not already complete expires at once; for testing the
                              FDTD_ERR_TIMEOUT path) */
   int32_t snapshots;      /* snapshot slots per lattice (Sec. III excited states); 0 = none */
-  int32_t graphs;         /* 1 (default): fdtd_evolve on one lattice runs its full pairs of
+  int32_t graphs;         /* 1 (default): fdtd_evolve runs each lattice's full pairs of
                              check_every-step segments as one CUDA graph whose while loop is
                              ended on the device by the convergence check (no host round trip
-                             per segment); the rest, and every run with profiling on, goes
-                             through the stream.  Results are identical either way. */
+                             per segment); the loops of a handle's lattices run at the same
+                             time, each on its own stream.  The rest, and the first two
+                             segments of a run with profiling on, go through the handle's
+                             stream.  Results are identical either way. */
   int32_t boundary;       /* 0 (default): psi = 0 beyond the lattice (Sec. III); 1: periodic
                              (neighbour index -1 is N-1 and N is 0 along every axis; the
                              paper notes that other boundary conditions are easily
@@ -255,8 +260,8 @@ FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
 /* The tile of that TMA stencil: tile_x x tile_y output sites of one z-plane
  * per block and step (tile_x 64 or 128, tile_y 16).  Both are 0 when the
- * one-step z-marching kernel is in use (FP64, BF16, periodic lattices,
- * stencil_kernel = 1, or the autotuner's choice) and for a batched handle. */
+ * one-step kernel is in use (FP64, BF16, periodic lattices, stencil_kernel
+ * 1 or 2, or the autotuner's choice) and for a batched handle. */
 FDTD_API int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y);
 
 /* Checkpoint files (Sec. VII.G: a run saves its wavefunction, and a later

@@ -1,6 +1,7 @@
 // Gradients through the unrolled evolution: fdtd_backward (sqrt(T)
-// checkpoints, segment recompute, the adjoint step: one fused pass for FP32
-// lattices, a pointwise and a stencil pass for FP64).
+// checkpoints, segment recompute, the adjoint step: a pointwise and a stencil
+// pass, four sites per thread for FP32 lattices with n % 4 == 0, one fused
+// z-marching pass for other FP32 lattices).
 #include "api_internal.cuh"
 
 using namespace fdtd;
@@ -26,6 +27,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
   const int K = L.bw_K;
   const int mask = h->o.reimpose_parity ? L.mask : 0;
   const size_t fb = L.n3 * L.es;
+  const bool f4 = L.d.precision == FDTD_F32 && L.d.n % 4 == 0;  // the direct four-site kernels
   auto field = [&](void* base, int64_t i) { return (void*)((char*)base + (size_t)i * fb); };
   LatState* scratch = &L.state[1];
   launch_state_reset(scratch, 0, h->st);
@@ -79,9 +81,14 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
         void* nxt = raw_of(t + 1);
         if constexpr (std::is_same_v<T_, double>)
           launch_step_f64((const double*)field(L.seg, t - t0), (double*)nxt, L.coefA, L.coefCB, L.p, nullptr, h->st);
-        else if constexpr (std::is_same_v<T_, float>)
-          launch_step_f32<float>((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr,
-                                 h->st);
+        else if constexpr (std::is_same_v<T_, float>) {
+          if (f4)
+            launch_direct_f32((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, false, nullptr,
+                              h->st);
+          else
+            launch_step_f32<float>((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr,
+                                   h->st);
+        }
         if constexpr (!std::is_same_v<T_, __nv_bfloat16>)
           if ((t + 1) % ce == 0 && t + 1 < t1)
             launch_scale_parity_from<T_>((const T_*)nxt, (T_*)field(L.seg, t + 1 - t0), L.d.n, mask,
@@ -93,8 +100,16 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
       with_type(L.d.precision, [&](auto* tag) {
         using T_ = std::remove_pointer_t<decltype(tag)>;
         if constexpr (std::is_same_v<T_, float>) {
-          launch_adjoint_step_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
-                                  (const float*)raw_of(t), (const float*)L.v, (float*)L.lam[1 - lc], L.gv, L.p, h->st);
+          if (f4) {
+            launch_adjoint_u_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
+                                 (const float*)raw_of(t), (const float*)L.v, (float*)L.bw_u, L.gv, L.p, h->st);
+            launch_direct_f32((const float*)L.bw_u, (float*)L.lam[1 - lc], (const float*)L.v, L.p, true, nullptr,
+                              h->st);
+          } else {
+            launch_adjoint_step_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
+                                    (const float*)raw_of(t), (const float*)L.v, (float*)L.lam[1 - lc], L.gv, L.p,
+                                    h->st);
+          }
         } else if constexpr (std::is_same_v<T_, double>) {
           launch_adjoint_pointwise<T_>((const T_*)L.lam[lc], (const T_*)field(L.seg, t - 1 - t0), (const T_*)raw_of(t),
                                        L.v, L.coefCB, (T_*)L.bw_u, L.gv, L.p, h->st);
@@ -106,7 +121,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
             launch_parity_adjoint_scale<T_>((T_*)L.lam[1 - lc], L.d.n, mask, L.scales + (t - 1) / ce, h->st);
         }
       });
-      h->stats.launches += ((t - 1) % ce == 0 ? 1 : 0) + (L.d.precision == FDTD_F64 ? 2 : 1);
+      h->stats.launches += ((t - 1) % ce == 0 ? 1 : 0) + (L.d.precision == FDTD_F64 || f4 ? 2 : 1);
       lc ^= 1;
     }
   }

@@ -71,8 +71,8 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "autotune must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
-  if (o.stencil_kernel < 0 || o.stencil_kernel > 1) {
-    err = "stencil_kernel must be 0 or 1";
+  if (o.stencil_kernel < 0 || o.stencil_kernel > 2) {
+    err = "stencil_kernel must be 0, 1 or 2";
     return FDTD_ERR_INVALID_ARG;
   }
   if (o.snapshots < 0 || o.snapshots > 1024) {
@@ -145,7 +145,9 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
       L.seg = cv.take((size_t)L.bw_K * L.n3 * L.es);
       L.lam[0] = cv.take(L.n3 * L.es);
       L.lam[1] = cv.take(L.n3 * L.es);
-      if (d[l].precision == FDTD_F64) L.bw_u = cv.take(L.n3 * L.es);  // FP32: one fused adjoint pass
+      // B lam of a split adjoint step (FP64, and FP32 with n % 4 == 0; other
+      // FP32 lattices take the fused z-marching step)
+      if (d[l].precision == FDTD_F64 || d[l].n % 4 == 0) L.bw_u = cv.take(L.n3 * L.es);
       L.bw_nraw = (L.bw_K - 1) / o.check_every + 2;  // check steps inside a segment + its last step
       L.bw_raw = cv.take((size_t)L.bw_nraw * L.n3 * L.es);
       L.gv = (double*)cv.take(L.n3 * 8);
@@ -426,11 +428,17 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
 int fdtd_destroy(fdtd_handle h) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->st);
-  for (auto& L : h->lats) release_graph(L);
+  for (auto& L : h->lats) {
+    release_graph(L);
+    if (L.run_st) {
+      cudaStreamSynchronize(L.run_st);
+      cudaStreamDestroy(L.run_st);
+    }
+    if (L.run_ev) cudaEventDestroy(L.run_ev);
+  }
   h->batch_graphs.release();
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
-  if (h->ev_out) cudaEventDestroy(h->ev_out);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
   return FDTD_OK;

@@ -10,19 +10,22 @@ namespace fdtd {
 namespace api {
 
 // ---- autotuning of the stencil configuration ---------------------------------
-// Fastest (depth, z-chunk) per (n, precision, device), shared by all handles.
+// Fastest (depth, tile width, span, one-step kernel, direct four-site
+// one-step kernel) per (n, precision, device), shared by all handles.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::tuple<int, int, int, bool>> g_tune;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
 
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
   L.plain = false;
+  L.direct = false;
   if (!tma) {
     L.depth = 1;
     L.tx = 128;
     L.zc = 0;
     L.plain = true;
+    L.direct = c->o.stencil_kernel == 2 && L.d.precision == FDTD_F32 && L.d.n % 4 == 0;
     return;
   }
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
@@ -38,7 +41,7 @@ void choose_config(fdtd_context* c, Lat& L) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      std::tie(L.depth, L.tx, L.zc, L.plain) = it->second;
+      std::tie(L.depth, L.tx, L.zc, L.plain, L.direct) = it->second;
       return;
     }
   }
@@ -51,7 +54,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   const int n = L.d.n;
   double best = 0.0;
   int bd = auto_depth(n, L.d.precision), bt = n > 64 ? 128 : 64, bz = tma_zchunk(n, bd, bt);
-  bool bp = false;
+  bool bp = false, bdir = false;
   auto time_it = [&](auto&& launch, int depth) {
     launch();
     const int reps = 3;
@@ -75,6 +78,21 @@ void choose_config(fdtd_context* c, Lat& L) {
     best = rate;
     bd = 1;
     bp = true;
+  }
+  // the direct four-site one-step kernel (n % 4 == 0 wherever the TMA kernel applies)
+  {
+    double rate = time_it(
+        [&]() {
+          launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, false,
+                            nullptr, c->st);
+        },
+        1);
+    if (rate > best) {
+      best = rate;
+      bd = 1;
+      bp = true;
+      bdir = true;
+    }
   }
   for (int ti = 0; ti < 2; ++ti) {
     const int tx = ti ? 128 : 64;
@@ -105,6 +123,7 @@ void choose_config(fdtd_context* c, Lat& L) {
           bt = tx;
           bz = zc;
           bp = false;
+          bdir = false;
         }
       }
     }
@@ -123,8 +142,9 @@ void choose_config(fdtd_context* c, Lat& L) {
   L.tx = bt;
   L.zc = bz;
   L.plain = bp;
+  L.direct = bdir;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[key] = std::make_tuple(bd, bt, bz, bp);
+  g_tune[key] = std::make_tuple(bd, bt, bz, bp, bdir);
 }
 
 // Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows),
@@ -143,6 +163,9 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
       if (tma)
         launch_step_tma(L.maps[L.tx == 128][k - 1][L.cur], L.maps[L.tx == 128][k - 1][2], (float*)L.psi[1 - L.cur],
                         L.p, k, L.tx, k == depth ? L.zc : 0, active, c->flags + 1, c->st);
+      else if (L.direct)
+        launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, false,
+                          active, c->st);
       else
         launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
                                c->st);
@@ -234,7 +257,7 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   choose_config(c, L);  // autotuning synchronises: never inside a capture
   const int mask = c->o.reimpose_parity ? L.mask : 0;
   const int b = L.cur;
-  const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain, ce};
+  const int64_t key[6] = {L.cur, mask, L.depth, L.zc, L.plain + 2 * L.direct, ce};
   if (L.graph_exec[b] && std::equal(key, key + 6, L.graph_key[b])) return true;
   release_graph(L, b);
   Range r("evolve graph build");
@@ -264,7 +287,7 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   const int64_t launches0 = c->stats.launches;
   const size_t pending0 = c->pending.size();
   // capture on the private stream (the handle's stream may be the legacy
-  // one, which cannot be captured); the graph is launched on the handle's
+  // one, which cannot be captured); the graph runs on the lattice's own
   if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
     c->cap_st = nullptr;
     cudaGraphDestroy(g);
@@ -290,11 +313,11 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   L.cur = cur0;
   cudaGraphExec_t exec = nullptr;
   if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
-  if (ok && !c->ev_in) {
-    ok = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !L.run_st) {
+    ok = cudaStreamCreateWithFlags(&L.run_st, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) L.run_st = nullptr;
   }
-  if (ok) ok = cudaGraphUpload(exec, c->cap_st) == cudaSuccess;
+  if (ok) ok = cudaGraphUpload(exec, L.run_st) == cudaSuccess;
   if (!ok) {
     cudaGraphDestroy(g);
     cudaGetLastError();
@@ -306,81 +329,109 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   return true;
 }
 
-int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
-  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
+// One lattice's evolve in stages, so that the graph loops of several
+// lattices of a handle can run at the same time: begin (state reset and,
+// with profiling on, the timed sample), the graph loop over full pairs of
+// segments, and the stream-driven tail (what the graph did not cover).
+struct EvolveRun {
+  int64_t t = 0, t_end = 0, pairs = 0;
+  int check_id = 0;
+  bool done = false, graph = false;
+};
+
+int evolve_begin(fdtd_context* c, Lat& L, int64_t max_steps, EvolveRun& r) {
   launch_state_reset(&L.state[0], 0, c->st);
   c->stats.launches += 1;
   const int64_t ce = c->o.check_every;
-  int64_t t = 0;
-  int check_id = 0;
-  int groups = 2;
-  bool done = false;
   if (c->o.graphs && c->profiling) {
     // the timed sample: two segments through the stream, every stencil
     // launch between CUDA events (a graph loop body cannot hold events)
-    for (int i = 0; i < 2 && t + ce <= max_steps; ++i) {
-      enqueue_check(c, L, check_id++, t);
-      run_steps(c, L, ce, &L.state[0].active, t);
-      t += ce;
+    for (int i = 0; i < 2 && r.t + ce <= max_steps; ++i) {
+      enqueue_check(c, L, r.check_id++, r.t);
+      run_steps(c, L, ce, &L.state[0].active, r.t);
+      r.t += ce;
     }
     int rc = cuda_check(c, "evolve launch");
     if (rc) return rc;
     if ((rc = read_state(c, L))) return rc;
-    if (!L.host_state.active) done = true;
+    if (!L.host_state.active) r.done = true;
   }
   // full pairs of segments in one graph launch, the convergence check
   // ending the loop on the device
-  const int64_t pairs = (!done && c->o.graphs) ? std::min<int64_t>((max_steps - t) / (2 * ce), 1 << 28) : 0;
-  if (pairs > 0 && ensure_graph(c, L, ce)) {
-    const int64_t t_end = t + 2 * pairs * ce;
-    launch_state_reset(&L.state[0], 2, c->st, check_id + (int)(2 * pairs));
+  r.pairs = (!r.done && c->o.graphs) ? std::min<int64_t>((max_steps - r.t) / (2 * ce), 1 << 28) : 0;
+  r.graph = r.pairs > 0 && ensure_graph(c, L, ce);
+  if (r.graph) {
+    r.t_end = r.t + 2 * r.pairs * ce;
+    launch_state_reset(&L.state[0], 2, c->st, r.check_id + (int)(2 * r.pairs));
     c->stats.launches += 1;
-    // launched on the private stream, ordered after and before the handle's
-    // stream by events (a graph launched into the legacy stream paid about
-    // half a millisecond per launch)
-    cudaEventRecord(c->ev_in, c->st);
-    cudaStreamWaitEvent(c->cap_st, c->ev_in, 0);
-    cudaGraphLaunch(L.graph_exec[L.cur], c->cap_st);
-    cudaEventRecord(c->ev_out, c->cap_st);
-    cudaStreamWaitEvent(c->st, c->ev_out, 0);
-    c->stats.graph_launches += 1;
-    int rc = cuda_check(c, "evolve graph launch");
-    if (rc) return rc;
-    if ((rc = read_state(c, L))) return rc;
-    const LatState& hs = L.host_state;
-    c->stats.launches += (int64_t)((hs.checks - check_id + 1) / 2) * L.graph_kernels;
-    const int64_t advanced = std::max<int64_t>(0, (hs.active ? t_end : hs.step) - t);  // steps taken while active
-    int64_t seg_l;
-    double seg_b;
-    segment_work(c, L, ce, &seg_l, &seg_b);
-    c->stats.stencil_launches += advanced / ce * seg_l;
-    c->stats.stencil_site_updates += advanced * (int64_t)L.n3;
-    c->stats.stencil_bytes += (double)(advanced / ce) * seg_b;
-    if (!hs.active) {
-      done = true;
-    } else {
-      t = t_end;
-      check_id = hs.checks;
-    }
   }
+  return FDTD_OK;
+}
+
+// Launch the graph loop on the lattice's own stream, ordered after the
+// handle's stream up to `ready` and before whatever the handle's stream
+// takes next.  (A graph launched into the legacy stream paid about half a
+// millisecond per launch, hence private non-blocking streams.)
+int evolve_graph_launch(fdtd_context* c, Lat& L, cudaEvent_t ready) {
+  if (!L.run_st && cudaStreamCreateWithFlags(&L.run_st, cudaStreamNonBlocking) != cudaSuccess) {
+    L.run_st = nullptr;
+    return cuda_check(c, "evolve stream");
+  }
+  if (!L.run_ev && cudaEventCreateWithFlags(&L.run_ev, cudaEventDisableTiming) != cudaSuccess) {
+    L.run_ev = nullptr;
+    return cuda_check(c, "evolve event");
+  }
+  cudaStreamWaitEvent(L.run_st, ready, 0);
+  cudaGraphLaunch(L.graph_exec[L.cur], L.run_st);
+  cudaEventRecord(L.run_ev, L.run_st);
+  cudaStreamWaitEvent(c->st, L.run_ev, 0);
+  c->stats.graph_launches += 1;
+  return cuda_check(c, "evolve graph launch");
+}
+
+int evolve_graph_finish(fdtd_context* c, Lat& L, EvolveRun& r) {
+  int rc = read_state(c, L);
+  if (rc) return rc;
+  const int64_t ce = c->o.check_every;
+  const LatState& hs = L.host_state;
+  c->stats.launches += (int64_t)((hs.checks - r.check_id + 1) / 2) * L.graph_kernels;
+  const int64_t advanced = std::max<int64_t>(0, (hs.active ? r.t_end : hs.step) - r.t);  // steps taken while active
+  int64_t seg_l;
+  double seg_b;
+  segment_work(c, L, ce, &seg_l, &seg_b);
+  c->stats.stencil_launches += advanced / ce * seg_l;
+  c->stats.stencil_site_updates += advanced * (int64_t)L.n3;
+  c->stats.stencil_bytes += (double)(advanced / ce) * seg_b;
+  if (!hs.active) {
+    r.done = true;
+  } else {
+    r.t = r.t_end;
+    r.check_id = hs.checks;
+  }
+  return FDTD_OK;
+}
+
+int evolve_tail(fdtd_context* c, Lat& L, int64_t max_steps, EvolveRun& r) {
+  const int64_t ce = c->o.check_every;
+  int groups = 2;
   int prev_checks = 0;
   double prev_delta = -1.0;
-  while (!done) {
-    for (int g = 0; g < groups && !done; ++g) {
-      enqueue_check(c, L, check_id++, t);
-      if (t >= max_steps) {
-        done = true;
+  while (!r.done) {
+    for (int g = 0; g < groups && !r.done; ++g) {
+      enqueue_check(c, L, r.check_id++, r.t);
+      if (r.t >= max_steps) {
+        r.done = true;
         break;
       }
-      int64_t nst = std::min<int64_t>(ce, max_steps - t);
-      run_steps(c, L, nst, &L.state[0].active, t);
-      t += nst;
+      int64_t nst = std::min<int64_t>(ce, max_steps - r.t);
+      run_steps(c, L, nst, &L.state[0].active, r.t);
+      r.t += nst;
     }
     int rc = cuda_check(c, "evolve launch");
     if (rc) return rc;
     rc = read_state(c, L);
     if (rc) return rc;
-    if (!L.host_state.active) done = true;
+    if (!L.host_state.active) r.done = true;
     // segments to enqueue before the next look: predicted from the decay of
     // |dE_b| per check, so that little work is queued past convergence
     const LatState& hs = L.host_state;
@@ -401,6 +452,35 @@ int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps) {
     return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
   L.cur = L.host_state.cur;
   L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
+  return FDTD_OK;
+}
+
+// Every lattice of a (non-batched) handle.  The graph loops of all lattices
+// are launched together, each on its own stream, so independent lattices
+// share the GPU (the small ones leave most of it idle on their own); every
+// lattice computes the same bits as when evolved alone.
+int evolve_lattices(fdtd_context* c, int64_t max_steps) {
+  cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
+  std::vector<EvolveRun> runs(c->lats.size());
+  int rc = FDTD_OK;
+  // every capture and autotuning pass (which times launches) before any loop runs
+  for (size_t i = 0; i < c->lats.size(); ++i)
+    if ((rc = evolve_begin(c, c->lats[i], max_steps, runs[i]))) return rc;
+  bool any = false;
+  for (const auto& r : runs) any = any || r.graph;
+  if (any) {
+    if (!c->ev_in && cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess) {
+      c->ev_in = nullptr;
+      return cuda_check(c, "evolve event");
+    }
+    cudaEventRecord(c->ev_in, c->st);
+    for (size_t i = 0; i < c->lats.size(); ++i)
+      if (runs[i].graph && (rc = evolve_graph_launch(c, c->lats[i], c->ev_in))) return rc;
+    for (size_t i = 0; i < c->lats.size(); ++i)
+      if (runs[i].graph && (rc = evolve_graph_finish(c, c->lats[i], runs[i]))) return rc;
+  }
+  for (size_t i = 0; i < c->lats.size(); ++i)
+    if ((rc = evolve_tail(c, c->lats[i], max_steps, runs[i]))) return rc;
   return FDTD_OK;
 }
 
@@ -542,10 +622,7 @@ int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
   if (h->o.batched) {
     rc = evolve_batched(h, max_steps);
   } else {
-    for (auto& L : h->lats) {
-      rc = evolve_one(h, L, max_steps);
-      if (rc) return rc;
-    }
+    rc = evolve_lattices(h, max_steps);
   }
   if (rc) return rc;
   int64_t mx = 0;

@@ -83,9 +83,10 @@ struct Lat {
   CUtensorMap maps[2][3][3];
   CUtensorMap sums_maps[3];
   // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet);
-  // plain = the one-step z-marching kernel (bit-identical) was timed fastest
+  // plain = a one-step kernel (bit-identical) was timed fastest: the
+  // z-marching one, or the direct four-site one when direct is set
   int depth = 0, tx = 128, zc = 0;
-  bool plain = false;
+  bool plain = false, direct = false;
   // evolve graphs: a while loop over pairs of (check, check_every steps),
   // one per start buffer (an evolve ends on either), each built for a mask,
   // stencil configuration and cadence
@@ -93,6 +94,10 @@ struct Lat {
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_key[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
   int64_t graph_kernels = 0;  // kernels per loop iteration
+  // the lattice's own stream for its graph loop (lattices of a handle run
+  // concurrently) and the event that orders the handle's stream after it
+  cudaStream_t run_st = nullptr;
+  cudaEvent_t run_ev = nullptr;
 };
 
 void release_graph(Lat& L, int b);
@@ -120,8 +125,8 @@ struct fdtd_context {
   int check_seq = 0;
   fdtd::BatchedGraphs batch_graphs;     // graphs of the batched persistent launch
   int batch_depth = 0, batch_zc = 0;  // configuration of the last batched evolve
-  cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured and launched on
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order cap_st after / before the handle's stream
+  cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured on
+  cudaEvent_t ev_in = nullptr;    // orders the lattices' graph loops after the handle's stream
   // stencil launches not yet credited to the stats: a launch enqueued past
   // the check at which its lattice converged runs as a no-op and is dropped
   struct Pending {
@@ -169,7 +174,7 @@ int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* act
 void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int mask, const LatState* s, int id,
                       int out_idx, LatState* sw);
 int read_state(fdtd_context* c, Lat& L);
-int evolve_one(fdtd_context* c, Lat& L, int64_t max_steps);
+int evolve_lattices(fdtd_context* c, int64_t max_steps);
 int evolve_batched(fdtd_context* c, int64_t max_steps);
 
 // fields and records (api_core.cu)

@@ -332,7 +332,7 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
     rng = np.random.default_rng(n)
     v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
     outs = {}
-    variants = [("plain", dict(stencil_kernel=1)), ("k1", dict(temporal_depth=1)),
+    variants = [("plain", dict(stencil_kernel=1)), ("direct", dict(stencil_kernel=2)), ("k1", dict(temporal_depth=1)),
                 ("k2", dict(temporal_depth=2)), ("k3", dict(temporal_depth=3)),
                 ("k1z2", dict(temporal_depth=1, zchunk=2)), ("k1z3", dict(temporal_depth=1, zchunk=3)),
                 ("k2z9", dict(temporal_depth=2, zchunk=9)), ("k3z12", dict(temporal_depth=3, zchunk=12)),
@@ -345,7 +345,7 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         s.init_symmetric(31, wl.ODD_Z)
         s.evolve(100)
         outs[name] = s.get_psi(dtype=np.float32)
-        if name == "plain":
+        if name in ("plain", "direct"):
             assert s.tuned_kernel() == (0, 0)
         elif name.startswith("k"):
             assert s.tuned_kernel() == (128 if n > 64 else 64, 16), name
@@ -392,6 +392,50 @@ def test_evolve_graph_matches_stream(fd, prec, n, kw):
             np.testing.assert_array_equal(a, b)
         else:
             assert a == b
+
+
+@pytest.mark.parametrize("profiling", [False, True])
+def test_lattices_of_a_handle_evolve_concurrently_as_alone(fd, profiling):
+    """The graph loops of a handle's lattices run at the same time on their
+    own streams; every lattice ends bit-identical to the same lattice
+    evolved alone: different sizes, masks and precisions, one that
+    converges early, one stopped by max_steps, and a second evolve."""
+    specs = [(64, fd.F32, wl.ODD_X, 11), (36, fd.F32, 0, 12), (24, fd.F64, wl.SYMMETRIC_ALL, 13),
+             (48, fd.F32, wl.ODD_Z | wl.ODD_Y, 14)]
+    opts = dict(check_every=50, tol=1e-6, tol_relative=1)
+
+    def potential(i, n):
+        # the 36^3 lattice is a free particle in the box: a small gap, slow to converge
+        L = 0.3 * n
+        return np.zeros((n, n, n)) if n == 36 else wl.harmonic(n, L) + 0.1 * np.cos(wl.radius2(n, L)) + 0.05 * i
+
+    together = fd.Solver([fd.Lattice(n, 0.3 * n, p) for n, p, _, _ in specs], fd.default_options(**opts))
+    together.set_profiling(profiling)
+    psi0 = []
+    for i, (n, _, mask, seed) in enumerate(specs):
+        together.set_potential(potential(i, n), lat=i)
+        together.init_symmetric(seed, mask, lat=i)  # the start hashes the lattice index too
+        psi0.append(together.get_psi(lat=i))
+    first = together.evolve(1900)
+    res_t = [(together.last_check(lat=i), together.get_psi(lat=i)) for i in range(len(specs))]
+    second = together.evolve(400)
+    res_t2 = [(together.last_check(lat=i), together.get_psi(lat=i)) for i in range(len(specs))]
+    assert together.stats()["graph_launches"] >= len(specs)
+    together.close()
+    for i, sp in enumerate(specs):
+        alone = fd.Solver(fd.Lattice(sp[0], 0.3 * sp[0], sp[1]), fd.default_options(**opts))
+        alone.set_profiling(profiling)
+        alone.set_potential(potential(i, sp[0]))
+        alone.set_psi(psi0[i], mask=sp[2])
+        alone.evolve(1900)
+        assert alone.last_check() == res_t[i][0], i
+        np.testing.assert_array_equal(alone.get_psi(), res_t[i][1], err_msg=str(i))
+        alone.evolve(400)
+        assert alone.last_check() == res_t2[i][0], i
+        np.testing.assert_array_equal(alone.get_psi(), res_t2[i][1], err_msg=str(i))
+        alone.close()
+    assert first[0] == max(r[0]["steps"] for r in res_t)
+    assert any(r[0]["converged"] for r in res_t)
 
 
 # ------------------------------------------------------------------ adjoint

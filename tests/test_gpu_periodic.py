@@ -120,9 +120,30 @@ def test_periodic_upsample_matches_oracle(fd, per):
     assert rel_max(fine.get_psi(), up) <= 1e-14
 
 
+@pytest.mark.parametrize("n", [4, 12, 24])
+def test_periodic_direct_kernel_bit_identical(fd, n):
+    """The four-site one-step kernel with wrapped neighbours (stencil_kernel
+    = 2) reproduces the periodic z-marching kernel bit for bit (n = 4: one
+    float4 per row, both x-neighbours wrap)."""
+    L = n / 3.0
+    v = crystal(n, L).astype(np.float32)
+    out = []
+    for k in (1, 2):
+        s = solver(fd, n, L, fd.F32, check_every=25, stencil_kernel=k)
+        s.set_potential(v)
+        s.init_symmetric(9, 0)
+        s.evolve(60)
+        out.append(s.get_psi(dtype=np.float32))
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("n", [10, 12])
 @pytest.mark.parametrize("prec,tol", [("F64", 1e-10), ("F32", 1e-4)])
-def test_periodic_backward_matches_oracle(fd, per, prec, tol):
-    n, L, T, ce = 10, 5.0, 40, 15
+def test_periodic_backward_matches_oracle(fd, per, prec, tol, n):
+    """n = 10: the fused z-marching FP32 adjoint step; n = 12: the split
+    four-site one."""
+    L, T, ce = n / 2.0, 40, 15
     a = L / n
     v = crystal(n, L)
     psi0 = per.init_random(n, 6)
