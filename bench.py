@@ -42,7 +42,7 @@ SEED = 904939
 # dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
 # from an ncu capture of the current kernel, by (depth, span, tile width,
 # tile height); a tuned configuration without a capture reports traffic null
-TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048}
+TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048, (3, -1, 128, 16): 236_390_000}
 
 
 def dist_env():
@@ -100,11 +100,13 @@ def run_step(fd, pots, seed, opts):
         ev1.record()
         ev1.synchronize()
         tot["level_ms"][str(n)] = ev0.elapsed_time(ev1)
+        tuned = list(s.tuned_config()) + list(s.tuned_kernel())
         for i, (name, _) in enumerate(SECTORS):
             o = s.last_check(lat=i)
             tot["updates"] += n**3 * o["steps"]
             tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": o["steps"],
-                                             "converged": bool(o["converged"]), "level_ms": ev0.elapsed_time(ev1)}
+                                             "converged": bool(o["converged"]), "level_ms": ev0.elapsed_time(ev1),
+                                             "stencil": tuned}
         if prev is not None:
             prev.close()
         prev = s
@@ -557,7 +559,8 @@ def main():
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc, tx, ty)),
-                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, span {zc}, tile {tx}x{ty})" if zc
+                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, "
+                                f"{'balanced one-wave partition' if zc < 0 else f'span {zc}'}, tile {tx}x{ty})" if zc
                                 else "k_step_f32 (256^3 level, one-step z-marching)"),
                      "launches": fine_launches, "timed_launches": fine_timed, "ms_per_launch": ms_launch,
                      "bytes_per_launch": bytes_launch, "peak_kind": peak_note,

@@ -31,7 +31,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
     L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
     L.tx = L.d.n > 64 ? 128 : 64;
-    L.zc = c->o.zchunk > 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
+    L.zc = c->o.zchunk != 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
     return;
   }
   int dev = 0;
@@ -108,6 +108,7 @@ void choose_config(fdtd_context* c, Lat& L) {
       }
       const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx);
       for (int m = 1; m <= 3; ++m) spans.push_back((int)std::max(1LL, (total + m * slots - 1) / (m * slots)));
+      spans.push_back(-1);  // the balanced one-wave partition
       std::sort(spans.begin(), spans.end());
       spans.erase(std::unique(spans.begin(), spans.end()), spans.end());
       for (int zc : spans) {

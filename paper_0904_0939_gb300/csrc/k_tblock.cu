@@ -21,11 +21,27 @@ namespace tb {
 // one item per column it touches.  A span that divides n is a plain z-chunk
 // grid; a span of ceil(ntiles * n / resident blocks) gives every SM the
 // same work in one wave whatever the lattice size.
+//
+// span <= 0 selects the balanced partition: every item costs its planes plus
+// wcost = 2(K - 1) warm-up and drain steps, so a block whose equal span runs
+// into the next column (two items) is the slowest of the wave.  Instead each
+// tile column counts n + wcost cost units (the item start first), the grid
+// splits the cost line into equal parts, and a cost coordinate u maps to the
+// tile plane  c n + clamp(u - c (n + wcost) - wcost, 0, n),  c = u / (n + wcost):
+// monotone, from 0 to ntiles * n, so the blocks' ranges cover every tile
+// plane once.
+__device__ __forceinline__ long long balanced_plane(long long u, int n, int wcost) {
+  const long long unit = n + wcost, c = u / unit;
+  long long o = u - c * unit - wcost;
+  o = o < 0 ? 0 : (o > n ? n : o);
+  return c * n + o;
+}
 template <int K, int TXT>
 __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                     const __grid_constant__ CUtensorMap map_v,
                                                                     float* __restrict__ out, int n, int ntx,
-                                                                    long long total, int span, float half_dtau,
+                                                                    long long total, int span, int wcost,
+                                                                    float half_dtau,
                                                                     float one_m6c, float cc,
                                                                     const int32_t* __restrict__ active,
                                                                     int32_t* __restrict__ err) {
@@ -35,8 +51,15 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   if (*(volatile const int32_t*)err != 0) return;  // an earlier wait expired: do nothing
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = aligned_smem(smem_raw);
-  long long g = (long long)blockIdx.x * span;
-  const long long gend = min(g + span, total);
+  long long g, gend;
+  if (span > 0) {
+    g = (long long)blockIdx.x * span;
+    gend = min(g + span, total);
+  } else {
+    const long long ctot = (total / n) * (n + wcost);
+    g = balanced_plane(ctot * blockIdx.x / gridDim.x, n, wcost);
+    gend = balanced_plane(ctot * (blockIdx.x + 1) / gridDim.x, n, wcost);
+  }
   while (g < gend) {
     const int t = (int)(g / n), z0 = (int)(g - (long long)t * n);
     const int z1 = (int)min((long long)n, z0 + (gend - g));
@@ -87,14 +110,20 @@ long long tile_planes(int n) {
 }
 
 template <int K, int TXT>
+int resident_blocks();
+
+// span > 0: equal spans; span <= 0: the balanced partition over one wave
+template <int K, int TXT>
 void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int span,
               const int32_t* active, int32_t* err, cudaStream_t st) {
   using G = Geo<K, TXT>;
   set_smem(k_step_tma<K, TXT>, G::SMEM);
   const long long total = tile_planes<K, TXT>(p.n);
-  const unsigned blocks = (unsigned)((total + span - 1) / span);
+  const unsigned blocks = span > 0 ? (unsigned)((total + span - 1) / span)
+                                   : (unsigned)std::min<long long>(resident_blocks<K, TXT>(), total);
   launch_pdl(k_step_tma<K, TXT>, dim3(blocks), dim3(G::THREADS), G::SMEM, st, mpsi, mv, out, p.n,
-             (p.n + TXT - 1) / TXT, total, span, p.half_dtau_f, p.one_m6c_f, p.c_f, active, err);
+             (p.n + TXT - 1) / TXT, total, span > 0 ? span : 0, 2 * (K - 1), p.half_dtau_f, p.one_m6c_f, p.c_f,
+             active, err);
 }
 
 // Blocks of k_step_tma<K, TXT> resident on the whole device at once
@@ -145,7 +174,7 @@ int tma_zchunk(int n, int depth, int tx) {
 
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                      int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st) {
-  if (zc <= 0) zc = tma_zchunk(p.n, depth, tx);
+  if (zc == 0) zc = tma_zchunk(p.n, depth, tx);  // zc < 0: the balanced partition
   if (tx == 64) {
     if (depth == 1)
       tb::launch_k<1, 64>(map_psi_in, map_v, out, p, zc, active, err, st);

@@ -77,7 +77,10 @@ void launch_step_f32(const T* in, T* out, const float* v, const Params& p, const
 // bounded wait expired.  A stencil launch gives each block `zc` consecutive
 // tile planes of the column-major sequence of tma_tile_planes(n, tx) (a
 // block's span may run on into the next tile column); tma_zchunk is the
-// span that fills the device's resident blocks in one wave.
+// span that fills the device's resident blocks in one wave, and zc = 0
+// takes it; zc < 0 is the balanced partition over one wave (each item's
+// warm-up and drain steps counted, so that a block spanning two columns
+// gets fewer planes).
 bool tma_supported(int n, int precision);
 int blocked_max_depth();
 int auto_depth(int n, int precision);

@@ -338,6 +338,8 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
                 ("k2z9", dict(temporal_depth=2, zchunk=9)), ("k3z12", dict(temporal_depth=3, zchunk=12)),
                 ("k2z1", dict(temporal_depth=2, zchunk=1)), ("k3z1", dict(temporal_depth=3, zchunk=1)),
                 ("k3z200", dict(temporal_depth=3, zchunk=200)),
+                ("k1bal", dict(temporal_depth=1, zchunk=-1)), ("k2bal", dict(temporal_depth=2, zchunk=-1)),
+                ("k3bal", dict(temporal_depth=3, zchunk=-1)),
                 ("auto", dict(autotune=1))]
     for name, kw in variants:
         s = solver(fd, n, L, fd.F32, check_every=50, **kw)
