@@ -221,6 +221,9 @@ FDTD_API int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_
  * sum psi^2 a^3 = 1 (Sec. III), re-imposition of the symmetry mask
  * (Sec. IV), and the convergence test on the binding energy (Sec. V).
  * A lattice stops at the first check whose |dE_b| meets the tolerance.
+ * The lattices of a non-batched handle are independent: with
+ * options.graphs their evolve loops run at the same time, each on its own
+ * stream, and every lattice ends bit-identical to an evolve of it alone.
  * *steps_done (may be NULL) receives the largest step count over lattices.
  * Returns FDTD_OK, FDTD_NOT_CONVERGED (tol > 0 and some lattice reached
  * max_steps), FDTD_ERR_NONFINITE, FDTD_ERR_TIMEOUT or another error. */
