@@ -12,8 +12,8 @@ steps, sums, renormalisation + symmetry re-imposition, transfer.
 
 metric: site updates per second (interior sites x update steps, all levels,
 both sectors), whole job; "value" times the device work with V already
-resident in HBM, "e2e" the same call with host-resident V (host->device
-copies inside the timed region) and the observables read back.
+resident in HBM, "e2e" the same call with V in pinned host memory
+(host->device copies inside the timed region) and the observables read back.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (update steps with checks on the 256^3 lattice).
@@ -61,7 +61,8 @@ def potentials(resident: bool, device):
     out = []
     for n in LEVELS:
         v = wl.coulomb_soft(n, LENGTH).astype(np.float32)
-        out.append(torch.from_numpy(v).to(device) if resident else v)
+        # host-resident: pinned (page-locked) memory, so each step's copies are plain DMA
+        out.append(torch.from_numpy(v).to(device) if resident else torch.from_numpy(v).pin_memory())
     return out
 
 
