@@ -16,8 +16,11 @@
  *   dtype; the library cannot check the length of a raw buffer.
  * - Memory: every pointer argument is paired with a mem_kind (FDTD_MEM_HOST
  *   or FDTD_MEM_DEVICE).  Inputs are borrowed for the duration of the call
- *   only: the library copies them into its own layout.  Outputs are written
- *   into caller-owned buffers.
+ *   only: the library copies them into its own layout.  A host input has
+ *   been read completely when the call returns (pinned or pageable); a
+ *   device input is read in stream order on the handle's stream, so the
+ *   caller may overwrite it with later work on that stream (or after
+ *   synchronising it).  Outputs are written into caller-owned buffers.
  * - Ownership: the caller allocates ONE device workspace of at least
  *   fdtd_workspace_size() bytes (256-byte aligned) and keeps it alive until
  *   fdtd_destroy(); the library never allocates device memory itself.  The

@@ -269,6 +269,9 @@ int import_field(fdtd_context* c, const void* src, int dt, int mem, void* dst, i
       cudaMemcpyAsync(c->staging, (const char*)src + off * isz, cnt * isz, cudaMemcpyHostToDevice, c->st);
       convert(c->staging, cnt, off);
     }
+    // a host input is borrowed for the call only: from pinned memory the
+    // copies above are asynchronous, so wait until they have read it
+    cudaStreamSynchronize(c->st);
   }
   return cuda_check(c, "import");
 }

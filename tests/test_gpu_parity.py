@@ -274,6 +274,33 @@ def test_input_guards(fd):
     assert e.value.code == fd.ERR_INVALID_ARG
 
 
+def test_pinned_host_input_is_read_before_the_call_returns(fd):
+    """A host input is borrowed for the call only, also from pinned memory
+    (where the copies are asynchronous): overwriting the buffer right after
+    fdtd_set_potential / fdtd_set_psi returns changes nothing."""
+    import torch
+
+    n, L = 64, 19.2
+    v = (wl.harmonic(n, L) + 0.1 * np.cos(wl.radius2(n, L))).astype(np.float32)
+    psi = np.exp(-0.5 * wl.radius2(n, L)).astype(np.float32)
+    out = []
+    for pinned in (False, True):
+        s = solver(fd, n, L, fd.F32, check_every=20)
+        if pinned:
+            vp, pp = torch.from_numpy(v.copy()).pin_memory(), torch.from_numpy(psi.copy()).pin_memory()
+            s.set_potential(vp)
+            vp.fill_(1.0e6)
+            s.set_psi(pp)
+            pp.fill_(-3.0)
+        else:
+            s.set_potential(torch.from_numpy(v).cuda())
+            s.set_psi(torch.from_numpy(psi).cuda())
+        s.evolve(60)
+        out.append(s.get_psi(dtype=np.float32))
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 def test_zero_field_reports_nonfinite(fd):
     s = solver(fd, 8, 4.0, fd.F64)
     s.set_potential(np.zeros((8, 8, 8)))
