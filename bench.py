@@ -367,6 +367,14 @@ def cpu_baseline(target_s: float = 12.0):
             "sample": f"{steps} FP64 update steps with checks on the 256^3 Coulomb lattice ({dt:.1f} s)"}
 
 
+def workload_config(ws: int) -> dict:
+    """The workload both arms report (the reference arm times a bounded
+    sample of it, described in its cpu_baseline)."""
+    return {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px", "levels": list(LEVELS), "length": LENGTH,
+            "tol_rel": TOL, "check_every": 100, "l2": "flushed (512 MiB write) between timed steps",
+            "parallelism": f"replicas{ws}"}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -383,7 +391,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px (oracle sample: 256^3 steps)"},
+            "config": workload_config(ws),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -554,10 +562,9 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px", "levels": list(LEVELS),
-                   "evolve": "cuda graph (device-side loop)" if args.graphs else "stream",
-                   "length": LENGTH, "tol_rel": TOL, "check_every": 100, "precision": "fp32 stencil, fp64 sums",
-                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas{ws}"},
+        "config": workload_config(ws),
+        "path": {"evolve": "cuda graph per lattice (device-side loop), the two sectors concurrently" if args.graphs
+                 else "stream", "precision": "fp32 stencil, fp64 sums"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc, tx, ty)),
                      "kernel": (f"k_step_tma (256^3 level, depth {depth}, "
