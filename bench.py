@@ -411,6 +411,38 @@ def reduce_over_ranks(times, counts, device, world_size):
     return t.tolist(), u.tolist()
 
 
+def backward_case(args):
+    """The differentiable workload (V_theta, L = 10, FP32, checks every 100
+    steps, sqrt(T) checkpoints) on an n^3 lattice through T = --iters
+    unrolled steps: three fdtd_backward calls (the first includes the
+    autotuner's first-use timings), wall time of each with a synchronise on
+    both sides.  Small enough to run under ncu."""
+    import numpy as np
+    import torch
+
+    import paper_0904_0939_gb300 as fd
+    import workloads as wl
+
+    n, L, T = args.n, 10.0, args.iters
+    dev = torch.device("cuda:0")
+    g, th = wl.config_theta(n, L)
+    v = torch.from_numpy(wl.v_theta(n, L, th, g).astype(np.float32)).to(dev)
+    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=100, tol=0.0, backward_steps=T))
+    s.set_potential(v)
+    psi0 = torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev)
+    out = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    ms = []
+    for _ in range(3):
+        s.set_psi(psi0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.backward(T, 1.0, 0.0, out=out)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    s.close()
+    print(json.dumps({"case": "backward", "n": n, "T": T, "ms_per_call": ms, "us_per_step": ms[-1] * 1e3 / T}))
+
+
 def stencil_case(args):
     """Fixed number of update steps on one lattice (512^3, L = 16 by default,
     the size of the anisotropic-oscillator workload; the kernel's time does
@@ -456,7 +488,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="0: every evolve through the stream (for launch lists under ncu)")
-    ap.add_argument("--case", default="solve", choices=["solve", "stencil"])
+    ap.add_argument("--case", default="solve", choices=["solve", "stencil", "backward"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--depth", type=int, default=0)
@@ -467,6 +499,8 @@ def main():
         return reference_arm(args)
     if args.case == "stencil":
         return stencil_case(args)
+    if args.case == "backward":
+        return backward_case(args)
 
     import torch
     import torch.distributed as dist
