@@ -1,7 +1,7 @@
 // Gradients through the unrolled evolution: fdtd_backward (sqrt(T)
-// checkpoints, segment recompute, the adjoint step: a pointwise and a stencil
-// pass, four sites per thread for FP32 lattices with n % 4 == 0, one fused
-// z-marching pass for other FP32 lattices).
+// checkpoints, segment recompute, the adjoint step: one pass for FP32
+// lattices -- four x sites per thread when n % 4 == 0, else z-marching --
+// and a pointwise and a stencil pass for FP64).
 #include "api_internal.cuh"
 
 using namespace fdtd;
@@ -83,8 +83,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
           launch_step_f64((const double*)field(L.seg, t - t0), (double*)nxt, L.coefA, L.coefCB, L.p, nullptr, h->st);
         else if constexpr (std::is_same_v<T_, float>) {
           if (f4)
-            launch_direct_f32((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, false, nullptr,
-                              h->st);
+            launch_direct_f32((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr, h->st);
           else
             launch_step_f32<float>((const float*)field(L.seg, t - t0), (float*)nxt, (const float*)L.v, L.p, nullptr,
                                    h->st);
@@ -101,10 +100,9 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
         using T_ = std::remove_pointer_t<decltype(tag)>;
         if constexpr (std::is_same_v<T_, float>) {
           if (f4) {
-            launch_adjoint_u_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
-                                 (const float*)raw_of(t), (const float*)L.v, (float*)L.bw_u, L.gv, L.p, h->st);
-            launch_direct_f32((const float*)L.bw_u, (float*)L.lam[1 - lc], (const float*)L.v, L.p, true, nullptr,
-                              h->st);
+            launch_adjoint_direct_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
+                                      (const float*)raw_of(t), (const float*)L.v, (float*)L.lam[1 - lc], L.gv, L.p,
+                                      h->st);
           } else {
             launch_adjoint_step_f32((const float*)L.lam[lc], (const float*)field(L.seg, t - 1 - t0),
                                     (const float*)raw_of(t), (const float*)L.v, (float*)L.lam[1 - lc], L.gv, L.p,
@@ -121,7 +119,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
             launch_parity_adjoint_scale<T_>((T_*)L.lam[1 - lc], L.d.n, mask, L.scales + (t - 1) / ce, h->st);
         }
       });
-      h->stats.launches += ((t - 1) % ce == 0 ? 1 : 0) + (L.d.precision == FDTD_F64 || f4 ? 2 : 1);
+      h->stats.launches += ((t - 1) % ce == 0 ? 1 : 0) + (L.d.precision == FDTD_F64 ? 2 : 1);
       lc ^= 1;
     }
   }

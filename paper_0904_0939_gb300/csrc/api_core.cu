@@ -145,9 +145,7 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
       L.seg = cv.take((size_t)L.bw_K * L.n3 * L.es);
       L.lam[0] = cv.take(L.n3 * L.es);
       L.lam[1] = cv.take(L.n3 * L.es);
-      // B lam of a split adjoint step (FP64, and FP32 with n % 4 == 0; other
-      // FP32 lattices take the fused z-marching step)
-      if (d[l].precision == FDTD_F64 || d[l].n % 4 == 0) L.bw_u = cv.take(L.n3 * L.es);
+      if (d[l].precision == FDTD_F64) L.bw_u = cv.take(L.n3 * L.es);  // FP32: one adjoint pass per step
       L.bw_nraw = (L.bw_K - 1) / o.check_every + 2;  // check steps inside a segment + its last step
       L.bw_raw = cv.take((size_t)L.bw_nraw * L.n3 * L.es);
       L.gv = (double*)cv.take(L.n3 * 8);

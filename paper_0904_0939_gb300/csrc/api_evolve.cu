@@ -83,8 +83,8 @@ void choose_config(fdtd_context* c, Lat& L) {
   {
     double rate = time_it(
         [&]() {
-          launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, false,
-                            nullptr, c->st);
+          launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, nullptr,
+                            c->st);
         },
         1);
     if (rate > best) {
@@ -165,8 +165,8 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
         launch_step_tma(L.maps[L.tx == 128][k - 1][L.cur], L.maps[L.tx == 128][k - 1][2], (float*)L.psi[1 - L.cur],
                         L.p, k, L.tx, k == depth ? L.zc : 0, active, c->flags + 1, c->st);
       else if (L.direct)
-        launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, false,
-                          active, c->st);
+        launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
+                          c->st);
       else
         launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
                                c->st);

@@ -64,7 +64,7 @@ struct Lat {
   void* pool = nullptr;
   void* seg = nullptr;
   void* lam[2] = {nullptr, nullptr};
-  void* bw_u = nullptr;    // B lam of the split adjoint step
+  void* bw_u = nullptr;    // B lam of the split FP64 adjoint step
   void* bw_raw = nullptr;  // step outputs before a check (and the segment's last output)
   int bw_nraw = 0;
   double* gv = nullptr;

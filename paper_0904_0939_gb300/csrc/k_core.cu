@@ -159,8 +159,8 @@ template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16
 // independent load instead of a z-march: on lattices too small to give a
 // z-marching grid many planes per block, each thread's loads no longer wait
 // on one another plane by plane.  The per-site arithmetic is k_step_f32's
-// (same bits).  ADJ: the adjoint form out = c S + alpha in (no B factor).
-template <bool P, bool ADJ>
+// (same bits).
+template <bool P>
 __global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ in, float* __restrict__ out,
                                                     const float* __restrict__ v, int n, float half_dtau,
                                                     float one_m6c, float cc, const int32_t* __restrict__ active) {
@@ -197,14 +197,7 @@ __global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ in
       xr = x4 < n4 - 1 ? __ldg(rp + 4 * x4 + 4) : 0.f;
     }
     const float4 vv = __ldg(reinterpret_cast<const float4*>(v) + q);
-    auto site = [&](float cv, float s, float vs) {
-      if constexpr (ADJ) {
-        const float alpha = __fsub_rn(one_m6c, __fmul_rn(half_dtau, vs));
-        return __fmaf_rn(cc, s, __fmul_rn(alpha, cv));
-      } else {
-        return update_f32(cv, s, coef_f32(vs, half_dtau, one_m6c), cc);
-      }
-    };
+    auto site = [&](float cv, float s, float vs) { return update_f32(cv, s, coef_f32(vs, half_dtau, one_m6c), cc); };
     float4 o;
     o.x = site(c.x, nbr_sum(xl, c.y, ym.x, yp.x, zm.x, zp.x), vv.x);
     o.y = site(c.y, nbr_sum(c.x, c.z, ym.y, yp.y, zm.y, zp.y), vv.y);
@@ -220,52 +213,97 @@ static int grid_f4(int n) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 64));
 }
 
-void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, bool adjoint,
-                       const int32_t* active, cudaStream_t st) {
-  auto k = p.periodic ? (adjoint ? k_direct_f32<true, true> : k_direct_f32<true, false>)
-                      : (adjoint ? k_direct_f32<false, true> : k_direct_f32<false, false>);
-  launch_pdl(k, dim3(grid_f4(p.n)), dim3(256), 0, st, in, out, v, p.n, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
+void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, const int32_t* active,
+                       cudaStream_t st) {
+  launch_pdl(p.periodic ? k_direct_f32<true> : k_direct_f32<false>, dim3(grid_f4(p.n)), dim3(256), 0, st, in, out, v,
+             p.n, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
 }
 
-// Pointwise half of a split FP32 adjoint step, four sites per thread:
-// u = B lam and g_V += -(dtau/2) u (psi_next + psi_prev), rounded as
-// k_adjoint_step_f32 rounds them (the direct stencil in adjoint form then
-// gives lam_out = c Adj(u) + alpha u).
-__global__ void __launch_bounds__(256) k_adjoint_u_f32(const float* __restrict__ lam,
-                                                       const float* __restrict__ psi_prev,
-                                                       const float* __restrict__ psi_next,
-                                                       const float* __restrict__ v, float* __restrict__ u,
-                                                       double* __restrict__ gv, size_t total4, float half_dtau,
-                                                       float one_m6c) {
+// One whole FP32 adjoint step, four x sites per thread (n % 4 == 0), no
+// z-march: with u = B lam formed as each value is loaded (B from V as the
+// forward computes it),
+//   lam_out = c Adj(u) + alpha u   and   g_V += -(dtau/2) u (psi_next + psi_prev),
+// the transpose of psi' = B (c Adj + alpha) psi and its site derivative.
+// The rounding is that of k_adjoint_step_f32 (same bits); u at the six
+// neighbours is recomputed (5.5 reciprocals per site) instead of stored.
+template <bool P>
+__global__ void __launch_bounds__(256) k_adjoint_direct_f32(const float* __restrict__ lam,
+                                                            const float* __restrict__ psi_prev,
+                                                            const float* __restrict__ psi_next,
+                                                            const float* __restrict__ v, float* __restrict__ lam_out,
+                                                            double* __restrict__ gv, int n, float half_dtau,
+                                                            float one_m6c, float cc) {
   pdl_wait();
   pdl_trigger();
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total4; q += (size_t)gridDim.x * blockDim.x) {
-    const float4 l = __ldg(reinterpret_cast<const float4*>(lam) + q);
+  const int n4 = n >> 2;
+  const size_t total = (size_t)n4 * n * n;
+  const float4* l4 = reinterpret_cast<const float4*>(lam);
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto wrap = [n](int q) { return q < 0 ? q + n : (q >= n ? q - n : q); };
+  auto b = [&](float vs) { return coef_f32(vs, half_dtau, one_m6c).b; };
+  auto u1 = [&](size_t i) { return __fmul_rn(b(__ldg(v + i)), __ldg(lam + i)); };
+  auto u4 = [&](size_t i4) {
+    const float4 l = __ldg(l4 + i4), vv = __ldg(v4 + i4);
+    return make_float4(__fmul_rn(b(vv.x), l.x), __fmul_rn(b(vv.y), l.y), __fmul_rn(b(vv.z), l.z),
+                       __fmul_rn(b(vv.w), l.w));
+  };
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int x4 = (int)(q % n4);
+    const size_t row = q / n4;  // z n + y
+    const int y = (int)(row % n), z = (int)(row / n);
+    auto at = [&](int yy, int zz) -> float4 {
+      if constexpr (P) {
+        yy = wrap(yy);
+        zz = wrap(zz);
+      } else if ((unsigned)yy >= (unsigned)n || (unsigned)zz >= (unsigned)n) {
+        return zero4;
+      }
+      return u4(((size_t)zz * n + yy) * n4 + x4);
+    };
+    const float4 vv = __ldg(v4 + q), l = __ldg(l4 + q);
+    const float4 c = make_float4(__fmul_rn(b(vv.x), l.x), __fmul_rn(b(vv.y), l.y), __fmul_rn(b(vv.z), l.z),
+                                 __fmul_rn(b(vv.w), l.w));
+    const float4 ym = at(y - 1, z), yp = at(y + 1, z), zm = at(y, z - 1), zp = at(y, z + 1);
+    const size_t r0 = row * n;
+    float xl, xr;
+    if constexpr (P) {
+      xl = u1(r0 + (x4 == 0 ? n - 1 : 4 * x4 - 1));
+      xr = u1(r0 + (x4 == n4 - 1 ? 0 : 4 * x4 + 4));
+    } else {
+      xl = x4 > 0 ? u1(r0 + 4 * x4 - 1) : 0.f;
+      xr = x4 < n4 - 1 ? u1(r0 + 4 * x4 + 4) : 0.f;
+    }
     const float4 pp = __ldg(reinterpret_cast<const float4*>(psi_prev) + q);
     const float4 pn = __ldg(reinterpret_cast<const float4*>(psi_next) + q);
-    const float4 vv = __ldg(reinterpret_cast<const float4*>(v) + q);
-    double2* g2 = reinterpret_cast<double2*>(gv) + 2 * q;
-    double2 g0 = g2[0], g1 = g2[1];
-    auto one = [&](float lv, float a, float b, float vs, double& g) {
-      const float uu = __fmul_rn(coef_f32(vs, half_dtau, one_m6c).b, lv);
-      g = __dadd_rn(g, (double)__fmul_rn(__fmul_rn(-half_dtau, uu), __fadd_rn(b, a)));
-      return uu;
+    auto out = [&](float cu, float s, float vs) {
+      const float alpha = __fsub_rn(one_m6c, __fmul_rn(half_dtau, vs));
+      return __fmaf_rn(cc, s, __fmul_rn(alpha, cu));
     };
     float4 o;
-    o.x = one(l.x, pp.x, pn.x, vv.x, g0.x);
-    o.y = one(l.y, pp.y, pn.y, vv.y, g0.y);
-    o.z = one(l.z, pp.z, pn.z, vv.z, g1.x);
-    o.w = one(l.w, pp.w, pn.w, vv.w, g1.y);
-    reinterpret_cast<float4*>(u)[q] = o;
+    o.x = out(c.x, nbr_sum(xl, c.y, ym.x, yp.x, zm.x, zp.x), vv.x);
+    o.y = out(c.y, nbr_sum(c.x, c.z, ym.y, yp.y, zm.y, zp.y), vv.y);
+    o.z = out(c.z, nbr_sum(c.y, c.w, ym.z, yp.z, zm.z, zp.z), vv.z);
+    o.w = out(c.w, nbr_sum(c.z, xr, ym.w, yp.w, zm.w, zp.w), vv.w);
+    reinterpret_cast<float4*>(lam_out)[q] = o;
+    double2* g2 = reinterpret_cast<double2*>(gv) + 2 * q;
+    double2 g0 = g2[0], g1 = g2[1];
+    auto dg = [&](float cu, float a, float bb) {
+      return (double)__fmul_rn(__fmul_rn(-half_dtau, cu), __fadd_rn(bb, a));
+    };
+    g0.x = __dadd_rn(g0.x, dg(c.x, pp.x, pn.x));
+    g0.y = __dadd_rn(g0.y, dg(c.y, pp.y, pn.y));
+    g1.x = __dadd_rn(g1.x, dg(c.z, pp.z, pn.z));
+    g1.y = __dadd_rn(g1.y, dg(c.w, pp.w, pn.w));
     g2[0] = g0;
     g2[1] = g1;
   }
 }
 
-void launch_adjoint_u_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v, float* u,
-                          double* gv, const Params& p, cudaStream_t st) {
-  launch_pdl(k_adjoint_u_f32, dim3(grid_f4(p.n)), dim3(256), 0, st, lam, psi_prev, psi_next, v, u, gv,
-             (size_t)(p.n >> 2) * p.n * p.n, p.half_dtau_f, p.one_m6c_f);
+void launch_adjoint_direct_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v,
+                               float* lam_out, double* gv, const Params& p, cudaStream_t st) {
+  launch_pdl(p.periodic ? k_adjoint_direct_f32<true> : k_adjoint_direct_f32<false>, dim3(grid_f4(p.n)), dim3(256), 0,
+             st, lam, psi_prev, psi_next, v, lam_out, gv, p.n, p.half_dtau_f, p.one_m6c_f, p.c_f);
 }
 
 // ------------------------------------------------------------------ adjoint stencil

@@ -188,14 +188,15 @@ void launch_adjoint_pointwise(const T* lam, const T* psi_prev, const T* psi_next
 template <typename T>
 void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v, const double* coefA, const Params& p,
                             cudaStream_t st);
-// FP32 stencil without z-march, four x sites per thread (n % 4 == 0):
-// adjoint = false is launch_step_f32's step (same bits); adjoint = true gives
-// out = c Adj(in) + alpha in, the stencil half of the split adjoint step
-void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, bool adjoint,
-                       const int32_t* active, cudaStream_t st);
-// pointwise half of the split FP32 adjoint step (n % 4 == 0): u = B lam, g_V accumulation
-void launch_adjoint_u_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v, float* u,
-                          double* gv, const Params& p, cudaStream_t st);
+// FP32 one-step stencil without z-march, four x sites per thread
+// (n % 4 == 0): launch_step_f32's step, same bits
+void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, const int32_t* active,
+                       cudaStream_t st);
+// one whole FP32 adjoint step the same way (n % 4 == 0): u = B lam on load,
+// lam_out = c Adj(u) + alpha u, g_V accumulation; same bits as
+// launch_adjoint_step_f32
+void launch_adjoint_direct_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v,
+                               float* lam_out, double* gv, const Params& p, cudaStream_t st);
 // one fused FP32 adjoint step (u = B lam, g_V accumulation, lam_out = M^T lam)
 void launch_adjoint_step_f32(const float* lam, const float* psi_prev, const float* psi_next, const float* v,
                              float* lam_out, double* gv, const Params& p, cudaStream_t st);
