@@ -42,7 +42,7 @@ SEED = 904939
 # dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
 # from an ncu capture of the current kernel, by (depth, span, tile width,
 # tile height); a tuned configuration without a capture reports traffic null
-TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048, (3, -1, 128, 16): 236_390_000}
+TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048, (3, -1, 128, 16): 237_899_008}
 
 
 def dist_env():
