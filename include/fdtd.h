@@ -111,8 +111,10 @@ typedef struct {
                              and no z-march where it applies (FP32, n % 4 == 0), else 1.
                              Results are identical for all. */
   int32_t autotune;       /* 1 (default): time every (depth, tile width, span) candidate and the
-                             one-step kernel on first use of a lattice size and keep the
-                             fastest (results are identical for all) */
+                             two one-step kernels on first use of a lattice size and keep the
+                             fastest (results are identical for all); FP32 lattices the TMA
+                             kernel does not take (periodic, n < 8) with n % 4 == 0 time the
+                             two one-step kernels */
   int32_t zchunk;         /* span of the TMA stencil when temporal_depth > 0: consecutive tile
                              planes per block, the x-y tile columns laid end to end with z
                              fastest (a span that divides n is a z-chunk; a longer or ragged

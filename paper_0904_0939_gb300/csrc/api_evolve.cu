@@ -11,13 +11,15 @@ namespace api {
 
 // ---- autotuning of the stencil configuration ---------------------------------
 // Fastest (depth, tile width, span, one-step kernel, direct four-site
-// one-step kernel) per (n, precision, device), shared by all handles.
+// one-step kernel) per (n, precision, device, periodic), shared by all
+// handles.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
+std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
 
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
+  const bool f4 = L.d.precision == FDTD_F32 && L.d.n % 4 == 0;  // the direct kernel applies
   L.plain = false;
   L.direct = false;
   if (!tma) {
@@ -25,10 +27,11 @@ void choose_config(fdtd_context* c, Lat& L) {
     L.tx = 128;
     L.zc = 0;
     L.plain = true;
-    L.direct = c->o.stencil_kernel == 2 && L.d.precision == FDTD_F32 && L.d.n % 4 == 0;
-    return;
-  }
-  if (c->o.temporal_depth > 0 || !c->o.autotune) {
+    L.direct = c->o.stencil_kernel == 2 && f4;
+    // a lattice the TMA kernel does not take (periodic, or n < 8) still
+    // times the two one-step kernels when none is forced
+    if (!(c->o.stencil_kernel == 0 && c->o.autotune && f4)) return;
+  } else if (c->o.temporal_depth > 0 || !c->o.autotune) {
     L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
     L.tx = L.d.n > 64 ? 128 : 64;
     L.zc = c->o.zchunk != 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
@@ -36,7 +39,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  auto key = std::make_tuple(L.d.n, L.d.precision, dev);
+  auto key = std::make_tuple(L.d.n, L.d.precision, dev, L.p.periodic);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
@@ -53,8 +56,8 @@ void choose_config(fdtd_context* c, Lat& L) {
   cudaEventCreate(&e1);
   const int n = L.d.n;
   double best = 0.0;
-  int bd = auto_depth(n, L.d.precision), bt = n > 64 ? 128 : 64, bz = tma_zchunk(n, bd, bt);
-  bool bp = false, bdir = false;
+  int bd = tma ? auto_depth(n, L.d.precision) : 1, bt = n > 64 ? 128 : 64, bz = tma ? tma_zchunk(n, bd, bt) : 0;
+  bool bp = !tma, bdir = false;
   auto time_it = [&](auto&& launch, int depth) {
     launch();
     const int reps = 3;
@@ -94,7 +97,7 @@ void choose_config(fdtd_context* c, Lat& L) {
       bdir = true;
     }
   }
-  for (int ti = 0; ti < 2; ++ti) {
+  for (int ti = 0; ti < (tma ? 2 : 0); ++ti) {
     const int tx = ti ? 128 : 64;
     if (tx == 128 && n <= 64) continue;
     for (int d = 1; d <= blocked_max_depth(); ++d) {
@@ -134,9 +137,11 @@ void choose_config(fdtd_context* c, Lat& L) {
   int32_t err = 0;
   cudaMemcpy(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (err) {  // the timed launches did no work: keep the heuristic, cache nothing
-    L.depth = auto_depth(n, L.d.precision);
-    L.tx = n > 64 ? 128 : 64;
-    L.zc = tma_zchunk(n, L.depth, L.tx);
+    if (tma) {
+      L.depth = auto_depth(n, L.d.precision);
+      L.tx = n > 64 ? 128 : 64;
+      L.zc = tma_zchunk(n, L.depth, L.tx);
+    }
     return;
   }
   L.depth = bd;

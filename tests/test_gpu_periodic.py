@@ -124,11 +124,12 @@ def test_periodic_upsample_matches_oracle(fd, per):
 def test_periodic_direct_kernel_bit_identical(fd, n):
     """The four-site one-step kernel with wrapped neighbours (stencil_kernel
     = 2) reproduces the periodic z-marching kernel bit for bit (n = 4: one
-    float4 per row, both x-neighbours wrap)."""
+    float4 per row, both x-neighbours wrap), and so does the autotuner's
+    choice between the two (stencil_kernel = 0)."""
     L = n / 3.0
     v = crystal(n, L).astype(np.float32)
     out = []
-    for k in (1, 2):
+    for k in (1, 2, 0):
         s = solver(fd, n, L, fd.F32, check_every=25, stencil_kernel=k)
         s.set_potential(v)
         s.init_symmetric(9, 0)
@@ -136,6 +137,7 @@ def test_periodic_direct_kernel_bit_identical(fd, n):
         out.append(s.get_psi(dtype=np.float32))
         s.close()
     np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("n", [10, 12])
