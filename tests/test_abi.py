@@ -114,3 +114,42 @@ def test_null_handle_calls_fail_cleanly(fd):
     assert fd.lib.fdtd_evolve(None, 10, None) == fd.ERR_INVALID_ARG
     assert fd.lib.fdtd_destroy(None) == fd.ERR_INVALID_ARG
     assert fd.lib.fdtd_set_potential(None, 0, None, 0, 0) == fd.ERR_INVALID_ARG
+
+
+def _struct_fields(text, name):
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"\b(\w+)(?:\s*\[\s*\d+\s*\])?\s*;", body)
+
+
+def test_struct_layouts_match_the_header(fd, tmp_path):
+    """Size and every field offset of the public structs, as gcc lays them
+    out from include/fdtd.h, equal the ctypes definitions of the binding."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    text = open(os.path.join(ROOT, "include", "fdtd.h")).read()
+    pairs = {"fdtd_lattice_desc": fd.LatticeDesc, "fdtd_options": fd.Options, "fdtd_obs": fd.Obs,
+             "fdtd_stats": fd.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fdtd.h"', "int main(void) {"]
+    for cname in pairs:
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in _struct_fields(text, cname):
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for row in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = row.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        names = _struct_fields(text, cname)
+        assert names == [f for f, _ in cls._fields_], cname
+        for f in names:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
