@@ -424,38 +424,93 @@ def multires(levels, potentials, mask: int = 0, seed: int = 904939, options: Opt
 def observables_noalloc(psi, v, length: float, mass: float = 1.0, out=None, stream=None):
     """Lattice sums of a caller-held CUDA field without any allocation in the
     library (fdtd_observables_noalloc).  psi and v are contiguous CUDA
-    tensors of n^3 values, both float64 or both float32; out is a CUDA
-    float64 tensor of 8 values (allocated here if not given).  Returns out:
-    [E, <r^2>, <V>, sum psi^2 a^3, S0, SH, Sr, SV]."""
+    tensors of n^3 values on one device, both float64 or both float32; out
+    is a contiguous float64 CUDA tensor of at least 8 values on that device
+    (allocated here if not given).  Returns out:
+    [E, <r^2>, <V>, sum psi^2 a^3, S0, SH, Sr, SV].
+
+    Everything the C entry cannot check on a raw pointer (dtype, device,
+    layout, length of out) is checked here before the call; the kernels are
+    enqueued on `stream` (default: the current stream of psi's device) and
+    the call does not synchronise."""
     import torch
 
+    for name, t in (("psi", psi), ("v", v)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise FdtdError(ERR_INVALID_ARG, f"observables_noalloc: {name} must be a CUDA tensor")
+        if t.dtype not in (torch.float32, torch.float64):
+            raise FdtdError(ERR_INVALID_ARG, f"observables_noalloc: {name} must be float32 or float64, not {t.dtype}")
+        if not t.is_contiguous():
+            raise FdtdError(ERR_INVALID_ARG, f"observables_noalloc: {name} must be contiguous")
+    if psi.dtype != v.dtype or psi.device != v.device:
+        raise FdtdError(ERR_INVALID_ARG, "observables_noalloc: psi and v need one dtype and one device")
     n = round(psi.numel() ** (1.0 / 3.0))
-    if psi.numel() != n**3 or v.numel() != n**3 or psi.dtype != v.dtype or not psi.is_cuda:
-        raise FdtdError(ERR_INVALID_ARG, "psi and v must be CUDA tensors of n^3 values with one dtype")
-    code = F64 if psi.dtype == torch.float64 else F32
+    if n < 1 or psi.numel() != n**3 or v.numel() != n**3:
+        raise FdtdError(ERR_SHAPE, "observables_noalloc: psi and v must hold n^3 values each")
     if out is None:
         out = torch.empty(8, dtype=torch.float64, device=psi.device)
+    elif (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or out.device != psi.device
+          or not out.is_contiguous() or out.numel() < 8):
+        raise FdtdError(ERR_INVALID_ARG,
+                        "observables_noalloc: out must be a contiguous float64 tensor of >= 8 values on psi's device")
+    code = F64 if psi.dtype == torch.float64 else F32
     st = stream if stream is not None else torch.cuda.current_stream(psi.device)
     with torch.cuda.device(psi.device):
-        _check(lib.fdtd_observables_noalloc(ctypes.c_void_p(psi.contiguous().data_ptr()),
-                                            ctypes.c_void_p(v.contiguous().data_ptr()), code, n, float(length),
-                                            float(mass), ctypes.c_void_p(out.data_ptr()),
+        _check(lib.fdtd_observables_noalloc(ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(v.data_ptr()), code, n,
+                                            float(length), float(mass), ctypes.c_void_p(out.data_ptr()),
                                             ctypes.c_void_p(st.cuda_stream)))
+    if st != torch.cuda.current_stream(psi.device):
+        # the kernels read psi and v (and write out) later on another stream:
+        # keep the caching allocator from handing their memory out meanwhile
+        for t in (psi, v, out):
+            t.record_stream(st)
     return out
 
 
 def energy_fn():
-    """torch.autograd.Function computing (E, <r^2>) after T unrolled steps
-    from a seeded start, with dV from fdtd_backward (sqrt(T) checkpointing)."""
+    """The torch.autograd.Function (E, <r^2>) = F(V) of T unrolled update
+    steps (Eq. updateeq) with the checks of fdtd_evolve, whose backward is
+    fdtd_backward (sqrt(T) checkpointing, the adjoint step).
+
+    ``EnergyFn.apply(v, solver, T, psi0=None, seed=0, mask=0)``:
+      v       the potential, n^3 values (any float tensor; on the GPU or the
+              host); V_theta built from parameters theta in torch gives
+              dL/dtheta through torch's own chain rule
+      solver  a Solver of one lattice created with options tol <= 0 (the
+              forward must run exactly T steps: a tolerance would stop it at
+              convergence, and the gradient would belong to another T) and
+              backward_steps >= T
+      psi0    the start field (n^3 values, e.g. the oscillator Gaussian);
+              None draws the seeded symmetric random start (seed, mask)
+      mask    the symmetry mask imposed on the start and at every check
+    Returns two float64 scalars on v's device: E and <r^2> at step T."""
     import torch
 
     class EnergyFn(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, v, solver, T, seed, mask):
+        def forward(ctx, v, solver, T, psi0=None, seed=0, mask=0):
+            T = int(T)
+            if len(solver.lattices) != 1:
+                raise FdtdError(ERR_INVALID_ARG, "EnergyFn: the solver must hold exactly one lattice")
+            if T < 1:
+                raise FdtdError(ERR_INVALID_ARG, "EnergyFn: T must be >= 1")
+            if solver.options.tol > 0:
+                raise FdtdError(ERR_INVALID_ARG, "EnergyFn: the solver needs options.tol <= 0 so that the forward "
+                                "runs exactly T steps (a tolerance would end it early at convergence)")
+            if solver.options.batched:
+                raise FdtdError(ERR_INVALID_ARG, "EnergyFn: batched handles have no backward pass")
+            if solver.options.backward_steps < T:
+                raise FdtdError(ERR_WORKSPACE, f"EnergyFn: options.backward_steps = {solver.options.backward_steps} "
+                                f"< T = {T}: create the solver with backward_steps >= T")
             solver.set_potential(v.detach())
-            solver.init_symmetric(seed, mask)
-            solver.evolve(T)
+            if psi0 is not None:
+                solver.set_psi(psi0.detach() if isinstance(psi0, torch.Tensor) else psi0, mask=mask)
+            else:
+                solver.init_symmetric(seed, mask)
+            steps, _ = solver.evolve(T)
             o = solver.last_check()
+            if steps != T or o["steps"] != T:
+                raise FdtdError(ERR_STATE, f"EnergyFn: the forward ran {steps} steps, not T = {T}")
             ctx.solver, ctx.T = solver, T
             ctx.shape, ctx.dtype, ctx.device = v.shape, v.dtype, v.device
             return (torch.tensor(o["energy"], dtype=torch.float64, device=v.device),
@@ -463,8 +518,10 @@ def energy_fn():
 
         @staticmethod
         def backward(ctx, g_e, g_r):
-            out = torch.empty(ctx.shape, dtype=torch.float64, device=ctx.device)
+            dev = ctx.device if ctx.device.type == "cuda" else ctx.solver.device
+            out = torch.empty(ctx.shape, dtype=torch.float64, device=dev)
+            # the loss weights are the incoming gradients of the two outputs
             ctx.solver.backward(ctx.T, float(g_e), float(g_r), out=out)
-            return out.to(ctx.dtype), None, None, None, None
+            return out.to(device=ctx.device, dtype=ctx.dtype), None, None, None, None, None
 
     return EnergyFn

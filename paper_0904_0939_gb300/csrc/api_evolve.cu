@@ -11,10 +11,13 @@ namespace api {
 
 // ---- autotuning of the stencil configuration ---------------------------------
 // Fastest (depth, tile width, span, one-step kernel, direct four-site
-// one-step kernel) per (n, precision, device, periodic), shared by all
-// handles.
+// one-step kernel) per (n, precision, device, periodic, TMA kernel usable),
+// shared by all handles.  The last key member keeps a lattice whose tensor
+// maps could not be encoded (timed on the one-step kernels only) from
+// handing its choice to lattices of the same size that can use the TMA
+// kernel.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
+std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
 
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
@@ -39,7 +42,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  auto key = std::make_tuple(L.d.n, L.d.precision, dev, L.p.periodic);
+  auto key = std::make_tuple(L.d.n, L.d.precision, dev, L.p.periodic, (int)tma);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);

@@ -34,7 +34,9 @@ def test_theta_gradients_128_finite_differences_and_hellmann_feynman(fd):
     unrolled steps from the oscillator Gaussian: the adjoint gradient of E
     and <r^2> w.r.t. theta (sqrt(T) checkpointing) against central
     differences of the FP64 forward (h = 1e-4), the FP32 adjoint against the
-    FP64 one, and dE/dtheta against Hellmann-Feynman <G_k>."""
+    FP64 one, and dE/dtheta against Hellmann-Feynman <G_k>; then the same
+    gradient of E + 0.3 <r^2> through torch (EnergyFn) against the central
+    differences."""
     n, L, T = 128, 10.0, 4000
     G, th = wl.config_theta(n, L)
     v = wl.v_theta(n, L, th, G)
@@ -84,6 +86,27 @@ def test_theta_gradients_128_finite_differences_and_hellmann_feynman(fd):
     w = psi_t**2 / np.sum(psi_t**2)
     hf = np.tensordot(G, w, axes=3)
     assert np.max(np.abs(ge64 - hf)) <= 2e-2 * np.max(np.abs(hf))
+    # the same gradients through torch: V_theta built from theta in torch,
+    # EnergyFn over fdtd_backward, theta.grad by torch's chain rule
+    import torch
+
+    dev = torch.device("cuda")
+    Gt = torch.from_numpy(G).to(dev)
+    r2 = torch.from_numpy(wl.radius2(n, L)).to(dev)
+    psi0_t = torch.from_numpy(psi0).to(dev)
+    w_r = 0.3
+    want = fd_e + w_r * fd_r
+    through_torch = {}
+    for prec in (fd.F64, fd.F32):
+        theta = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
+        s = solver(prec, True)
+        E, R = fd.energy_fn().apply(0.5 * r2 + torch.tensordot(theta, Gt, dims=1), s, T, psi0_t)
+        (E + w_r * R).backward()
+        through_torch[prec] = theta.grad.cpu().numpy()
+        assert float(E) == pytest.approx(grads[prec][2]["energy"], rel=1e-12)
+        s.close()
+    np.testing.assert_allclose(through_torch[fd.F64], want, rtol=1e-5, atol=1e-7 * np.abs(want).max())
+    assert np.max(np.abs(through_torch[fd.F32] - want)) <= 1e-3 * np.max(np.abs(want))
 
 
 # ------------------------------------------------------------------ full-size sampled parity
@@ -173,6 +196,26 @@ def test_paper_dodecahedron_128(fd, printed):
     print(f"dodecahedron 128^3 ({'printed' if printed else 'regular'} vertices): E0 = {e:.5f}")
     assert -100.0 < e < -99.5
     assert e == pytest.approx(g["E0"], rel=1e-3)
+
+
+def test_dodecahedron_24_matches_oracle(fd, orc):
+    """The dodecahedral well (Eq. dodecahedronpotential) at 24^3, a = 0.1,
+    dtau = 0.001, m = 1: 100 steps from the seeded random start with a check
+    every 50, element by element against the oracle: FP64 to 1e-12, FP32 to
+    2e-5 (max-norm relative), energies to 1e-12 / 1e-6."""
+    n, a, dtau = 24, 0.1, 1e-3
+    v = wl.dodecahedron(n)
+    psi0 = orc.init_symmetric(n, 7, 0)
+    ref, rec, _ = orc.evolve(psi0, v, a, dtau, 100, 50, 0.0, False, 0)
+    for prec, tol in ((fd.F64, 1e-12), (fd.F32, 2e-5)):
+        s = fd.Solver(fd.Lattice(n, n * a, prec, dtau=dtau), fd.default_options(check_every=50, tol=0.0))
+        s.set_potential(v.astype(np.float32) if prec == fd.F32 else v)
+        s.set_psi(psi0)
+        s.evolve(100)
+        got = s.get_psi()
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)), prec
+        assert s.last_check()["energy"] == pytest.approx(rec["E"], rel=1e-12 if prec == fd.F64 else 1e-6)
+        s.close()
 
 
 def test_paper_antisymmetric_z_coulomb_256(fd):

@@ -488,6 +488,26 @@ def test_backward_matches_oracle(fd, orc, n, mask, T, ce):
         assert o["energy"] == pytest.approx(obs["E"], rel=1e-12 if prec == fd.F64 else 1e-6)
 
 
+def test_backward_fp32_across_tiles_matches_oracle(fd, orc):
+    """The FP32 adjoint at n = 132: the four-site adjoint pass and the
+    blocked forward cover several 128-wide tiles with a ragged 4-site tail
+    and many z-chunks.  dL/dV of L = E + 0.3 <r^2> after T = 24 steps with
+    checks every 10 (A_x projection), element by element against the
+    oracle's full-trajectory adjoint to 1e-4 (max-norm relative)."""
+    n, L, T, ce, mask = 132, 10.0, 24, 10, wl.ODD_X
+    a = L / n
+    v = wl.anisotropic(n, L)
+    psi0 = orc.init_symmetric(n, 5, mask)
+    ref, obs = orc.backward(psi0, v, a, a * a / 4, T, ce, mask, 1.0, 0.3)
+    s = solver(fd, n, L, fd.F32, check_every=ce, backward_steps=T)
+    s.set_potential(v)
+    s.set_psi(psi0, mask=mask)
+    g, o = s.backward(T, 1.0, 0.3)
+    assert rel_max(g, ref) <= 1e-4
+    assert o["energy"] == pytest.approx(obs["E"], rel=1e-6)
+    s.close()
+
+
 # ------------------------------------------------------------------ snapshots
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])

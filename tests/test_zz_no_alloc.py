@@ -82,3 +82,48 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(fd):
                                          10.0, 1.0, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == fd.ERR_SHAPE
     assert "1024" in fd.last_error(None)
+
+
+def test_noalloc_python_wrapper_all_eight_values(fd):
+    """fd.observables_noalloc (n inferred from the tensor, dtype mapped, the
+    current stream) against Solver.observables: the four derived values and
+    the four raw sums S0 = norm / a^3, SH = E S0, Sr = <r^2> S0, SV = <V> S0."""
+    import torch
+
+    n, length = 40, 8.0
+    a = length / n
+    rng = np.random.default_rng(3)
+    v = wl.anisotropic(n, length).astype(np.float32).astype(np.float64)
+    psi = (np.exp(-0.5 * wl.radius2(n, length)) * (1 + 0.1 * rng.standard_normal((n, n, n)))).astype(np.float32)
+    psi = psi.astype(np.float64)
+    ref = regular(fd, psi, v, length, fd.F32)
+    for _ in range(2):
+        out = fd.observables_noalloc(torch.from_numpy(psi).to("cuda", torch.float32),
+                                     torch.from_numpy(v).to("cuda", torch.float32), length)
+        got = out.cpu().numpy()
+        s0 = ref["norm"] / a**3
+        want = [ref["energy"], ref["r2"], ref["v_expect"], ref["norm"], s0, ref["energy"] * s0, ref["r2"] * s0,
+                ref["v_expect"] * s0]
+        np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+def test_noalloc_python_wrapper_refuses_what_the_kernels_would_misread(fd):
+    """dtypes other than float32/float64, a mismatched pair, a short or
+    non-float64 out and non-contiguous fields are refused on the host."""
+    import torch
+
+    n = 8
+    f32 = torch.zeros((n, n, n), dtype=torch.float32, device="cuda")
+    for bad in (f32.to(torch.bfloat16), f32.to(torch.float16), f32.to(torch.int32)):
+        with pytest.raises(fd.FdtdError):
+            fd.observables_noalloc(bad, bad, 4.0)
+    with pytest.raises(fd.FdtdError):
+        fd.observables_noalloc(f32, f32.double(), 4.0)
+    with pytest.raises(fd.FdtdError):
+        fd.observables_noalloc(f32, f32, 4.0, out=torch.zeros(8, dtype=torch.float32, device="cuda"))
+    with pytest.raises(fd.FdtdError):
+        fd.observables_noalloc(f32, f32, 4.0, out=torch.zeros(7, dtype=torch.float64, device="cuda"))
+    with pytest.raises(fd.FdtdError):
+        fd.observables_noalloc(f32, f32, 4.0, out=torch.zeros(8, dtype=torch.float64))
+    with pytest.raises(fd.FdtdError):
+        fd.observables_noalloc(f32.transpose(0, 2), f32, 4.0)
