@@ -1,26 +1,35 @@
 """Benchmark of the FDTD hot path on one GB300 (or N replicas under torchrun).
 
-Workload (one "step"): the soft-core Coulomb problem V = -1/sqrt(r^2 + a^2)
-in a box of L = 40 Bohr radii, solved for two symmetry sectors -- the
-all-symmetric sector (1s, E -> -1/2) and the A_x sector (2p_x, E -> -1/8) --
-by the multi-resolution bootstrap 64^3 -> 128^3 -> 256^3 (Sec. VI): random
-start on 64^3, FP32 stencil, FP64/compensated sums, check every 100 steps,
-convergence of the binding energy to a part in 10^6 at every level
-(Sec. V), trilinear transfer to the next level.  Every row of the hot path
-runs inside the step: potential upload, symmetric random start, update
-steps, sums, renormalisation + symmetry re-imposition, transfer.
+Workload (one "step"): the anisotropic oscillator V = (x^2 + 2y^2 + 3z^2)/2
+plus 32 seeded Gaussians (amplitude U[-1/2, 1/2], width U[1/2, 2]) in a box
+of L = 16, solved for its ground state by the multi-resolution bootstrap
+(Sec. VI): random start on 128^3 with BF16 storage, 256^3 BF16, then 512^3
+FP32 (0.5 GB per field); FP64/compensated sums, a check every 100 steps,
+convergence of the energy to 1e-4 on the BF16 levels and to a part in 10^6
+on the 512^3 level (Sec. V), trilinear transfer between levels.  Every row
+of the hot path runs inside the step: potential upload, random start,
+update steps, sums, renormalisation, transfer.
 
-metric: site updates per second (interior sites x update steps, all levels,
-both sectors), whole job; "value" times the device work with V already
-resident in HBM, "e2e" the same call with V in pinned host memory
-(host->device copies inside the timed region) and the observables read back.
+metric: site updates per second (interior sites x update steps, all three
+levels), whole job; "value" times the device work with V already resident
+in HBM, "e2e" the same call with V in pinned host memory (host->device
+copies inside the timed region) and the observables read back.
+"roofline" is the dominant kernel, the stencil of the 512^3 level.
+
+Extras: the soft-core Coulomb chain 64^3 -> 128^3 -> 256^3 for two
+symmetry sectors, time to |dE| < 1e-6 of the FP32 multi-resolution path
+against the plain FP64 form, the 64-lattice batch in one persistent launch
+(with its own roofline), the theta-gradient through torch (EnergyFn) on
+128^3 x 4000 steps, the plain FP64 form's rate at 512^3 and the FP32
+chain's error against an FP64-converged energy.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (update steps with checks on the 256^3 lattice).
+workload (update steps with checks on the 512^3 lattice).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -34,15 +43,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gsite-updates/s"
-LEVELS = (64, 128, 256)
-LENGTH = 40.0
-SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
-TOL = 1e-6
 SEED = 904939
-# dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 stencil launch
-# from an ncu capture of the current kernel, by (depth, span, tile width,
-# tile height); a tuned configuration without a capture reports traffic null
-TRAFFIC_256 = {(3, 54, 128, 16): 238_210_048, (3, -1, 128, 16): 237_899_008}
+TOL = 1e-6
+# the headline chain: (n, storage, relative tolerance)
+C3_LENGTH = 16.0
+C3_PLAN = ((128, "bf16", 1e-4), (256, "bf16", 1e-4), (512, "f32", TOL))
+# the Coulomb chain (an extra)
+C2_LEVELS = (64, 128, 256)
+C2_LENGTH = 40.0
+C2_SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
+# dram__bytes_read.sum + dram__bytes_write.sum of one stencil launch from an
+# ncu capture, keyed by the digest of the stencil's source files and the
+# launch configuration (n, depth, span, tile width, tile height).  A kernel
+# changed since its capture has another digest, so its traffic is reported
+# as null (with the reason) instead of a stale figure.
+STENCIL_SOURCES = ("paper_0904_0939_gb300/csrc/tma_item.cuh", "paper_0904_0939_gb300/csrc/k_tblock.cu",
+                   "paper_0904_0939_gb300/csrc/common.cuh")
+TRAFFIC = {}
+
+
+def stencil_digest() -> str:
+    h = hashlib.sha256()
+    for rel in STENCIL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def dist_env():
@@ -52,62 +77,166 @@ def dist_env():
     return ws, rank, local
 
 
-def potentials(resident: bool, device):
-    import numpy as np
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------------------- C3: the headline
+
+def c3_potentials(resident: bool, device):
     import torch
 
     import workloads as wl
 
     out = []
-    for n in LEVELS:
-        v = wl.coulomb_soft(n, LENGTH).astype(np.float32)
+    for n, _, _ in C3_PLAN:
+        v = wl.anisotropic_device(n, C3_LENGTH, device, dtype=torch.float32)
         # host-resident: pinned (page-locked) memory, so each step's copies are plain DMA
-        out.append(torch.from_numpy(v).to(device) if resident else torch.from_numpy(v).pin_memory())
+        out.append(v if resident else v.cpu().pin_memory())
     return out
 
 
-def run_step(fd, pots, seed, opts):
-    """Both sectors, three levels each: one handle per level holding the two
-    sectors' lattices (their evolve loops run concurrently, each lattice
-    upsampled from its own sector's coarser level).  Returns a dict of
-    totals: site updates, kernel launches, and the stencil time / algorithmic
-    bytes of the finest level (the dominant kernel), plus per-level results."""
+def c3_step(fd, pots, seed, keep_last=False):
+    """One pass of the chain: one handle per level, random start on the
+    first, transfer into the next.  Returns totals: site updates, kernel
+    launches, the 512^3 level's stencil time / algorithmic bytes / updates,
+    and per-level results."""
     import torch
 
-    tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0,
-           "fine_launches": 0, "fine_timed": 0, "results": {}, "config": None, "level_ms": {}}
+    prec = {"bf16": fd.BF16, "f32": fd.F32}
+    tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0, "fine_launches": 0,
+           "fine_timed": 0, "results": {}, "config": None, "last": None}
     prev = None
-    for lvl, n in enumerate(LEVELS):
+    for (n, kind, tol), v in zip(C3_PLAN, pots):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        s = fd.Solver([fd.Lattice(n, LENGTH, fd.F32) for _ in SECTORS], opts)
-        s.set_profiling(n == LEVELS[-1])
-        for i, (name, mask) in enumerate(SECTORS):
-            s.set_potential(pots[lvl], lat=i)
-            if prev is None:
-                s.init_symmetric(seed, mask, lat=i)
-            else:
-                s.upsample_from(prev, lat_src=i, lat=i)
-        _, conv = s.evolve(2_000_000)
+        s = fd.Solver(fd.Lattice(n, C3_LENGTH, prec[kind]), fd.default_options(check_every=100, tol=tol,
+                                                                               tol_relative=1))
+        fine = n == C3_PLAN[-1][0]
+        s.set_profiling(fine)
+        s.set_potential(v)
+        if prev is None:
+            s.init_symmetric(seed, 0)
+        else:
+            s.upsample_from(prev)
+        steps, conv = s.evolve(2_000_000)
         st = s.stats()
         tot["launches"] += st["launches"]
-        if n == LEVELS[-1]:
+        if fine:
             tot["fine_ms"] += st["stencil_ms"]
             tot["fine_bytes"] += st["stencil_bytes"]
             tot["fine_updates"] += st["stencil_site_updates"]
             tot["fine_launches"] += st["stencil_launches"]
             tot["fine_timed"] += st["stencil_timed_launches"]
             tot["config"] = s.tuned_config() + s.tuned_kernel()
+        o = s.last_check()
         ev1.record()
         ev1.synchronize()
-        tot["level_ms"][str(n)] = ev0.elapsed_time(ev1)
-        tuned = list(s.tuned_config()) + list(s.tuned_kernel())
-        for i, (name, _) in enumerate(SECTORS):
+        tot["updates"] += n**3 * o["steps"]
+        tot["results"][f"{n}_{kind}"] = {"E": o["energy"], "r2": o["r2"], "steps": o["steps"],
+                                         "converged": bool(o["converged"]), "level_ms": ev0.elapsed_time(ev1),
+                                         "stencil": list(s.tuned_config()) + list(s.tuned_kernel())}
+        if prev is not None:
+            prev.close()
+        prev = s
+    if keep_last:
+        tot["last"] = prev
+    else:
+        prev.close()
+    return tot
+
+
+def c3_fp64_reference(fd, fine, dev):
+    """The plain FP64 form at 512^3 and an FP64-converged energy for the
+    chain's result: the chain's final field is first run on in FP32 to its
+    rounding floor (1e-9 relative per check, at most 40k steps), then in
+    FP64 until E changes by less than 1e-10 relative per check; the FP64
+    form's rate is timed on 1000 further FP64 steps (CUDA events)."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+
+    n = C3_PLAN[-1][0]
+    e32 = fine.last_check()
+    v64 = wl.anisotropic_device(n, C3_LENGTH, dev, dtype=torch.float64)
+    r = fd.Solver(fd.Lattice(n, C3_LENGTH, fd.F32), fd.default_options(check_every=100, tol=1e-9, tol_relative=1))
+    r.set_potential(v64.float())
+    psi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    fine.get_psi(out=psi)
+    r.set_psi(psi)
+    s32, _ = r.evolve(40_000)
+    r.get_psi(out=psi)
+    r.close()
+    d = fd.Solver(fd.Lattice(n, C3_LENGTH, fd.F64), fd.default_options(check_every=100, tol=1e-10, tol_relative=1))
+    d.set_potential(v64)
+    d.set_psi(psi.double())
+    del psi
+    s64, conv = d.evolve(20_000)
+    ref = d.last_check()
+    # rate of the plain FP64 form: a fixed number of steps, no tolerance
+    t = fd.Solver(fd.Lattice(n, C3_LENGTH, fd.F64), fd.default_options(check_every=100, tol=0.0))
+    t.set_potential(v64)
+    t.init_symmetric(SEED, 0)
+    t.evolve(200)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    t.evolve(1000)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t.close()
+    d.close()
+    del v64
+    torch.cuda.empty_cache()
+    return {"E_ref_fp64": ref["energy"], "r2_ref_fp64": ref["r2"], "fp32_refine_steps": s32,
+            "fp64_steps": s64, "fp64_converged": bool(conv),
+            "chain_E_rel_err": abs(e32["energy"] - ref["energy"]) / abs(ref["energy"]),
+            "chain_r2_rel_err": abs(e32["r2"] - ref["r2"]) / abs(ref["r2"]),
+            "fp64_form_gsite_per_s": n**3 * 1000 / (ms * 1e-3) / 1e9, "fp64_form_ms_per_1000_steps": ms}
+
+
+# --------------------------------------------------------------------------- C2: the Coulomb chain (extra)
+
+def c2_potentials(device):
+    import numpy as np
+    import torch
+
+    import workloads as wl
+
+    return [torch.from_numpy(wl.coulomb_soft(n, C2_LENGTH).astype(np.float32)).to(device) for n in C2_LEVELS]
+
+
+def c2_step(fd, pots, seed, opts):
+    """Both sectors, three levels each: one handle per level holding the two
+    sectors' lattices (their evolve loops run concurrently, each lattice
+    upsampled from its own sector's coarser level)."""
+    tot = {"updates": 0, "launches": 0, "results": {}}
+    prev = None
+    for lvl, n in enumerate(C2_LEVELS):
+        s = fd.Solver([fd.Lattice(n, C2_LENGTH, fd.F32) for _ in C2_SECTORS], opts)
+        for i, (name, mask) in enumerate(C2_SECTORS):
+            s.set_potential(pots[lvl], lat=i)
+            if prev is None:
+                s.init_symmetric(seed, mask, lat=i)
+            else:
+                s.upsample_from(prev, lat_src=i, lat=i)
+        s.evolve(2_000_000)
+        tot["launches"] += s.stats()["launches"]
+        for i, (name, _) in enumerate(C2_SECTORS):
             o = s.last_check(lat=i)
             tot["updates"] += n**3 * o["steps"]
-            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "r2": o["r2"], "steps": o["steps"],
-                                             "converged": bool(o["converged"]), "level_ms": ev0.elapsed_time(ev1),
-                                             "stencil": tuned}
+            tot["results"][f"{name}_{n}"] = {"E": o["energy"], "steps": o["steps"], "converged": bool(o["converged"])}
         if prev is not None:
             prev.close()
         prev = s
@@ -115,9 +244,32 @@ def run_step(fd, pots, seed, opts):
     return tot
 
 
-def time_to_e0(fd, pots, seed, opts, dev):
-    """Wall time until |E - E_ref| < 1e-6 |E_ref| per sector, E_ref being the
-    plain FP64 256^3 solve converged to 1e-11 (relative): the FP32
+def c2_run(fd, dev, seed, flush, steps=3):
+    import torch
+
+    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1)
+    pots = c2_potentials(dev)
+    for _ in range(2):
+        c2_step(fd, pots, seed, opts)
+    ms, upd, res = 0.0, 0, None
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tot = c2_step(fd, pots, seed, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        upd += tot["updates"]
+        res = tot["results"]
+    return {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px", "gsite_per_s": upd / (ms * 1e-3) / 1e9,
+            "ms_per_step": ms / steps, "steps": steps, "results": res}
+
+
+def time_to_e0(fd, seed, dev):
+    """Wall time until |E - E_ref| < 1e-6 |E_ref| per Coulomb sector, E_ref
+    being the plain FP64 256^3 solve converged to 1e-11 (relative): the FP32
     multi-resolution path (coarse levels to a part in 10^6, the 256^3 level in
     chunks of 100 steps until within 1e-6 of E_ref) against the plain FP64
     form from a random start on the same GB300, both timed with CUDA events
@@ -127,7 +279,9 @@ def time_to_e0(fd, pots, seed, opts, dev):
     import workloads as wl
 
     out = {}
-    v64 = torch.from_numpy(wl.coulomb_soft(LEVELS[-1], LENGTH)).to(dev)
+    pots = c2_potentials(dev)
+    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1)
+    v64 = torch.from_numpy(wl.coulomb_soft(C2_LEVELS[-1], C2_LENGTH)).to(dev)
     ref_opts = fd.default_options(check_every=100, tol=1e-11, tol_relative=1)
     chunk_opts = fd.default_options(check_every=100, tol=0.0)
 
@@ -145,8 +299,8 @@ def time_to_e0(fd, pots, seed, opts, dev):
                 break
         return steps, t_ms * 1e-3
 
-    for name, mask in SECTORS:
-        r = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F64), ref_opts)
+    for name, mask in C2_SECTORS:
+        r = fd.Solver(fd.Lattice(C2_LEVELS[-1], C2_LENGTH, fd.F64), ref_opts)
         r.set_potential(v64)
         r.init_symmetric(seed + 17, mask)
         ref_steps, _ = r.evolve(1_000_000)
@@ -156,8 +310,8 @@ def time_to_e0(fd, pots, seed, opts, dev):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         prev = None
-        for lvl, n in enumerate(LEVELS[:-1]):
-            s = fd.Solver(fd.Lattice(n, LENGTH, fd.F32), opts)
+        for lvl, n in enumerate(C2_LEVELS[:-1]):
+            s = fd.Solver(fd.Lattice(n, C2_LENGTH, fd.F32), opts)
             s.set_potential(pots[lvl])
             if prev is None:
                 s.init_symmetric(seed, mask)
@@ -165,7 +319,7 @@ def time_to_e0(fd, pots, seed, opts, dev):
                 s.upsample_from(prev)
             s.evolve(2_000_000)
             prev = s
-        fine = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F32), chunk_opts)
+        fine = fd.Solver(fd.Lattice(C2_LEVELS[-1], C2_LENGTH, fd.F32), chunk_opts)
         fine.set_potential(pots[-1])
         fine.upsample_from(prev)
         e1.record()
@@ -174,7 +328,7 @@ def time_to_e0(fd, pots, seed, opts, dev):
         mr_steps, mr_s = until_within(fine, e_ref)
         e_mr = fine.last_check()["energy"]
         # plain FP64 from a random start
-        p64 = fd.Solver(fd.Lattice(LEVELS[-1], LENGTH, fd.F64), chunk_opts)
+        p64 = fd.Solver(fd.Lattice(C2_LEVELS[-1], C2_LENGTH, fd.F64), chunk_opts)
         e0.record()
         p64.set_potential(v64)
         p64.init_symmetric(seed, mask)
@@ -192,73 +346,13 @@ def time_to_e0(fd, pots, seed, opts, dev):
     return out
 
 
-def anisotropic_multires(fd, dev, seed):
-    """The 512^3, L = 16 anisotropic workload (oscillator + 32 Gaussians):
-    128^3 and 256^3 levels with BF16 storage (to 1e-4), the 512^3 level in
-    FP32 to a part in 10^6."""
-    import torch
+# --------------------------------------------------------------------------- C4 and C5 (extras)
 
-    import workloads as wl
-
-    L = 16.0
-    plan = ((128, fd.BF16, 1e-4), (256, fd.BF16, 1e-4), (512, fd.F32, TOL))
-    pots = [wl.anisotropic_device(n, L, dev, dtype=torch.float32) for n, _, _ in plan]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    prev, upd, levels = None, 0, {}
-    for (n, prec, tol), v in zip(plan, pots):
-        s = fd.Solver(fd.Lattice(n, L, prec), fd.default_options(check_every=100, tol=tol, tol_relative=1))
-        s.set_potential(v)
-        if prev is None:
-            s.init_symmetric(seed, 0)
-        else:
-            s.upsample_from(prev)
-        steps, conv = s.evolve(2_000_000)
-        o = s.last_check()
-        upd += n**3 * steps
-        levels[f"{n}_{'bf16' if prec == fd.BF16 else 'f32'}"] = {"steps": steps, "E": o["energy"], "r2": o["r2"],
-                                                                  "converged": conv}
-        prev = s
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    return {"levels": levels, "ms": ms, "site_updates": upd, "gsite_per_s": upd / (ms * 1e-3) / 1e9}
-
-
-def backward_run(fd, dev):
-    """Gradient of E w.r.t. V through 4000 unrolled FP32 steps on 128^3
-    (V_theta = r^2/2 + 16 Gaussians, L = 10), sqrt(T) checkpointing: forward,
-    segment recompute and adjoint, all inside fdtd_backward."""
-    import numpy as np
-    import torch
-
-    import workloads as wl
-
-    n, L, T = 128, 10.0, 4000
-    g, th = wl.config_theta(n, L)
-    v = torch.from_numpy(wl.v_theta(n, L, th, g).astype(np.float32)).to(dev)
-    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=100, tol=0.0, backward_steps=T))
-    s.set_potential(v)
-    s.set_psi(torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev))
-    out = torch.empty((n, n, n), dtype=torch.float64, device=dev)
-    s.backward(T, 1.0, 0.0, out=out)  # warm-up
-    s.set_psi(torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    _, obs = s.backward(T, 1.0, 0.0, out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    dtheta = torch.tensordot(torch.from_numpy(g).to(dev), out, dims=3).cpu().numpy()
-    s.close()
-    return {"n": n, "T": T, "checkpoint_every": int(np.ceil(np.sqrt(T))), "ms": ms,
-            "forward_equivalent_gsite_per_s": 3 * n**3 * T / (ms * 1e-3) / 1e9, "E_T": obs["energy"],
-            "dE_dtheta_first4": [float(x) for x in dtheta[:4]]}
-
-
-def batched_run(fd, dev, seed):
+def batched_run(fd, dev, seed, hbm):
     """The 64-lattice batch (sizes 48..160, oscillator or soft Coulomb,
-    four symmetry sectors), FP32, one persistent launch to a part in 10^6."""
+    four symmetry sectors), FP32, one persistent launch to a part in 10^6.
+    Roofline: the launch's algorithmic stencil bytes (12 B per site per
+    pass of K steps, summed over lattices and passes) over its duration."""
     import numpy as np
     import torch
 
@@ -280,13 +374,14 @@ def batched_run(fd, dev, seed):
     s.evolve(200_000)
     start()
     s.reset_stats()
+    s.set_profiling(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     steps, conv = s.evolve(200_000)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    graph_launches = s.stats()["graph_launches"]
+    st = s.stats()
     upd = 0
     worst = 0
     for i, l in enumerate(lats):
@@ -295,11 +390,160 @@ def batched_run(fd, dev, seed):
         worst = max(worst, o["steps"])
     tuned = s.tuned_config()
     s.close()
+    kms = st["stencil_ms"] if st["stencil_ms"] > 0 else ms
+    achieved = st["stencil_bytes"] / (kms * 1e-3) / 1e9
     return {"lattices": len(lats), "sites": int(sum(l.n**3 for l in lats)), "site_updates": upd, "ms": ms,
             "gsite_per_s": upd / (ms * 1e-3) / 1e9, "max_steps_taken": worst, "all_converged": bool(conv),
-            "launches": graph_launches, "launch": "cooperative kernel in a CUDA graph",
-            "tuned": tuned}
+            "launches": st["graph_launches"], "launch": "cooperative kernel in a CUDA graph", "tuned": list(tuned),
+            "roofline": {"bound": "hbm", "kernel": f"k_batched (depth {tuned[0]}, {tuned[1]}-plane items)",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "bytes": st["stencil_bytes"], "kernel_ms": kms,
+                         "effective_frac": upd * 12.0 / (kms * 1e-3) / 1e9 / hbm,
+                         "note": "bytes: 12 B per site per K-step pass; the launch also runs every check"}}
 
+
+def backward_run(fd, dev):
+    """dL/dtheta for L = E + 0.3 <r^2> after 4000 unrolled FP32 steps on
+    128^3 (V_theta = r^2/2 + 16 Gaussians built in torch from theta, L = 10,
+    start e^{-r^2/2}), through EnergyFn: forward (evolve) and backward
+    (fdtd_backward: sqrt(T) checkpoints, segment recompute, adjoint)."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+
+    n, L, T = 128, 10.0, 4000
+    g, th = wl.config_theta(n, L)
+    G = torch.from_numpy(g).to(dev)
+    r2 = torch.from_numpy(wl.radius2(n, L)).to(dev)
+    psi0 = torch.from_numpy(np.exp(-0.5 * wl.radius2(n, L))).to(dev)
+    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=100, tol=0.0, backward_steps=T))
+    EnergyFn = fd.energy_fn()
+    res = None
+    for it in range(2):  # the first includes the autotuner's first-use timings
+        theta = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
+        v = 0.5 * r2 + torch.tensordot(theta, G, dims=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, R = EnergyFn.apply(v, s, T, psi0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        (E + 0.3 * R).backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res = {"n": n, "T": T, "checkpoint_every": int(np.ceil(np.sqrt(T))), "forward_ms": (t1 - t0) * 1e3,
+               "backward_ms": (t2 - t1) * 1e3, "E_T": float(E.detach()), "r2_T": float(R.detach()),
+               "backward_forward_equivalent_gsite_per_s": 3 * n**3 * T / (t2 - t1) / 1e9,
+               "dL_dtheta_first4": [float(x) for x in theta.grad[:4].cpu()], "path": "torch EnergyFn"}
+    s.close()
+    return res
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def _omp_threads(k):
+    """Set the OpenMP thread count of the oracle's runtime (libgomp is the
+    one the oracle's library loaded)."""
+    import ctypes
+
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(k))
+        return True
+    except OSError:
+        return False
+
+
+def cpu_sample(psi, v, a, k):
+    """Site-update rate of k FP64 oracle steps (plus one check) on the given
+    lattice: t(k steps) - t(0 steps) removes the per-call padding."""
+    import oracle
+
+    n = psi.shape[0]
+    t0 = time.perf_counter()
+    oracle.evolve(psi, v, a, a * a / 4, 0, 100, 0.0, False, 0)
+    t1 = time.perf_counter()
+    oracle.evolve(psi, v, a, a * a / 4, k, 100, 0.0, False, 0)
+    t2 = time.perf_counter()
+    return n**3 * k / max((t2 - t1) - (t1 - t0), 1e-6) / 1e9, t2 - t0
+
+
+def mean_se(vals):
+    m = statistics.mean(vals)
+    se = statistics.stdev(vals) / math.sqrt(len(vals)) if len(vals) > 1 else None
+    return m, se
+
+
+def cpu_baseline():
+    """The FP64 oracle on the host cores, on the 512^3 lattice of the
+    headline workload: all cores (3 repeats) and one thread (2 repeats), each
+    repeat k update steps with checks; mean and standard error sigma/sqrt(n)."""
+    import oracle
+    import workloads as wl
+
+    n = C3_PLAN[-1][0]
+    a = C3_LENGTH / n
+    v = wl.anisotropic_device(n, C3_LENGTH, "cpu").numpy()
+    psi = oracle.init_symmetric(n, SEED, 0)
+    cores = host_cores()
+    out = {}
+    for label, threads, reps, k in (("all_cores", cores, 3, 12), ("one_thread", 1, 2, 2)):
+        _omp_threads(threads)
+        vals, secs = [], 0.0
+        for _ in range(reps):
+            r, dt = cpu_sample(psi, v, a, k)
+            vals.append(r)
+            secs += dt
+        m, se = mean_se(vals)
+        out[label] = {"value": m, "stderr": se, "threads": threads, "repeats": reps, "steps_per_repeat": k,
+                      "seconds": secs}
+    _omp_threads(cores)
+    return {"value": out["all_cores"]["value"], "unit": METRIC, "cores": cores, "kind": "oracle",
+            "stderr": out["all_cores"]["stderr"], "one_thread": out["one_thread"],
+            "sample": (f"FP64 update steps with checks on the 512^3 anisotropic lattice: {cores} threads "
+                       f"(3 x 12 steps) and 1 thread (2 x 2 steps); cores from the affinity mask")}
+
+
+def workload_config(ws: int) -> dict:
+    """The workload both arms report (the reference arm times a bounded
+    sample of it, described in its cpu_baseline)."""
+    return {"workload": "anisotropic_osc+32gauss_L16_multires_128bf16-256bf16-512f32",
+            "levels": [list(p) for p in C3_PLAN], "length": C3_LENGTH, "check_every": 100,
+            "l2": "inputs larger than L2 (0.5 GB fields at 512^3) and a 512 MiB write between timed steps",
+            "parallelism": f"replicas{ws}"}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as wl
+
+    n = C3_PLAN[-1][0]
+    a = C3_LENGTH / n
+    v = wl.anisotropic_device(n, C3_LENGTH, "cpu").numpy()
+    psi = oracle.init_symmetric(n, SEED, 0)
+    cores = host_cores()
+    _omp_threads(cores)
+    for _ in range(args.warmup):
+        cpu_sample(psi, v, a, 1)
+    vals, secs = [], 0.0
+    for _ in range(max(1, args.steps)):
+        r, dt = cpu_sample(psi, v, a, 4)
+        vals.append(r)
+        secs += dt
+    value, se = mean_se(vals)
+    cb = {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "stderr": se,
+          "sample": f"{args.steps} x 4 FP64 update steps with checks on the 512^3 anisotropic lattice ({secs:.1f} s)"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(ws),
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- shared helpers and cases
 
 class Clocks:
     """nvidia-smi sampling during the timed region."""
@@ -337,64 +581,6 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def cpu_baseline(target_s: float = 12.0):
-    """The FP64 oracle on the host cores: update steps with checks on the
-    256^3 Coulomb lattice (a bounded sample of the workload)."""
-    import numpy as np
-
-    import oracle
-    import workloads as wl
-
-    n = LEVELS[-1]
-    a = LENGTH / n
-    v = wl.coulomb_soft(n, LENGTH)
-    psi = oracle.init_symmetric(n, SEED, SECTORS[0][1])
-    # per-step cost from two short runs (each call also pads/unpads the field)
-    t0 = time.perf_counter()
-    psi, _, _ = oracle.evolve(psi, v, a, a * a / 4, 2, 100, 0.0, False, SECTORS[0][1])
-    t1 = time.perf_counter()
-    psi, _, _ = oracle.evolve(psi, v, a, a * a / 4, 6, 100, 0.0, False, SECTORS[0][1])
-    t2 = time.perf_counter()
-    per = max((t2 - t1) - (t1 - t0), 1e-3) / 4
-    steps = max(4, min(2000, int(target_s / per)))
-    t0 = time.perf_counter()
-    oracle.evolve(psi, v, a, a * a / 4, steps, 100, 0.0, False, SECTORS[0][1])
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n**3 * steps / dt / 1e9, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} FP64 update steps with checks on the 256^3 Coulomb lattice ({dt:.1f} s)"}
-
-
-def workload_config(ws: int) -> dict:
-    """The workload both arms report (the reference arm times a bounded
-    sample of it, described in its cpu_baseline)."""
-    return {"workload": "coulomb_soft_L40_multires_64-128-256_1s+2px", "levels": list(LEVELS), "length": LENGTH,
-            "tol_rel": TOL, "check_every": 100, "l2": "flushed (512 MiB write) between timed steps",
-            "parallelism": f"replicas{ws}"}
-
-
-def reference_arm(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; each step is independent
-    vals = []
-    cb = None
-    for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(target_s=max(3.0, 60.0 / max(1, args.steps)))
-        vals.append(cb["value"])
-    value = statistics.mean(vals)
-    cb["value"] = value
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(ws),
-            "cpu_baseline": cb, "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
 
 
 def reduce_over_ranks(times, counts, device, world_size):
@@ -470,24 +656,23 @@ def stencil_case(args):
     ms = st["stencil_ms"] / max(1, st["stencil_timed_launches"])
     upd = st["stencil_site_updates"] / (st["stencil_ms"] * 1e-3) / 1e9
     gbs = st["stencil_bytes"] / (st["stencil_ms"] * 1e-3) / 1e9
-    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    peak = peaks().get("hbm_gbs", 6800.0)
     print(json.dumps({"case": "stencil", "n": n, "precision": args.precision, "depth": args.depth,
-                      "tuned": s.tuned_config(),
+                      "tuned": s.tuned_config(), "kernel": s.tuned_kernel(), "digest": stencil_digest(),
                       "launches": st["stencil_launches"], "ms_per_launch": ms, "gsite_per_s": upd,
                       "achieved_gbs": gbs, "hbm_frac": gbs / peak, "effective_frac_12B": upd * 12 / peak}))
 
 
+# --------------------------------------------------------------------------- main
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
-                    help="0: every evolve through the stream (for launch lists under ncu)")
     ap.add_argument("--case", default="solve", choices=["solve", "stencil", "backward"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=40)
@@ -512,14 +697,13 @@ def main():
     dev = torch.device("cuda", local)
     import paper_0904_0939_gb300 as fd
 
-    opts = fd.default_options(check_every=100, tol=TOL, tol_relative=1, graphs=args.graphs)
     seed = SEED + rank
-    pots_dev = potentials(True, dev)
-    pots_host = potentials(False, dev)
+    pots_dev = c3_potentials(True, dev)
+    pots_host = c3_potentials(False, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     for _ in range(max(3, args.warmup)):
-        run_step(fd, pots_dev, seed, opts)
+        c3_step(fd, pots_dev, seed)
     torch.cuda.synchronize()
 
     def barrier():
@@ -529,7 +713,7 @@ def main():
 
     clocks = Clocks(local)
     tot_ms, tot_upd, tot_launch = 0.0, 0, 0
-    fine_ms, fine_bytes, fine_upd, fine_launches, fine_timed = 0.0, 0.0, 0, 0, 0
+    fine = {"ms": 0.0, "bytes": 0.0, "upd": 0, "launches": 0, "timed": 0}
     tot = None
     barrier()
     for _ in range(args.steps):
@@ -537,17 +721,15 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        tot = run_step(fd, pots_dev, seed, opts)
+        tot = c3_step(fd, pots_dev, seed)
         e1.record()
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
         tot_upd += tot["updates"]
         tot_launch += tot["launches"]
-        fine_ms += tot["fine_ms"]
-        fine_bytes += tot["fine_bytes"]
-        fine_upd += tot["fine_updates"]
-        fine_launches += tot["fine_launches"]
-        fine_timed += tot["fine_timed"]
+        for k, src in (("ms", "fine_ms"), ("bytes", "fine_bytes"), ("upd", "fine_updates"),
+                       ("launches", "fine_launches"), ("timed", "fine_timed")):
+            fine[k] += tot[src]
     barrier()
     clk = clocks.stop()
 
@@ -558,56 +740,60 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_upd += run_step(fd, pots_host, seed, opts)["updates"]
+        e2e_upd += c3_step(fd, pots_host, seed)["updates"]
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
 
     (ms_max, e2e_max), (upd_all, e2e_upd_all) = reduce_over_ranks([tot_ms, e2e_ms],
                                                                   [float(tot_upd), float(e2e_upd)], dev, ws)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
     extra = {}
     if not args.no_extras:
-        extra["time_to_E0"] = time_to_e0(fd, pots_dev, seed, opts, dev)
-        extra["batched_64_lattices"] = batched_run(fd, dev, seed)
-        extra["anisotropic_512_multires_bf16_coarse"] = anisotropic_multires(fd, dev, seed)
-        extra["backward_128_T4000"] = backward_run(fd, dev)
+        last = c3_step(fd, pots_dev, seed, keep_last=True)
+        extra["c3_fp64"] = c3_fp64_reference(fd, last["last"], dev)
+        last["last"].close()
+        del pots_host
+        extra["coulomb_256_multires"] = c2_run(fd, dev, seed, flush)
+        extra["time_to_E0_coulomb_256"] = time_to_e0(fd, seed, dev)
+        extra["batched_64_lattices"] = batched_run(fd, dev, seed, hbm)
+        extra["theta_gradient_128_T4000"] = backward_run(fd, dev)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
     value = upd_all / (ms_max * 1e-3) / 1e9
     e2e_value = e2e_upd_all / (e2e_max * 1e-3) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_note = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
     # the dominant kernel's average launch: duration over the launches timed
     # with CUDA events, algorithmic bytes and site updates over all of them
-    ms_launch = fine_ms / fine_timed if fine_timed else None
-    bytes_launch = fine_bytes / max(1, fine_launches)
+    ms_launch = fine["ms"] / fine["timed"] if fine["timed"] else None
+    bytes_launch = fine["bytes"] / max(1, fine["launches"])
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9 if ms_launch else None
-    eff = fine_upd / max(1, fine_launches) * 12.0 / (ms_launch * 1e-3) / 1e9 / hbm if ms_launch else None
+    eff = fine["upd"] / max(1, fine["launches"]) * 12.0 / (ms_launch * 1e-3) / 1e9 / hbm if ms_launch else None
     depth, zc, tx, ty = tot["config"] if tot and tot["config"] else (None, None, None, None)
-    h2d = sum(n**3 * 4 for n in LEVELS) * len(SECTORS)
+    n_fine = C3_PLAN[-1][0]
+    digest = stencil_digest()
+    traffic = TRAFFIC.get((digest, n_fine, depth, zc, tx, ty))
+    h2d = sum(n**3 * 4 for n, _, _ in C3_PLAN)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": workload_config(ws),
-        "path": {"evolve": "cuda graph per lattice (device-side loop), the two sectors concurrently" if args.graphs
-                 else "stream", "precision": "fp32 stencil, fp64 sums"},
+        "path": {"evolve": "cuda graph per lattice (device-side loop)",
+                 "precision": "bf16 storage + fp32 arithmetic on 128^3/256^3, fp32 at 512^3, fp64 sums"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": TRAFFIC_256.get((depth, zc, tx, ty)),
-                     "kernel": (f"k_step_tma (256^3 level, depth {depth}, "
-                                f"{'balanced one-wave partition' if zc < 0 else f'span {zc}'}, tile {tx}x{ty})" if zc
-                                else "k_step_f32 (256^3 level, one-step z-marching)"),
-                     "launches": fine_launches, "timed_launches": fine_timed, "ms_per_launch": ms_launch,
-                     "bytes_per_launch": bytes_launch, "peak_kind": peak_note,
-                     "effective_frac": eff},
-        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 6 * 96},
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "traffic_key": {"digest": digest, "n": n_fine, "depth": depth, "span": zc, "tile": [tx, ty]},
+                     "traffic_note": None if traffic else "no ncu capture of this kernel source and configuration",
+                     "kernel": (f"k_step_tma (512^3 level, depth {depth}, "
+                                f"{'balanced one-wave partition' if zc < 0 else f'span {zc}'}, tile {tx}x{ty})"
+                                if zc else f"one-step kernel (512^3 level, depth {depth})"),
+                     "launches": fine["launches"], "timed_launches": fine["timed"], "ms_per_launch": ms_launch,
+                     "bytes_per_launch": bytes_launch, "peak_kind": peak_note, "effective_frac": eff},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 3 * 96},
         "gpu_launches": tot_launch,
         "clocks": clk,
         "results": tot["results"] if tot else None,

@@ -49,7 +49,7 @@ def torch_grad(fd, prec, n, L, T, ce, g, th, psi0, mask, seed, w_e, w_r, vdtype=
     E, R = fd.energy_fn().apply(v, s, T, None if psi0 is None else torch.from_numpy(psi0).to(dev), seed, mask)
     loss = w_e * E + w_r * R
     loss.backward()
-    out = theta.grad.detach().double().cpu().numpy(), float(E), float(R)
+    out = theta.grad.detach().double().cpu().numpy(), float(E.detach()), float(R.detach())
     s.close()
     return out
 
