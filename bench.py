@@ -60,6 +60,7 @@ C2_SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 STENCIL_SOURCES = ("paper_0904_0939_gb300/csrc/tma_item.cuh", "paper_0904_0939_gb300/csrc/k_tblock.cu",
                    "paper_0904_0939_gb300/csrc/common.cuh")
 TRAFFIC = {}
+PARTITIONS = {-1: "balanced one-wave partition", -2: "columns-first partition"}
 
 
 def stencil_digest() -> str:
@@ -794,7 +795,7 @@ def main():
                      "traffic_key": {"digest": digest, "n": n_fine, "depth": depth, "span": zc, "tile": [tx, ty]},
                      "traffic_note": None if traffic else "no ncu capture of this kernel source and configuration",
                      "kernel": (f"k_step_tma (512^3 level, depth {depth}, "
-                                f"{'balanced one-wave partition' if zc < 0 else f'span {zc}'}, tile {tx}x{ty})"
+                                f"{PARTITIONS.get(zc, f'span {zc}')}, tile {tx}x{ty})"
                                 if zc else f"one-step kernel (512^3 level, depth {depth})"),
                      "launches": fine["launches"], "timed_launches": fine["timed"], "ms_per_launch": ms_launch,
                      "bytes_per_launch": bytes_launch, "peak_kind": peak_note, "effective_frac": eff},

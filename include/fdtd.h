@@ -121,7 +121,10 @@ typedef struct {
                              one runs on into the next column); 0 = one equal span per
                              resident block; -1 = one wave with each block's planes cut so
                              that blocks whose range starts a second column (its warm-up
-                             and drain steps counted) get fewer */
+                             and drain steps counted) get fewer; -2 = columns first: one
+                             block per tile column from plane 0, the other resident blocks
+                             share the column tops (falls back to -1 when there are no
+                             more resident blocks than columns) */
   int32_t wait_limit_us;  /* bound on every device-side wait: 0 = default (0.2 s per pipeline
                              wait, 2 s per grid barrier), > 0 = microseconds, < 0 = none (a wait
                              that is not already complete expires at once; for testing the
@@ -263,7 +266,8 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
 
 /* Stencil configuration in use for lattice `lat` (after autotuning, if on):
  * temporal depth (steps per launch) and the span (tile planes per block,
- * options.zchunk; -1 = the balanced one-wave partition) of the TMA kernel;
+ * options.zchunk; -1 = the balanced one-wave partition, -2 = columns first) of
+ * the TMA kernel;
  * zchunk = 0 (depth 1) when the one-step
  * z-marching kernel is in use.  For a batched handle after an evolve: the
  * depth and z-planes per item of its persistent launch. */

@@ -115,6 +115,7 @@ void choose_config(fdtd_context* c, Lat& L) {
       const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx);
       for (int m = 1; m <= 3; ++m) spans.push_back((int)std::max(1LL, (total + m * slots - 1) / (m * slots)));
       spans.push_back(-1);  // the balanced one-wave partition
+      spans.push_back(-2);  // columns first (neighbouring tiles in step)
       std::sort(spans.begin(), spans.end());
       spans.erase(std::unique(spans.begin(), spans.end()), spans.end());
       for (int zc : spans) {

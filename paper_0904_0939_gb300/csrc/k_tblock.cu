@@ -30,6 +30,13 @@ namespace tb {
 // tile plane  c n + clamp(u - c (n + wcost) - wcost, 0, n),  c = u / (n + wcost):
 // monotone, from 0 to ntiles * n, so the blocks' ranges cover every tile
 // plane once.
+//
+// span == -2 selects the columns-first partition (for grids with more
+// blocks than tile columns): block b < C (C = ntiles) takes planes
+// [0, zsplit) of column b, and the other blocks cut the column tops
+// [zsplit, n), laid end to end, into equal parts.  The first C blocks move
+// through z in step, so a tile's y-neighbours are read at about the same z
+// and the halo rows of its box come from L2 instead of HBM.
 __device__ __forceinline__ long long balanced_plane(long long u, int n, int wcost) {
   const long long unit = n + wcost, c = u / unit;
   long long o = u - c * unit - wcost;
@@ -41,7 +48,7 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
                                                                     const __grid_constant__ CUtensorMap map_v,
                                                                     float* __restrict__ out, int n, int ntx,
                                                                     long long total, int span, int wcost,
-                                                                    float half_dtau,
+                                                                    int zsplit, float half_dtau,
                                                                     float one_m6c, float cc,
                                                                     const int32_t* __restrict__ active,
                                                                     int32_t* __restrict__ err) {
@@ -51,22 +58,39 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   if (*(volatile const int32_t*)err != 0) return;  // an earlier wait expired: do nothing
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = aligned_smem(smem_raw);
-  long long g, gend;
-  if (span > 0) {
-    g = (long long)blockIdx.x * span;
-    gend = min(g + span, total);
+  // the block's items: the range [r, rend) of a sequence of columns of
+  // `top` planes each, starting at plane `base` of every column
+  long long r, rend;
+  int top = n, base = 0;
+  if (span == -2) {
+    const int C = (int)(total / n);
+    if ((int)blockIdx.x < C) {
+      top = zsplit;
+      r = (long long)blockIdx.x * top;
+      rend = r + top;
+    } else {
+      const int rb = gridDim.x - C;
+      top = n - zsplit;
+      base = zsplit;
+      const long long rest = (long long)C * top;
+      r = rest * (blockIdx.x - C) / rb;
+      rend = rest * (blockIdx.x - C + 1) / rb;
+    }
+  } else if (span > 0) {
+    r = (long long)blockIdx.x * span;
+    rend = min(r + span, total);
   } else {
     const long long ctot = (total / n) * (n + wcost);
-    g = balanced_plane(ctot * blockIdx.x / gridDim.x, n, wcost);
-    gend = balanced_plane(ctot * (blockIdx.x + 1) / gridDim.x, n, wcost);
+    r = balanced_plane(ctot * blockIdx.x / gridDim.x, n, wcost);
+    rend = balanced_plane(ctot * (blockIdx.x + 1) / gridDim.x, n, wcost);
   }
-  while (g < gend) {
-    const int t = (int)(g / n), z0 = (int)(g - (long long)t * n);
-    const int z1 = (int)min((long long)n, z0 + (gend - g));
-    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, z0, z1, half_dtau,
-                               one_m6c, cc, err))
+  while (r < rend) {
+    const int t = (int)(r / top), z0 = (int)(r - (long long)t * top);
+    const int z1 = (int)min((long long)top, z0 + (rend - r));
+    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, base + z0,
+                               base + z1, half_dtau, one_m6c, cc, err))
       return;
-    g += z1 - z0;
+    r += z1 - z0;
   }
 }
 
@@ -112,7 +136,8 @@ long long tile_planes(int n) {
 template <int K, int TXT>
 int resident_blocks();
 
-// span > 0: equal spans; span <= 0: the balanced partition over one wave
+// span > 0: equal spans; span == -2: columns first; other span <= 0: the balanced
+// partition over one wave
 template <int K, int TXT>
 void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int span,
               const int32_t* active, int32_t* err, cudaStream_t st) {
@@ -121,9 +146,18 @@ void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const 
   const long long total = tile_planes<K, TXT>(p.n);
   const unsigned blocks = span > 0 ? (unsigned)((total + span - 1) / span)
                                    : (unsigned)std::min<long long>(resident_blocks<K, TXT>(), total);
+  const int w = 2 * (K - 1);
+  int zsplit = 0;
+  if (span == -2) {
+    // columns first needs more blocks than columns; zsplit = C (n + w) / blocks
+    // gives both groups the same planes plus warm-up steps
+    const long long C = total / p.n;
+    zsplit = (int)std::min<long long>(p.n, C * (p.n + w) / std::max(1u, blocks));
+    if ((long long)blocks <= C || zsplit < 1 || zsplit >= p.n) span = -1;
+  }
   launch_pdl(k_step_tma<K, TXT>, dim3(blocks), dim3(G::THREADS), G::SMEM, st, mpsi, mv, out, p.n,
-             (p.n + TXT - 1) / TXT, total, span > 0 ? span : 0, 2 * (K - 1), p.half_dtau_f, p.one_m6c_f, p.c_f,
-             active, err);
+             (p.n + TXT - 1) / TXT, total, span > 0 ? span : (span == -2 ? -2 : 0), w, zsplit, p.half_dtau_f,
+             p.one_m6c_f, p.c_f, active, err);
 }
 
 // Blocks of k_step_tma<K, TXT> resident on the whole device at once
@@ -174,7 +208,7 @@ int tma_zchunk(int n, int depth, int tx) {
 
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                      int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st) {
-  if (zc == 0) zc = tma_zchunk(p.n, depth, tx);  // zc < 0: the balanced partition
+  if (zc == 0) zc = tma_zchunk(p.n, depth, tx);  // zc -2: columns first, other zc < 0: balanced
   if (tx == 64) {
     if (depth == 1)
       tb::launch_k<1, 64>(map_psi_in, map_v, out, p, zc, active, err, st);

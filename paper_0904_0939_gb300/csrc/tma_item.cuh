@@ -38,9 +38,15 @@ namespace tb {
 
 constexpr int TY = 16;   // interior tile height
 constexpr int HX = 4;    // x margin of the box: >= K and a multiple of 4 (TMA x * 4 B % 16 == 0)
-constexpr int D = 2;     // planes prefetched beyond the newest one in use
+constexpr int RING = 6;  // ring slots: a multiple of 2 and 3, so a six-step group sees every slot at a fixed place
 constexpr unsigned long long kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per wait
 
+// Shared-memory layout of a tile item with K update levels.  The ring
+// holds psi and V of RING planes: the three planes level 1 reads, the V of
+// the K - 1 older planes the deeper levels need, and D planes prefetched.
+// Level 1's planes are triple-buffered (a thread writes the next one before
+// the other threads have finished reading the previous step's), the planes
+// of levels 2..K-1 double-buffered (written after the step's wait).
 template <int K, int TXT>
 struct Geo {
   static constexpr int TX = TXT;
@@ -50,15 +56,19 @@ struct Geo {
   static constexpr int BH = TY + 2 * K;
   static constexpr int USED = C4 * BH;                       // threads that own a box column
   static constexpr int THREADS = (USED + 31) / 32 * 32;      // whole warps
-  static constexpr int R = D + 2 + (K > 1 ? K - 1 : 1);      // ring slots
+  static constexpr int R = RING;                             // ring slots
+  static constexpr int D = R - 2 - (K > 1 ? K - 1 : 1);      // planes prefetched beyond the newest in use
+  static_assert(D >= 1, "the ring must prefetch at least one plane");
   static constexpr int PLANE = ((BW * BH * 4 + 127) / 128) * 128 / 4;  // floats per box, 128 B multiple
   static constexpr int LPLANE = LW * BH;
+  static constexpr int NLEV = K > 1 ? 3 + 2 * (K - 2) : 0;  // level planes
   static constexpr size_t RING_OFF = 128;                    // guard before the ring
   static constexpr size_t SLOT_BYTES = 2 * (size_t)PLANE * 4;
   static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;     // bytes the two box loads deliver
   static constexpr size_t LEVEL_OFF = RING_OFF + R * SLOT_BYTES + 128;
-  static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)(K > 1 ? K - 1 : 0) * 2 * LPLANE * 4;
-  static constexpr size_t FLAG_OFF = BAR_OFF + 8 * R;        // "a wait expired" word of the item
+  static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)NLEV * LPLANE * 4;
+  static constexpr size_t CBAR_OFF = BAR_OFF + 8 * R;        // the step barrier of the block
+  static constexpr size_t FLAG_OFF = CBAR_OFF + 8;           // "a wait expired" word of the item
   static constexpr size_t RED_OFF = FLAG_OFF + 8;            // block reduction scratch (sums)
   static constexpr size_t SMEM = RED_OFF + 8 * 4 * (THREADS / 32) + 128;  // + base alignment slack
 };
@@ -220,12 +230,15 @@ __device__ __forceinline__ float4 update4(float4 c, float xl, float xr, float4 y
   return make_float4(o0.x, o0.y, o1.x, o1.y);
 }
 
-// The ring pipeline: barriers, prologue, and the bounded waits; the body
-// callable sees plane j's slot and the level planes.
+// The ring pipeline: barriers, prologue, and the bounded waits.  Step items
+// also use the block's step barrier (an mbarrier counting every thread):
+// a thread arrives after its last level-plane store of a z-step and waits
+// for that phase in the middle of the next z-step.
 template <int K, int TXT>
 struct Pipe {
   using G = Geo<K, TXT>;
   static constexpr int R = G::R;
+  static constexpr int D = G::D;
   char* smem;
   const CUtensorMap* mpsi;
   const CUtensorMap* mv;
@@ -233,7 +246,8 @@ struct Pipe {
   const int32_t* err;
   long long budget = 0;  // wall-clock wait budget in ns (< 0: do not wait)
   uint64_t* bars;
-  int* flag;  // shared: set by any thread whose wait expired, read by all after the barrier
+  uint64_t* cbar;
+  int* flag;  // shared: set by any thread whose wait expired, read by all after a barrier
   float* ring;
   unsigned phase = 0;        // bit s: parity of the next wait on slot s (toggled on success)
   unsigned outstanding = 0;  // (thread 0) slots with a copy in flight
@@ -255,15 +269,18 @@ struct Pipe {
       timeout = 1;
     }
   }
-  // Set up barriers and issue planes j0-1 .. min(j0+D, jlast) into slots 0, 1, ...
-  __device__ __forceinline__ void begin(int j0, int jlast) {
+  // Set up barriers and issue planes j0-1 .. min(j0+D, jlast) into slots 0, 1, ...;
+  // with `step`, also the step barrier and its first phase (the item start).
+  __device__ __forceinline__ void begin(int j0, int jlast, bool step = false) {
     bars = (uint64_t*)(smem + G::BAR_OFF);
+    cbar = (uint64_t*)(smem + G::CBAR_OFF);
     flag = (int*)(smem + G::FLAG_OFF);
     ring = (float*)(smem + G::RING_OFF);
     budget = wait_budget_ns(err);
     if (threadIdx.x == 0) {
       *(volatile int*)flag = 0;
       for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
+      if (step) mbar_init(cbar, G::THREADS);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -274,25 +291,38 @@ struct Pipe {
     }
     wait(0);
     wait(1);
+    if (step) cta_arrive();
   }
-  // Start of iteration j (slot sj): prefetch plane j+1+D, wait for plane j+1.
-  __device__ __forceinline__ void advance(int j, int sj, int jlast) {
-    if (threadIdx.x == 0 && !timeout && j + 1 + D <= jlast) {  // no new copy after an expired wait
+  // Issue plane j + 1 + D into the slot of plane j + 1 + D - R (thread 0;
+  // no new copy after an expired wait).
+  __device__ __forceinline__ void refill(int j, int sj, int jlast) {
+    if (threadIdx.x == 0 && !timeout && j + 1 + D <= jlast) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(j + 1 + D, slot_add<R>(sj, 1 + D));
     }
+  }
+  // Start of iteration j (slot sj): prefetch plane j+1+D, wait for plane j+1.
+  __device__ __forceinline__ void advance(int j, int sj, int jlast) {
+    refill(j, sj, jlast);
     wait(slot_add<R>(sj, 1));
   }
-  // End of a z-step: a thread whose wait expired marks the shared flag and
-  // the barrier publishes it.
+  // End of a z-step of a sums item: a thread whose wait expired marks the
+  // shared flag and the barrier publishes it.
   __device__ __forceinline__ void end_step() {
     if (timeout) *(volatile int*)flag = 1;
     __syncthreads();
   }
+  // The step barrier: arrive (after marking the flag if a wait expired) and
+  // wait for a phase, bounded like every wait.
+  __device__ __forceinline__ void cta_arrive() {
+    if (timeout) *(volatile int*)flag = 1;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(cbar)) : "memory");
+  }
+  __device__ __forceinline__ void cta_wait(unsigned parity) {
+    if (!mbar_wait_bounded(cbar, parity, err, budget)) timeout = 1;
+  }
   // After a barrier: every thread reads the same flag; on a timeout drain
-  // and report.  Step items read it once per three z-steps (the steps run
-  // in between on whatever the ring holds, in bounds, and the item's output
-  // is discarded), which keeps the unrolled loop free of exits.
+  // and report.
   __device__ __forceinline__ bool ok(int32_t* err_w) {
     if (*(volatile const int*)flag) {
       if (threadIdx.x == 0) {
@@ -311,24 +341,37 @@ struct Pipe {
   __device__ __forceinline__ const float* box(int s) const { return ring + s * (G::SLOT_BYTES / 4); }
 };
 
-// Per-thread constants of a step item.
+// Per-thread constants of a step item: the shared-memory bases every access
+// adds a compile-time offset to, the output column, and which levels this
+// thread's column computes.
 template <int K, int TXT>
 struct StepCtx {
   using G = Geo<K, TXT>;
-  float* lev;
-  float* out_col;
-  int n, z0, z1, ro, lo;
-  bool owner, inside, interior_col, interior_row, fix_l, fix_r;
-  int row;
+  const float* rb;   // ring + this thread's offset in a box
+  float* lb;         // level planes + this thread's offset in a level plane
+  float* outp;       // output column at the plane level K writes this z-step
+  size_t plane;      // n * n
+  int n, z0, z1;
+  bool owner, fix_l, fix_r, interior_row;
+  bool need[K + 1];  // level l computes this column (without the z tests)
   float hd, om6c, cc;
-  Chk sm, gl;  // shared memory of the item, the output field
+  Chk sm, gl;        // shared memory of the item, the output field
 };
 
-// One z-step of a step item.  ROT (compile time, 0..2) names which of the
-// three window registers of each level holds the oldest plane, so the
-// windows rotate by renaming instead of moving.  After level l computes
-// its new plane into w[l][ROT], the window reads zm = w[(ROT+1)%3],
-// c = w[(ROT+2)%3], zp = w[ROT].
+// One z-step of a step item.  U = (j - j0) mod 6 makes every ring slot, the
+// register-window rotation and the level-plane buffers compile-time
+// constants: plane q sits in ring slot (q - j0 + 1) mod 6; level 1's plane p
+// in buffer (p - j0) mod 3; level l's (1 < l < K) in buffer (p - j0) mod 2;
+// the three window registers of each level rotate by renaming (after level l
+// computes its new plane into w[l][U mod 3] the window reads zm = w[(U+1)%3],
+// c = w[(U+2)%3], zp = w[U%3]).
+//
+// Level 1 needs only ring data, so it runs before the step barrier (the
+// wait for every thread's stores of the previous z-step); the ring refill,
+// which overwrites a plane last read in the previous z-step, and levels
+// 2..K follow it; the thread arrives after its last store.  STEADY: every
+// level's plane lies inside the lattice and level K's inside [z0, z1), so
+// no z tests are needed.
 //
 // Sites outside the lattice must read as zero at every level.  The level
 // planes and windows start each item at zero, so a site is simply never
@@ -336,72 +379,117 @@ struct StepCtx {
 // compute) or below it in z (p < 0 comes first in an item); above it
 // (p >= n, block-uniform) zeros are written.  The last level computes only
 // the planes it stores.
-template <int K, int TXT, int ROT>
-__device__ __forceinline__ void step_iteration(const StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int j, int sj,
+template <int K, int TXT, int U, bool STEADY>
+__device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int j, int jlast,
                                                float4 (&w)[K > 1 ? K - 1 : 1][3]) {
   using G = Geo<K, TXT>;
   constexpr int R = G::R;
+  static_assert(R == 6, "the step assumes a six-slot ring");
+  constexpr int SJ = (U + 1) % R;  // slot of plane j
+  constexpr int I0 = U % 3, I1 = (U + 1) % 3, I2 = (U + 2) % 3;
+  constexpr int SL = G::SLOT_BYTES / 4;
   constexpr int BW = G::BW, LW = G::LW;
-  constexpr int I0 = ROT, I1 = (ROT + 1) % 3, I2 = (ROT + 2) % 3;  // newest, oldest, middle after update
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  pp.wait((SJ + 1) % R);  // plane j + 1
   // ---- level 1: plane j from the ring
   {
-    const float* b0 = pp.box(sj);
-    const float* bm = pp.box(slot_add<R>(sj, -1));
-    const float* bp = pp.box(slot_add<R>(sj, 1));
     const int p = j;
-    const bool need = x.inside && (x.row >= 1 && x.row < G::BH - 1) && (K > 1 || x.interior_col);
-    float4 c = x.owner ? x.sm.ld4(b0 + x.ro) : zero4;
+    constexpr int S0 = SJ, SM = (SJ + R - 1) % R, SP = (SJ + 1) % R;
+    const float* b0 = x.rb + S0 * SL;
+    float4 c = x.owner ? x.sm.ld4(b0) : zero4;
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (x.fix_l) xl = x.sm.ld1(b0 + x.ro - 1);
-    if (x.fix_r) xr = x.sm.ld1(b0 + x.ro + 4);
+    // lanes 0 and 31 read their outer neighbour from shared memory (at a row
+    // end the neighbouring row's value is taken, which only reaches margins)
+    if (x.fix_l) xl = x.sm.ld1(b0 - 1);
+    if (x.fix_r) xr = x.sm.ld1(b0 + 4);
     auto upd = [&]() {
-      return update4(c, xl, xr, x.sm.ld4(b0 + x.ro - BW), x.sm.ld4(b0 + x.ro + BW), x.sm.ld4(bm + x.ro),
-                     x.sm.ld4(bp + x.ro), x.sm.ld4(b0 + G::PLANE + x.ro), x.hd, x.om6c, x.cc);
+      return update4(c, xl, xr, x.sm.ld4(b0 - BW), x.sm.ld4(b0 + BW), x.sm.ld4(x.rb + SM * SL),
+                     x.sm.ld4(x.rb + SP * SL), x.sm.ld4(b0 + G::PLANE), x.hd, x.om6c, x.cc);
     };
     if constexpr (K == 1) {
-      if (need && x.interior_row && p >= x.z0 && p < x.z1) x.gl.st4(x.out_col + (size_t)p * x.n * x.n, upd());
-    } else if (p >= x.n) {
-      if (need) {
-        x.sm.st4(x.lev + (p & 1) * G::LPLANE + x.lo, zero4);
-        w[0][I0] = zero4;
+      if (x.need[1] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.outp, upd());
+    } else {
+      float* dst = x.lb + (U % 3) * G::LPLANE;
+      if constexpr (STEADY) {
+        if (x.need[1]) {
+          const float4 r = upd();
+          x.sm.st4(dst, r);
+          w[0][I0] = r;
+        }
+      } else if (p >= x.n) {
+        if (x.need[1]) {
+          x.sm.st4(dst, zero4);
+          w[0][I0] = zero4;
+        }
+      } else if (p >= 0 && x.need[1]) {
+        const float4 r = upd();
+        x.sm.st4(dst, r);
+        w[0][I0] = r;
       }
-    } else if (p >= 0 && need) {
-      const float4 r = upd();
-      x.sm.st4(x.lev + (p & 1) * G::LPLANE + x.lo, r);
-      w[0][I0] = r;
     }
   }
+  pp.cta_wait(U & 1);  // every thread's stores of z-step j - 1
+  pp.refill(j, SJ, jlast);
   // ---- levels 2..K: plane j - l + 1 from level l-1
 #pragma unroll
   for (int l = 2; l <= K; ++l) {
     const int p = j - l + 1;
-    const bool need = x.inside && (x.row >= l && x.row < G::BH - l) && (l < K || x.interior_col);
-    const float* lp = x.lev + ((l - 2) * 2 + (p & 1)) * G::LPLANE;  // level l-1, plane p
+    const float* lp = l == 2 ? x.lb + ((U + 5) % 3) * G::LPLANE                         // level 1, plane j - 1
+                             : x.lb + (3 + 2 * (l - 3) + ((U - l + 7) & 1)) * G::LPLANE;  // level l-1, plane p
     const float4 c = w[l - 2][I2];
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (x.fix_l) xl = x.sm.ld1(lp + x.lo - 1);
-    if (x.fix_r) xr = x.sm.ld1(lp + x.lo + 4);
+    if (x.fix_l) xl = x.sm.ld1(lp - 1);
+    if (x.fix_r) xr = x.sm.ld1(lp + 4);
     auto upd = [&]() {
-      const float4 v = x.sm.ld4(pp.box(slot_add<R>(sj, 1 - l)) + G::PLANE + x.ro);
-      return update4(c, xl, xr, x.sm.ld4(lp + x.lo - LW), x.sm.ld4(lp + x.lo + LW), w[l - 2][I1], w[l - 2][I0], v,
-                     x.hd, x.om6c, x.cc);
+      return update4(c, xl, xr, x.sm.ld4(lp - LW), x.sm.ld4(lp + LW), w[l - 2][I1], w[l - 2][I0],
+                     x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + G::PLANE), x.hd, x.om6c, x.cc);
     };
     if (l == K) {
-      if (need && x.interior_row && p >= x.z0 && p < x.z1) x.gl.st4(x.out_col + (size_t)p * x.n * x.n, upd());
-    } else if (p >= x.n) {
-      if (need) {
-        x.sm.st4(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo, zero4);
-        w[l - 1][I0] = zero4;
+      if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.outp, upd());
+    } else {
+      float* dst = x.lb + (3 + 2 * (l - 2) + ((U - l + 7) & 1)) * G::LPLANE;
+      if constexpr (STEADY) {
+        if (x.need[l]) {
+          const float4 r = upd();
+          x.sm.st4(dst, r);
+          w[l - 1][I0] = r;
+        }
+      } else if (p >= x.n) {
+        if (x.need[l]) {
+          x.sm.st4(dst, zero4);
+          w[l - 1][I0] = zero4;
+        }
+      } else if (p >= 0 && x.need[l]) {
+        const float4 r = upd();
+        x.sm.st4(dst, r);
+        w[l - 1][I0] = r;
       }
-    } else if (p >= 0 && need) {
-      const float4 r = upd();
-      x.sm.st4(x.lev + ((l - 1) * 2 + (p & 1)) * G::LPLANE + x.lo, r);
-      w[l - 1][I0] = r;
     }
   }
+  pp.cta_arrive();
+  x.outp += x.plane;
+}
+
+// Six z-steps from j (j - j0 a multiple of 6); a partial group stops after
+// step j1.
+template <int K, int TXT, bool STEADY>
+__device__ __forceinline__ void step_group(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int& j, int j1,
+                                           float4 (&w)[K > 1 ? K - 1 : 1][3]) {
+  const int jl = j1 + 1;
+  step_iteration<K, TXT, 0, STEADY>(x, pp, j, jl, w);
+  if (!STEADY && j + 1 > j1) { j += 1; return; }
+  step_iteration<K, TXT, 1, STEADY>(x, pp, j + 1, jl, w);
+  if (!STEADY && j + 2 > j1) { j += 2; return; }
+  step_iteration<K, TXT, 2, STEADY>(x, pp, j + 2, jl, w);
+  if (!STEADY && j + 3 > j1) { j += 3; return; }
+  step_iteration<K, TXT, 3, STEADY>(x, pp, j + 3, jl, w);
+  if (!STEADY && j + 4 > j1) { j += 4; return; }
+  step_iteration<K, TXT, 4, STEADY>(x, pp, j + 4, jl, w);
+  if (!STEADY && j + 5 > j1) { j += 5; return; }
+  step_iteration<K, TXT, 5, STEADY>(x, pp, j + 5, jl, w);
+  j += 6;
 }
 
 // K update steps on one tile item.  Returns false (in every thread) if a
@@ -411,39 +499,39 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
                               float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
                               float one_m6c, float cc, int32_t* err) {
   using G = Geo<K, TXT>;
-  constexpr int R = G::R;
   constexpr int C4 = G::C4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   StepCtx<K, TXT> x;
   x.owner = tid < G::USED;
-  x.row = x.owner ? tid / C4 : 0;
+  const int row = x.owner ? tid / C4 : 0;
   const int col = x.owner ? tid % C4 : 0;
   const int xg = x0 - HX + 4 * col;
-  const int yg = y0 - K + x.row;
-  x.inside = x.owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
-  x.interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
-  x.interior_row = x.owner && (x.row >= K) && (x.row < K + TY);
-  // x-neighbours come from the adjacent lanes; lanes 0 and 31 read them from
-  // shared memory (at a row end the neighbouring row's value is taken, which
-  // only ever reaches margin sites)
+  const int yg = y0 - K + row;
+  const bool inside = x.owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
+  const bool interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
+  x.interior_row = x.owner && (row >= K) && (row < K + TY);
   x.fix_l = x.owner && lane == 0 && col > 0;
   x.fix_r = x.owner && lane == 31 && col < C4 - 1;
+#pragma unroll
+  for (int l = 1; l <= K; ++l) x.need[l] = inside && (row >= l && row < G::BH - l) && (l < K || interior_col);
   x.n = n;
   x.z0 = z0;
   x.z1 = z1;
-  x.lev = (float*)(smem + G::LEVEL_OFF);
-  x.ro = x.row * G::BW + 4 * col;
-  x.lo = x.row * G::LW + 4 + 4 * col;
-  x.out_col = out + (size_t)yg * n + xg;
   x.hd = half_dtau;
   x.om6c = one_m6c;
   x.cc = cc;
+  float* lev = (float*)(smem + G::LEVEL_OFF);
+  x.lb = lev + row * G::LW + 4 + 4 * col;
+  x.rb = (const float*)(smem + G::RING_OFF) + row * G::BW + 4 * col;
+  x.plane = (size_t)n * n;
   x.sm.set(smem, smem + (G::SMEM - 128), err);
   x.gl.set(out, out + (size_t)n * n * n, err);
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
+  // level K writes plane j - K + 1 at z-step j (only planes in [z0, z1) are stored)
+  x.outp = out + (size_t)yg * n + xg + (ptrdiff_t)(j0 - K + 1) * (ptrdiff_t)x.plane;
 
-  for (int i = tid; i < (K > 1 ? (K - 1) * 2 * G::LPLANE : 0); i += G::THREADS) x.lev[i] = 0.f;
+  for (int i = tid; i < G::NLEV * G::LPLANE; i += G::THREADS) lev[i] = 0.f;
   Pipe<K, TXT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
@@ -451,34 +539,29 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   pp.x0 = x0;
   pp.y0 = y0;
   pp.err = err;
-  pp.begin(j0, j1 + 1);
+  pp.begin(j0, j1 + 1, true);
 
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 w[K > 1 ? K - 1 : 1][3];
 #pragma unroll
   for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l) w[l][0] = w[l][1] = w[l][2] = zero4;
-
-  int sj = 1;  // slot of plane j (plane j0 sits in slot 1)
+  // steady z-steps: level K's plane j - K + 1 in [z0, z1) and level 1's
+  // plane j in [0, n)
+  const int ss = z0 + K - 1, se = min(z1 + K - 2, n - 1);
   int j = j0;
-  auto one = [&](auto rot) {
-    constexpr int ROT = decltype(rot)::value;
-    pp.advance(j, sj, j1 + 1);
-    step_iteration<K, TXT, ROT>(x, pp, j, sj, w);
-    pp.end_step();
-    sj = slot_add<R>(sj, 1);
-    ++j;
-  };
-  using R0 = std::integral_constant<int, 0>;
-  using R1 = std::integral_constant<int, 1>;
-  using R2 = std::integral_constant<int, 2>;
-  while (j + 2 <= j1) {
-    one(R0{});
-    one(R1{});
-    one(R2{});
-    if (!pp.ok(err)) return false;
+  while (j <= j1) {
+    if (j >= ss && j + 5 <= se)
+      step_group<K, TXT, true>(x, pp, j, j1, w);
+    else
+      step_group<K, TXT, false>(x, pp, j, j1, w);
+    // an expired wait seen early ends the loop; the decision that counts is
+    // taken below, after a barrier, the same in every thread
+    if (*(volatile const int*)pp.flag) break;
   }
-  if (j <= j1) one(R0{});
-  if (j <= j1) one(R1{});
+  // every thread's last z-step is complete before the caller's next item
+  // reinitialises the shared memory
+  pp.cta_wait((unsigned)((j - j0) & 1));
+  __syncthreads();
   return pp.ok(err);
 }
 

@@ -28,7 +28,7 @@ for n in (8, 12, 20, 36, 44, 68, 132):
     L = 0.4 * n
     v = wl.harmonic(n, L).astype(np.float32)
     for depth in (1, 2, 3):
-        for zc in (0, -1, 1, 3, 9, n + 5):
+        for zc in (0, -1, -2, 1, 3, 9, n + 5):
             s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=5, tol=0.0, temporal_depth=depth,
                                                                          zchunk=zc))
             s.set_potential(v)

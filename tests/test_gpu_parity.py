@@ -354,7 +354,8 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
     bit (ragged x/y tiles and z-chunks at n = 132; check cadence not a
     multiple of K), also with short spans that run on into the next tile
     column or leave a ragged last chunk (down to one plane) and in the
-    configuration the autotuner picks."""
+    configuration the autotuner picks, the balanced and the columns-first
+    partitions."""
     L = 0.3 * n
     rng = np.random.default_rng(n)
     v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
@@ -367,6 +368,8 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
                 ("k3z200", dict(temporal_depth=3, zchunk=200)),
                 ("k1bal", dict(temporal_depth=1, zchunk=-1)), ("k2bal", dict(temporal_depth=2, zchunk=-1)),
                 ("k3bal", dict(temporal_depth=3, zchunk=-1)),
+                ("k1col", dict(temporal_depth=1, zchunk=-2)), ("k2col", dict(temporal_depth=2, zchunk=-2)),
+                ("k3col", dict(temporal_depth=3, zchunk=-2)),
                 ("auto", dict(autotune=1))]
     for name, kw in variants:
         s = solver(fd, n, L, fd.F32, check_every=50, **kw)
