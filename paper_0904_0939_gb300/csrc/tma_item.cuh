@@ -280,7 +280,9 @@ struct Pipe {
     if (threadIdx.x == 0) {
       *(volatile int*)flag = 0;
       for (int s = 0; s < R; ++s) mbar_init(bars + s, 1);
-      if (step) mbar_init(cbar, G::THREADS);
+      // every thread of the block arrives (a batched launch runs shallower
+      // items with the deepest item's block size)
+      if (step) mbar_init(cbar, blockDim.x);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -531,7 +533,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   // level K writes plane j - K + 1 at z-step j (only planes in [z0, z1) are stored)
   x.outp = out + (size_t)yg * n + xg + (ptrdiff_t)(j0 - K + 1) * (ptrdiff_t)x.plane;
 
-  for (int i = tid; i < G::NLEV * G::LPLANE; i += G::THREADS) lev[i] = 0.f;
+  for (int i = tid; i < G::NLEV * G::LPLANE; i += blockDim.x) lev[i] = 0.f;
   Pipe<K, TXT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
