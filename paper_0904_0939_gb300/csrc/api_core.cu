@@ -63,8 +63,8 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "temporal_depth out of range";
     return FDTD_ERR_INVALID_ARG;
   }
-  if (o.zchunk < -1) {
-    err = "zchunk must be >= -1";
+  if (o.zchunk < -2) {
+    err = "zchunk must be >= -2";
     return FDTD_ERR_INVALID_ARG;
   }
   if (o.autotune < 0 || o.autotune > 1) {
