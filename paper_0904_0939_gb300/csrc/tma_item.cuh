@@ -315,13 +315,24 @@ struct Pipe {
     __syncthreads();
   }
   // The step barrier: arrive (after marking the flag if a wait expired) and
-  // wait for a phase, bounded like every wait.
+  // wait for a phase, bounded like every wait.  The bounds-checking build
+  // orders the z-steps with a full block barrier at the wait instead (same
+  // accesses, same results): with its checked loads the split form gave up
+  // waits on some blocks that run several items, which the unchecked build
+  // never did in the same configurations.
   __device__ __forceinline__ void cta_arrive() {
     if (timeout) *(volatile int*)flag = 1;
+#ifndef FDTD_CHECK_BOUNDS
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(cbar)) : "memory");
+#endif
   }
   __device__ __forceinline__ void cta_wait(unsigned parity) {
+#ifdef FDTD_CHECK_BOUNDS
+    (void)parity;
+    __syncthreads();
+#else
     if (!mbar_wait_bounded(cbar, parity, err, budget)) timeout = 1;
+#endif
   }
   // After a barrier: every thread reads the same flag; on a timeout drain
   // and report.
@@ -351,7 +362,9 @@ struct StepCtx {
   using G = Geo<K, TXT>;
   const float* rb;   // ring + this thread's offset in a box
   float* lb;         // level planes + this thread's offset in a level plane
-  float* outp;       // output column at the plane level K writes this z-step
+  float* out;        // the output field
+  long long ooff;    // offset of this thread's output column at the plane level K writes this
+                     // z-step (negative before the lattice: only planes in [z0, z1) are stored)
   size_t plane;      // n * n
   int n, z0, z1;
   bool owner, fix_l, fix_r, interior_row;
@@ -410,7 +423,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
                      x.sm.ld4(x.rb + SP * SL), x.sm.ld4(b0 + G::PLANE), x.hd, x.om6c, x.cc);
     };
     if constexpr (K == 1) {
-      if (x.need[1] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.outp, upd());
+      if (x.need[1] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
     } else {
       float* dst = x.lb + (U % 3) * G::LPLANE;
       if constexpr (STEADY) {
@@ -449,7 +462,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
                      x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + G::PLANE), x.hd, x.om6c, x.cc);
     };
     if (l == K) {
-      if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.outp, upd());
+      if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
     } else {
       float* dst = x.lb + (3 + 2 * (l - 2) + ((U - l + 7) & 1)) * G::LPLANE;
       if constexpr (STEADY) {
@@ -471,7 +484,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
     }
   }
   pp.cta_arrive();
-  x.outp += x.plane;
+  x.ooff += (long long)x.plane;
 }
 
 // Six z-steps from j (j - j0 a multiple of 6); a partial group stops after
@@ -530,8 +543,10 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.sm.set(smem, smem + (G::SMEM - 128), err);
   x.gl.set(out, out + (size_t)n * n * n, err);
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
-  // level K writes plane j - K + 1 at z-step j (only planes in [z0, z1) are stored)
-  x.outp = out + (size_t)yg * n + xg + (ptrdiff_t)(j0 - K + 1) * (ptrdiff_t)x.plane;
+  // level K writes plane j - K + 1 at z-step j (only planes in [z0, z1) are
+  // stored, so the offset is never dereferenced while negative)
+  x.out = out;
+  x.ooff = (long long)yg * n + xg + (long long)(j0 - K + 1) * (long long)x.plane;
 
   for (int i = tid; i < G::NLEV * G::LPLANE; i += blockDim.x) lev[i] = 0.f;
   Pipe<K, TXT> pp;
