@@ -83,6 +83,11 @@ __device__ __forceinline__ char* aligned_smem(char* raw) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+// Invalidate a barrier whose phases are all complete, so that its shared
+// memory can be reused (the next item's barriers or another item's data).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
@@ -159,20 +164,23 @@ __device__ __forceinline__ float4 f4(const float* p) { return *reinterpret_cast<
 // Bounds-checking build (nvcc -DFDTD_CHECK_BOUNDS): every shared-memory
 // load and store of the tile pipelines and every store to the output field
 // goes through Chk, which tests the address against its allocation; an
-// access outside is skipped (a load gives 0) and counted in *bad (the word
-// after the wait budget), so a debug run reports index errors without
-// faulting the GPU.  In the normal build Chk is empty and the accessors are
-// plain loads and stores.
+// access outside is not performed (a load reads the allocation's first
+// element and gives 0, a store is dropped) and counted per thread, and the
+// count is added to *bad (the word after the wait budget) when the item
+// ends (flush), so a debug run reports index errors without faulting the
+// GPU.  The checks add no branch around an access.  In the normal build
+// Chk is empty and the accessors are plain loads and stores.
 struct Chk {
 #ifdef FDTD_CHECK_BOUNDS
   const char* lo = nullptr;
   const char* hi = nullptr;
   int32_t* bad = nullptr;
-  __device__ __forceinline__ bool ok(const void* p, int bytes) const {
+  int miss = 0;
+  __device__ __forceinline__ bool ok(const void* p, int bytes) {
     const char* q = (const char*)p;
-    if (q >= lo && q + bytes <= hi) return true;
-    atomicAdd(bad, 1);
-    return false;
+    const bool good = q >= lo && q + bytes <= hi;
+    miss += good ? 0 : 1;
+    return good;
   }
 #endif
   __device__ __forceinline__ void set(const void* l, const void* h, int32_t* err) {
@@ -180,27 +188,41 @@ struct Chk {
     lo = (const char*)l;
     hi = (const char*)h;
     bad = err + 2;
+    miss = 0;
 #else
     (void)l, (void)h, (void)err;
 #endif
   }
-  __device__ __forceinline__ float4 ld4(const float* p) const {
+  __device__ __forceinline__ float4 ld4(const float* p) {
 #ifdef FDTD_CHECK_BOUNDS
-    if (!ok(p, 16)) return make_float4(0.f, 0.f, 0.f, 0.f);
-#endif
+    const bool good = ok(p, 16);
+    const float4 v = f4(good ? p : (const float*)lo);
+    return good ? v : make_float4(0.f, 0.f, 0.f, 0.f);
+#else
     return f4(p);
-  }
-  __device__ __forceinline__ float ld1(const float* p) const {
-#ifdef FDTD_CHECK_BOUNDS
-    if (!ok(p, 4)) return 0.f;
 #endif
-    return *p;
   }
-  __device__ __forceinline__ void st4(float* p, float4 v) const {
+  __device__ __forceinline__ float ld1(const float* p) {
+#ifdef FDTD_CHECK_BOUNDS
+    const bool good = ok(p, 4);
+    const float v = *(good ? p : (const float*)lo);
+    return good ? v : 0.f;
+#else
+    return *p;
+#endif
+  }
+  __device__ __forceinline__ void st4(float* p, float4 v) {
 #ifdef FDTD_CHECK_BOUNDS
     if (!ok(p, 16)) return;
 #endif
     *reinterpret_cast<float4*>(p) = v;
+  }
+  // add this thread's count of accesses outside the allocation to *bad
+  __device__ __forceinline__ void flush() {
+#ifdef FDTD_CHECK_BOUNDS
+    if (miss) atomicAdd(bad, miss);
+    miss = 0;
+#endif
   }
 };
 
@@ -315,24 +337,13 @@ struct Pipe {
     __syncthreads();
   }
   // The step barrier: arrive (after marking the flag if a wait expired) and
-  // wait for a phase, bounded like every wait.  The bounds-checking build
-  // orders the z-steps with a full block barrier at the wait instead (same
-  // accesses, same results): with its checked loads the split form gave up
-  // waits on some blocks that run several items, which the unchecked build
-  // never did in the same configurations.
+  // wait for a phase, bounded like every wait.
   __device__ __forceinline__ void cta_arrive() {
     if (timeout) *(volatile int*)flag = 1;
-#ifndef FDTD_CHECK_BOUNDS
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(cbar)) : "memory");
-#endif
   }
   __device__ __forceinline__ void cta_wait(unsigned parity) {
-#ifdef FDTD_CHECK_BOUNDS
-    (void)parity;
-    __syncthreads();
-#else
     if (!mbar_wait_bounded(cbar, parity, err, budget)) timeout = 1;
-#endif
   }
   // After a barrier: every thread reads the same flag; on a timeout drain
   // and report.
@@ -352,6 +363,17 @@ struct Pipe {
     return true;
   }
   __device__ __forceinline__ const float* box(int s) const { return ring + s * (G::SLOT_BYTES / 4); }
+  // End of an item, after its last barrier and ok(): the barriers are
+  // invalidated (thread 0) before the next item initialises barriers or
+  // stores data in the same shared memory (a barrier's memory may be reused
+  // only after mbarrier.inval; without it, blocks that ran several items
+  // gave up waits in some builds).
+  __device__ __forceinline__ void finish(bool step) {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < R; ++s) mbar_inval(bars + s);
+      if (step) mbar_inval(cbar);
+    }
+  }
 };
 
 // Per-thread constants of a step item: the shared-memory bases every access
@@ -578,8 +600,12 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   // every thread's last z-step is complete before the caller's next item
   // reinitialises the shared memory
   pp.cta_wait((unsigned)((j - j0) & 1));
+  x.sm.flush();
+  x.gl.flush();
   __syncthreads();
-  return pp.ok(err);
+  const bool good = pp.ok(err);
+  pp.finish(true);
+  return good;
 }
 
 // Partition of the lattice sums: 64 x TY tile columns cut along z into
@@ -673,9 +699,14 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
       }
     }
     pp.end_step();
-    if (!pp.ok(err)) return false;
+    if (!pp.ok(err)) {
+      sm.flush();
+      pp.finish(false);
+      return false;
+    }
     sj = slot_add<R>(sj, 1);
   }
+  sm.flush();
   // fixed-order block reduction
   double v4[4] = {s0.value(), sh.value(), sr.value(), sv.value()};
 #pragma unroll
@@ -692,6 +723,7 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
     for (int w = 0; w < G::THREADS / 32; ++w) acc += red[w * 4 + tid];
     dst[tid] = acc;
   }
+  pp.finish(false);
   __syncthreads();
   return true;
 }
