@@ -59,7 +59,10 @@ C2_SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 # as null (with the reason) instead of a stale figure.
 STENCIL_SOURCES = ("paper_0904_0939_gb300/csrc/tma_item.cuh", "paper_0904_0939_gb300/csrc/k_tblock.cu",
                    "paper_0904_0939_gb300/csrc/common.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    ("9924fd38e51e842b", 512, 3, -1, 128, 16): 1_763_456_000 + 522_286_336,
+    ("9924fd38e51e842b", 512, 3, -2, 128, 16): 1_194_080_768 + 514_817_280,
+}
 PARTITIONS = {-1: "balanced one-wave partition", -2: "columns-first partition"}
 
 
