@@ -25,6 +25,10 @@ Every function cites the passage of the paper it follows:
   set_boundary /
   periodic_boundary    Sec. III remark on other boundary conditions:
                        periodic ones (default: the zero shell)
+  cstep, cobservables, cevolve
+                       complex potentials (Sec. VIII outlook): Eq. updateeq
+                       with complex A, B; Hermitian Rayleigh quotient
+                       (fdtd_oracle_complex.c)
 """
 from __future__ import annotations
 
@@ -82,6 +86,12 @@ def _load():
     lib.oracle_grad_v_accum.restype = None
     lib.oracle_backward.argtypes = [i, d, d, d, P, P, i64, i64, i, d, d, P, P]
     lib.oracle_backward.restype = ctypes.c_int
+    lib.oracle_cstep.argtypes = [i, d, d, d, P, P, P, P, P, P]
+    lib.oracle_cstep.restype = None
+    lib.oracle_cobservables.argtypes = [i, d, d, P, P, P, P, P]
+    lib.oracle_cobservables.restype = None
+    lib.oracle_cevolve.argtypes = [i, d, d, d, P, P, P, P, P, P, i64, i64, d, i, i, d, P]
+    lib.oracle_cevolve.restype = i64
     _lib = lib
     return lib
 
@@ -278,3 +288,58 @@ def backward(psi0, v, a, dtau, T, check_every=100, mask=0, w_e=1.0, w_r=0.0, mas
     if rc != 0:
         raise MemoryError("oracle_backward could not allocate its trajectory")
     return g, {"E": obs[0], "r2": obs[1], "S0": obs[2], "loss": obs[3]}
+
+
+# --- complex potentials ------------------------------------------------------
+
+def _parts(x):
+    x = np.asarray(x)
+    return _dense(x.real), _dense(x.imag) if np.iscomplexobj(x) else np.zeros(x.shape)
+
+
+def cstep(psi, v, a, dtau, mass=1.0):
+    """One application of Eq. updateeq with a complex potential."""
+    n = _n_of(np.asarray(psi))
+    vr, vi = _parts(v)
+    pr, pi = _parts(psi)
+    pr, pi = pad(pr), pad(pi)
+    outr, outi = np.zeros_like(pr), np.zeros_like(pi)
+    _load().oracle_cstep(n, a, dtau, mass, _ptr(vr), _ptr(vi), _ptr(pr), _ptr(pi), _ptr(outr), _ptr(outi))
+    return unpad(outr) + 1j * unpad(outi)
+
+
+def cobservables(psi, v, a, mass=1.0) -> dict:
+    """Sums with the Hermitian inner product: S0, SH (complex), Sr, SV
+    (complex), and E = SH/S0, <r^2>, <V>."""
+    n = _n_of(np.asarray(psi))
+    vr, vi = _parts(v)
+    pr, pi = _parts(psi)
+    out = np.zeros(6)
+    _load().oracle_cobservables(n, a, mass, _ptr(vr), _ptr(vi), _ptr(pad(pr)), _ptr(pad(pi)), _ptr(out))
+    s0, sh, sr, sv = out[0], out[1] + 1j * out[2], out[3], out[4] + 1j * out[5]
+    return {"S0": s0, "SH": sh, "Sr": sr, "SV": sv, "E": sh / s0, "r2": sr / s0, "V": sv / s0}
+
+
+def cevolve(psi, v, a, dtau, max_steps, check_every=100, tol=0.0, tol_relative=False, mask=0, v_inf=0.0,
+            mass=1.0):
+    """Complex-potential evolution with checks (Secs. III-V); returns (psi, rec)."""
+    n = _n_of(np.asarray(psi))
+    vr, vi = _parts(v)
+    pr, pi = _parts(psi)
+    pr, pi = pad(pr), pad(pi)
+    tr, ti = np.zeros_like(pr), np.zeros_like(pi)
+    rec = np.zeros(10)
+    nchk = _load().oracle_cevolve(n, a, dtau, mass, _ptr(vr), _ptr(vi), _ptr(pr), _ptr(pi), _ptr(tr), _ptr(ti),
+                                  int(max_steps), int(check_every), float(tol), int(bool(tol_relative)), int(mask),
+                                  float(v_inf), _ptr(rec))
+    if nchk < 0:
+        raise ValueError("bad evolve arguments")
+    r = {"E": rec[0] + 1j * rec[1], "Eb": rec[2] + 1j * rec[1], "S0": rec[3], "r2": rec[4],
+         "V": rec[5] + 1j * rec[6], "dE": rec[7], "steps": int(rec[8]), "converged": bool(rec[9])}
+    return unpad(pr) + 1j * unpad(pi), r
+
+
+def cupsample(psi_c):
+    """The trilinear transfer (Sec. VI) of the real and imaginary parts."""
+    p = np.asarray(psi_c)
+    return upsample(p.real) + 1j * upsample(p.imag) if np.iscomplexobj(p) else upsample(p)

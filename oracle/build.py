@@ -11,13 +11,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def build_oracle(force: bool = False) -> str:
-    src = os.path.join(_HERE, "fdtd_oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("fdtd_oracle.c", "fdtd_oracle_complex.c")]
     out = os.path.join(_HERE, "liboracle.so")
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
         return out
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-           src, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp"] + srcs + ["-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

@@ -19,6 +19,9 @@ Potentials (paper citations):
   anisotropic     V = (x^2 + 2 y^2 + 3 z^2)/2 + sum of seeded Gaussians
   dodecahedron    V = -100 inside the regular dodecahedron of Sec. VII.E
   v_theta         V = r^2/2 + sum_k theta_k G_k(r)     differentiable workload
+  complex_oscillator  V = w2 r^2 / 2 with complex w2    complex potentials (Sec. VIII)
+  absorbing_layer W = eta sum_axes ((|x| - x0)/w)^2 beyond x0 = L/2 - w: the
+                  imaginary part -W of an absorbing boundary layer
 """
 from __future__ import annotations
 
@@ -135,6 +138,22 @@ def theta_basis(n: int, length: float, seed: int = BASE_SEED + 5, count: int = 1
 
 def v_theta(n: int, length: float, theta, basis) -> np.ndarray:
     return 0.5 * radius2(n, length) + np.tensordot(np.asarray(theta, dtype=np.float64), basis, axes=1)
+
+
+def complex_oscillator(n: int, length: float, omega2: complex) -> np.ndarray:
+    """V = omega2 r^2 / 2 with a complex omega2 (complex128 array)."""
+    return 0.5 * complex(omega2) * radius2(n, length).astype(np.complex128)
+
+
+def absorbing_layer(n: int, length: float, width: float, strength: float) -> np.ndarray:
+    """W(r) = strength * sum over axes of ((|x| - x0) / width)^2 where |x| > x0
+    = L/2 - width, else 0: the magnitude of a negative imaginary potential
+    -i W that absorbs what reaches the last `width` of the box on each side
+    (a complex absorbing layer; V = V_R - i W)."""
+    x0 = 0.5 * length - width
+    ax = axis(n, length)
+    f = np.where(np.abs(ax) > x0, ((np.abs(ax) - x0) / width) ** 2, 0.0)
+    return strength * (f[:, None, None] + f[None, :, None] + f[None, None, :])
 
 
 PHI = 0.5 * (1.0 + math.sqrt(5.0))
