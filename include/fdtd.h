@@ -67,6 +67,17 @@ extern "C" {
 #define FDTD_F64 0   /* psi and V in FP64 ("plain FP64 form") */
 #define FDTD_F32 1   /* psi and V in FP32, sums in FP64 / compensated FP32 */
 #define FDTD_BF16 2  /* psi stored as BF16, V and arithmetic in FP32 (coarse levels) */
+/* Complex potentials V = V_R + i V_I (the paper's outlook, Sec. VIII): a
+ * complex wavefunction, fields stored as interleaved (re, im) pairs.  As a
+ * lattice precision: psi, V and the per-site A, cB of Eq. updateeq as FP64
+ * (C64) or FP32 (C32) pairs, A and cB formed in FP64.  As a dtype of a field
+ * passed across the ABI: n^3 interleaved pairs of doubles (C64) or floats
+ * (C32).  Complex lattices take the one-step z-parallel kernel, zero
+ * boundaries, and evolve / observables / upsample (complex to complex);
+ * backward, snapshots, checkpoint files and batched mode are for real
+ * lattices only (FDTD_ERR_INVALID_ARG). */
+#define FDTD_C64 3
+#define FDTD_C32 4
 
 #define FDTD_MEM_HOST 0
 #define FDTD_MEM_DEVICE 1
@@ -153,8 +164,8 @@ typedef struct {
   double r2;              /* <r^2> = sum r^2 psi^2 / sum psi^2 */
   double r_rms;           /* sqrt(<r^2>) */
   double v_expect;        /* <V> = sum V psi^2 / sum psi^2 */
-  double delta_e;         /* |E_b - E_b(previous check)|, -1 if none */
-  double reserved;
+  double delta_e;         /* |E_b - E_b(previous check)|, -1 if none (complex lattices: the modulus) */
+  double energy_imag;     /* Im E = <V_I> for complex lattices (Hermitian Rayleigh quotient), 0 otherwise */
   int64_t steps;          /* steps taken by the last fdtd_evolve on this lattice */
   int32_t converged;      /* 1 if the last fdtd_evolve met the tolerance */
   int32_t checks;         /* checks made by the last fdtd_evolve */

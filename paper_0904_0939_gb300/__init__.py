@@ -30,6 +30,7 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_UNSTABLE_DT, ERR_NONFINITE, ERR_CUDA = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_SHAPE, ERR_WORKSPACE, ERR_STATE, ERR_IO = -5, -6, -7, -8, -9
 F64, F32, BF16 = 0, 1, 2
+C64, C32 = 3, 4  # complex potentials: interleaved (re, im) pairs of doubles / floats
 MEM_HOST, MEM_DEVICE = 0, 1
 DIST_UNIFORM, DIST_GAUSSIAN = 0, 1
 PARITY_NONE, PARITY_S, PARITY_A = 0, 1, 2
@@ -64,7 +65,7 @@ class Options(ctypes.Structure):
 class Obs(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("binding_energy", ctypes.c_double), ("norm", ctypes.c_double),
                 ("r2", ctypes.c_double), ("r_rms", ctypes.c_double), ("v_expect", ctypes.c_double),
-                ("delta_e", ctypes.c_double), ("reserved", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("delta_e", ctypes.c_double), ("energy_imag", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("converged", ctypes.c_int32), ("checks", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
@@ -181,22 +182,25 @@ def _check(rc: int, handle=None, allow_soft: bool = False) -> int:
 
 
 def _buffer(arr, want_dtype=None):
-    """(pointer, dtype code, mem kind, keepalive) for a numpy array or torch tensor."""
+    """(pointer, dtype code, mem kind, keepalive) for a numpy array or torch
+    tensor: float64 / float32 are passed as they are, complex128 / complex64
+    as interleaved pairs (C64 / C32), anything else is converted to float64."""
     try:
         import torch
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(arr, torch.Tensor):
         t = arr.contiguous()
-        if t.dtype not in (torch.float64, torch.float32):
+        codes = {torch.float64: F64, torch.float32: F32, torch.complex128: C64, torch.complex64: C32}
+        if t.dtype not in codes:
             t = t.double()
-        code = F64 if t.dtype == torch.float64 else F32
-        return ctypes.c_void_p(t.data_ptr()), code, (MEM_DEVICE if t.is_cuda else MEM_HOST), t
+        return ctypes.c_void_p(t.data_ptr()), codes[t.dtype], (MEM_DEVICE if t.is_cuda else MEM_HOST), t
     a = np.ascontiguousarray(arr)
-    if a.dtype not in (np.float64, np.float32):
+    codes = {np.dtype(np.float64): F64, np.dtype(np.float32): F32, np.dtype(np.complex128): C64,
+             np.dtype(np.complex64): C32}
+    if a.dtype not in codes:
         a = a.astype(np.float64)
-    code = F64 if a.dtype == np.float64 else F32
-    return ctypes.c_void_p(a.ctypes.data), code, MEM_HOST, a
+    return ctypes.c_void_p(a.ctypes.data), codes[a.dtype], MEM_HOST, a
 
 
 class Solver:
@@ -268,10 +272,13 @@ class Solver:
         with self._ctx():
             _check(lib.fdtd_set_psi(self.handle, lat, ptr, code, mem, mask), self.handle)
 
-    def get_psi(self, lat: int = 0, dtype=np.float64, out=None):
-        """psi as a dense (n, n, n) array [z][y][x]; `out` may be a CUDA tensor."""
+    def get_psi(self, lat: int = 0, dtype=None, out=None):
+        """psi as a dense (n, n, n) array [z][y][x] (float64 by default,
+        complex128 for complex lattices); `out` may be a CUDA tensor."""
         n = self.lattices[lat].n
         if out is None:
+            if dtype is None:
+                dtype = np.complex128 if self.lattices[lat].precision in (C64, C32) else np.float64
             out = np.empty((n, n, n), dtype=dtype)
         ptr, code, mem, keep = _buffer(self._sized(out, lat, "get_psi"))
         with self._ctx():

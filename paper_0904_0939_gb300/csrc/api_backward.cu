@@ -15,6 +15,8 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
   int rc = lat_check(h, lat);
   if (rc) return rc;
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "backward: not available for complex lattices");
   if (!gv_out || (dtype != FDTD_F64 && dtype != FDTD_F32) ||
       (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE) || T < 1 || !std::isfinite(w_e) ||
       !std::isfinite(w_r))

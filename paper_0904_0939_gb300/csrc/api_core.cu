@@ -36,7 +36,8 @@ int check_desc(const fdtd_lattice_desc& d, std::string& err) {
     err = "lattice n must be in [1, 2048]";
     return FDTD_ERR_INVALID_ARG;
   }
-  if (d.precision != FDTD_F64 && d.precision != FDTD_F32 && d.precision != FDTD_BF16) {
+  if (d.precision != FDTD_F64 && d.precision != FDTD_F32 && d.precision != FDTD_BF16 && d.precision != FDTD_C64 &&
+      d.precision != FDTD_C32) {
     err = "unknown precision";
     return FDTD_ERR_INVALID_ARG;
   }
@@ -125,18 +126,20 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
     L.es = (int)elem_bytes(d[l].precision);
     L.psi[0] = cv.take(L.n3 * L.es);
     L.psi[1] = cv.take(L.n3 * L.es);
-    if (d[l].precision == FDTD_F64) {
-      L.v = cv.take(L.n3 * 8);
-      L.coefA = (double*)cv.take(L.n3 * 8);
-      L.coefCB = (double*)cv.take(L.n3 * 8);
+    const bool cplx = is_complex(d[l].precision);
+    if (d[l].precision == FDTD_F64 || cplx) {
+      // FP64: V, A, cB as doubles; complex: V, A, cB as (re, im) pairs of the lattice's scalar
+      L.v = cv.take(L.n3 * L.es);
+      L.coefA = (double*)cv.take(L.n3 * L.es);
+      L.coefCB = (double*)cv.take(L.n3 * L.es);
     } else {
       L.v = cv.take(L.n3 * 4);
     }
-    L.nparts = std::max(sums_blocks(d[l].n), tma_sums_blocks(d[l].n));
-    L.partials = (double*)cv.take((size_t)L.nparts * 4 * sizeof(double));
+    L.nparts = cplx ? csums_blocks(d[l].n) : std::max(sums_blocks(d[l].n), tma_sums_blocks(d[l].n));
+    L.partials = (double*)cv.take((size_t)L.nparts * sums_per_block(d[l].precision) * sizeof(double));
     L.state = (LatState*)cv.take(2 * sizeof(LatState));
     L.hist = (double*)cv.take((size_t)kHistCap * kHistFields * sizeof(double));
-    if (o.backward_steps > 0 && d[l].precision != FDTD_BF16) {
+    if (o.backward_steps > 0 && d[l].precision != FDTD_BF16 && !cplx) {
       L.bw_T = o.backward_steps;
       L.bw_K = (int)std::ceil(std::sqrt((double)o.backward_steps));
       L.bw_npool = (L.bw_T + L.bw_K - 1) / L.bw_K;
@@ -151,7 +154,7 @@ void layout(const fdtd_lattice_desc* d, int count, const fdtd_options& o, Carve&
       L.gv = (double*)cv.take(L.n3 * 8);
       L.scales = (double*)cv.take((size_t)(L.bw_T / o.check_every + 2) * sizeof(double));
     }
-    if (o.snapshots > 0) {
+    if (o.snapshots > 0 && !cplx) {
       L.nsnap = o.snapshots;
       L.snaps = cv.take((size_t)L.nsnap * L.n3 * L.es);
     }
@@ -241,12 +244,18 @@ void fill_obs(const Lat& L, const LatState& s, fdtd_obs* out) {
   out->r_rms = std::sqrt(std::max(0.0, s.r2));
   out->v_expect = s.vexp;
   out->delta_e = s.delta_e;
+  out->energy_imag = s.energy_im;
 }
 
 // Copy n3 elements of dtype `dt` from user memory into a typed device
 // buffer of lattice precision `prec` (through the staging buffer for host
 // memory).
 int import_field(fdtd_context* c, const void* src, int dt, int mem, void* dst, int prec, size_t n3) {
+  if (is_complex(prec)) {  // a complex field is 2 n3 interleaved scalars
+    n3 *= 2;
+    dt = dt == FDTD_C64 ? FDTD_F64 : FDTD_F32;
+    prec = prec == FDTD_C64 ? FDTD_F64 : FDTD_F32;
+  }
   const size_t isz = dt == FDTD_F64 ? 8 : 4;
   auto convert = [&](const void* s, size_t count, size_t off) {
     with_type(prec, [&](auto* tag) {
@@ -275,6 +284,11 @@ int import_field(fdtd_context* c, const void* src, int dt, int mem, void* dst, i
 }
 
 int export_field(fdtd_context* c, const void* src, int prec, void* dst, int dt, int mem, size_t n3) {
+  if (is_complex(prec)) {  // a complex field is 2 n3 interleaved scalars
+    n3 *= 2;
+    dt = dt == FDTD_C64 ? FDTD_F64 : FDTD_F32;
+    prec = prec == FDTD_C64 ? FDTD_F64 : FDTD_F32;
+  }
   const size_t osz = dt == FDTD_F64 ? 8 : 4;
   auto convert = [&](void* d, size_t count, size_t off) {
     with_type(prec, [&](auto* tag) {
@@ -384,6 +398,18 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
     g_create_err = "workspace is not device memory";
     return FDTD_ERR_WORKSPACE;
   }
+  {
+    fdtd_options oo;
+    if (o)
+      oo = *o;
+    else
+      fdtd_default_options(&oo);
+    for (int l = 0; l < count; ++l)
+      if (is_complex(d[l].precision) && (oo.boundary != 0 || oo.batched)) {
+        g_create_err = "complex lattices need zero boundaries and a non-batched handle";
+        return FDTD_ERR_INVALID_ARG;
+      }
+  }
   fdtd_context* c = new fdtd_context();
   if (o)
     c->o = *o;
@@ -458,10 +484,37 @@ int fdtd_last_error(fdtd_handle h, char* buf, size_t n) {
 int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
   int rc = lat_check(h, lat);
   if (rc) return rc;
-  if (!v || (dtype != FDTD_F64 && dtype != FDTD_F32) || (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
+  const bool cplx_in = dtype == FDTD_C64 || dtype == FDTD_C32;
+  if (!v || (dtype != FDTD_F64 && dtype != FDTD_F32 && !cplx_in) ||
+      (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
     return fail(h, FDTD_ERR_INVALID_ARG, "set_potential: null pointer, bad dtype or mem_kind");
   Lat& L = h->lats[lat];
+  if (cplx_in && !is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "set_potential: a complex potential needs a complex lattice (FDTD_C64/C32)");
   cudaMemsetAsync(h->flags, 0, sizeof(int32_t), h->st);
+  if (is_complex(L.d.precision)) {
+    // V, A and cB of a complex lattice (real input: V_I = 0)
+    const bool in64 = dtype == FDTD_F64 || dtype == FDTD_C64;
+    const size_t isz = (in64 ? 8 : 4) * (cplx_in ? 2 : 1);
+    auto cconv = [&](const void* src, size_t cnt, size_t off) {
+      with_ctype(L.d.precision, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        launch_cset_potential<T>(src, in64, cplx_in, cnt, off, (T*)L.v, (T*)L.coefA, (T*)L.coefCB, L.p, h->flags,
+                                 h->st);
+      });
+      h->stats.launches += 1;
+    };
+    if (mem_kind == FDTD_MEM_DEVICE) {
+      cconv(v, L.n3, 0);
+    } else {
+      const size_t chunk = kStagingBytes / isz;
+      for (size_t off = 0; off < L.n3; off += chunk) {
+        size_t cnt = std::min(chunk, L.n3 - off);
+        cudaMemcpyAsync(h->staging, (const char*)v + off * isz, cnt * isz, cudaMemcpyHostToDevice, h->st);
+        cconv(h->staging, cnt, off);
+      }
+    }
+  }
   const size_t isz = dtype == FDTD_F64 ? 8 : 4;
   float* vf = L.d.precision == FDTD_F64 ? nullptr : (float*)L.v;
   double* vd = L.d.precision == FDTD_F64 ? (double*)L.v : nullptr;
@@ -472,7 +525,9 @@ int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem
       launch_set_potential<float>((const float*)src, cnt, off, vf, vd, L.coefA, L.coefCB, L.p, h->flags, h->st);
     h->stats.launches += 1;
   };
-  if (mem_kind == FDTD_MEM_DEVICE) {
+  if (is_complex(L.d.precision)) {
+    // done above
+  } else if (mem_kind == FDTD_MEM_DEVICE) {
     conv(v, L.n3, 0);
   } else {
     const size_t chunk = kStagingBytes / isz;
@@ -488,7 +543,7 @@ int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem
   if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("set_potential: ") + cudaGetErrorString(e));
   if ((rc = cuda_check(h, "set_potential"))) return rc;
   if (flags & 1) return fail(h, FDTD_ERR_NONFINITE, "set_potential: NaN or Inf in V");
-  if (flags & 2) return fail(h, FDTD_ERR_UNSTABLE_DT, "set_potential: 1 + dtau V / 2 <= 0 at some site");
+  if (flags & 2) return fail(h, FDTD_ERR_UNSTABLE_DT, "set_potential: 1 + dtau Re V / 2 <= 0 at some site");
   L.has_v = true;
   return FDTD_OK;
 }
@@ -499,10 +554,17 @@ int fdtd_init_symmetric(fdtd_handle h, int lat, uint64_t seed, int parity_mask, 
   if (!valid_mask(parity_mask) || (dist != FDTD_DIST_UNIFORM && dist != FDTD_DIST_GAUSSIAN))
     return fail(h, FDTD_ERR_INVALID_ARG, "init_symmetric: bad parity mask or distribution");
   Lat& L = h->lats[lat];
-  with_type(L.d.precision, [&](auto* tag) {
-    using T = std::remove_pointer_t<decltype(tag)>;
-    launch_init_random<T>((T*)L.psi[0], L.d.n, seed, (uint64_t)lat, dist, h->st);
-  });
+  if (is_complex(L.d.precision)) {
+    with_ctype(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      launch_cinit_random<T>((T*)L.psi[0], L.d.n, seed, (uint64_t)lat, dist, h->st);
+    });
+  } else {
+    with_type(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      launch_init_random<T>((T*)L.psi[0], L.d.n, seed, (uint64_t)lat, dist, h->st);
+    });
+  }
   h->stats.launches += 1;
   L.cur = 0;
   if (parity_mask) {
@@ -518,10 +580,12 @@ int fdtd_init_symmetric(fdtd_handle h, int lat, uint64_t seed, int parity_mask, 
 int fdtd_set_psi(fdtd_handle h, int lat, const void* psi, int dtype, int mem_kind, int parity_mask) {
   int rc = lat_check(h, lat);
   if (rc) return rc;
-  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32) ||
+  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32 && dtype != FDTD_C64 && dtype != FDTD_C32) ||
       (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE) || !valid_mask(parity_mask))
     return fail(h, FDTD_ERR_INVALID_ARG, "set_psi: null pointer, bad dtype, mem_kind or mask");
   Lat& L = h->lats[lat];
+  if (is_complex(dtype) != is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "set_psi: complex lattices take complex fields (FDTD_C64/C32), real ones real");
   if ((rc = import_field(h, psi, dtype, mem_kind, L.psi[L.cur], L.d.precision, L.n3))) return rc;
   L.mask = parity_mask;
   L.has_psi = true;
@@ -532,9 +596,12 @@ int fdtd_set_psi(fdtd_handle h, int lat, const void* psi, int dtype, int mem_kin
 int fdtd_get_psi(fdtd_handle h, int lat, void* psi, int dtype, int mem_kind) {
   int rc = lat_check(h, lat);
   if (rc) return rc;
-  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32) || (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
+  if (!psi || (dtype != FDTD_F64 && dtype != FDTD_F32 && dtype != FDTD_C64 && dtype != FDTD_C32) ||
+      (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
     return fail(h, FDTD_ERR_INVALID_ARG, "get_psi: null pointer, bad dtype or mem_kind");
   Lat& L = h->lats[lat];
+  if (is_complex(dtype) != is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "get_psi: complex lattices give complex fields (FDTD_C64/C32), real ones real");
   if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "get_psi: no wavefunction yet");
   return export_field(h, L.psi[L.cur], L.d.precision, psi, dtype, mem_kind, L.n3);
 }
@@ -601,7 +668,8 @@ int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out) {
   if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "observables: set_potential and init/set_psi first");
   int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
   launch_state_reset(&L.state[1], 0, h->st);
-  launch_finalize(&L.state[1], L.partials, np, 0, 0, L.p, L.d.v_inf, 0.0, 0, 1, h->st);
+  launch_finalize(&L.state[1], L.partials, np, 0, 0, L.p, L.d.v_inf, 0.0, 0, 1, h->st, 0, 0, nullptr, nullptr,
+                  sums_per_block(L.d.precision));
   h->stats.launches += 2;
   LatState s;
   cudaMemcpyAsync(&s, &L.state[1], sizeof(LatState), cudaMemcpyDeviceToHost, h->st);
@@ -628,6 +696,8 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
   if (!S.has_psi) return fail(dst, FDTD_ERR_STATE, "upsample: source has no wavefunction");
   if (S.p.periodic != D.p.periodic) return fail(dst, FDTD_ERR_INVALID_ARG, "upsample: boundaries differ");
   if (!D.has_v) return fail(dst, FDTD_ERR_STATE, "upsample: set the destination potential first");
+  if (is_complex(S.d.precision) != is_complex(D.d.precision))
+    return fail(dst, FDTD_ERR_INVALID_ARG, "upsample: both lattices complex or both real");
   if (src->st != dst->st) {
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -636,19 +706,30 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
     cudaEventDestroy(ev);
   }
   void* tmp = D.psi[1 - D.cur];
-  with_type(S.d.precision, [&](auto* tin) {
-    using Ti = std::remove_pointer_t<decltype(tin)>;
-    with_type(D.d.precision, [&](auto* tout) {
-      using To = std::remove_pointer_t<decltype(tout)>;
-      launch_upsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, D.p.periodic, dst->st);
+  if (is_complex(S.d.precision)) {
+    with_ctype(S.d.precision, [&](auto* tin) {
+      using Ti = std::remove_pointer_t<decltype(tin)>;
+      with_ctype(D.d.precision, [&](auto* tout) {
+        using To = std::remove_pointer_t<decltype(tout)>;
+        launch_cupsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, dst->st);
+      });
     });
-  });
+  } else {
+    with_type(S.d.precision, [&](auto* tin) {
+      using Ti = std::remove_pointer_t<decltype(tin)>;
+      with_type(D.d.precision, [&](auto* tout) {
+        using To = std::remove_pointer_t<decltype(tout)>;
+        launch_upsample<Ti, To>((const Ti*)S.psi[S.cur], S.d.n, (To*)tmp, D.p.periodic, dst->st);
+      });
+    });
+  }
   dst->stats.launches += 1;
   // renormalise and give the field the source's symmetry (Sec. VI)
   int id = 1000000 + (dst->check_seq++);
   int np = launch_sums_any(dst, D, tmp, nullptr);
   launch_state_reset(&D.state[1], 0, dst->st);
-  launch_finalize(&D.state[1], D.partials, np, id, 0, D.p, D.d.v_inf, 0.0, 0, 0, dst->st);
+  launch_finalize(&D.state[1], D.partials, np, id, 0, D.p, D.d.v_inf, 0.0, 0, 0, dst->st, 0, 0, nullptr, nullptr,
+                  sums_per_block(D.d.precision));
   scale_parity_any(dst, D, tmp, D.psi[D.cur], S.mask, &D.state[1], id, D.cur, nullptr);
   dst->stats.launches += 2;
   D.mask = S.mask;

@@ -167,7 +167,13 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
     const long ev = prof_begin(c);
-    if (prec == FDTD_F64) {
+    if (is_complex(prec)) {
+      with_ctype(prec, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        launch_cstep<T>((const T*)L.psi[L.cur], (T*)L.psi[1 - L.cur], (const T*)L.coefA, (const T*)L.coefCB, L.p,
+                        active, c->st);
+      });
+    } else if (prec == FDTD_F64) {
       launch_step_f64((const double*)L.psi[L.cur], (double*)L.psi[1 - L.cur], L.coefA, L.coefCB, L.p, active, c->st);
     } else if (prec == FDTD_F32) {
       if (tma)
@@ -185,8 +191,8 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
     }
     prof_end(c);
     c->stats.launches += 1;
-    // algorithmic bytes: psi read + psi write + V (FP64: A and cB) read once per launch
-    c->pending.push_back({t0, (int64_t)L.n3 * k, (double)L.n3 * (2.0 * L.es + (prec == FDTD_F64 ? 16.0 : 4.0)), ev});
+    // algorithmic bytes: psi read + psi write + V (FP64: A and cB; complex: A and cB pairs) read once per launch
+    c->pending.push_back({t0, (int64_t)L.n3 * k, (double)L.n3 * (2.0 * L.es + coef_bytes(prec)), ev});
     L.cur ^= 1;
     count -= k;
     t0 += k;
@@ -195,6 +201,14 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
 
 int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* active) {
   int np = 0;
+  if (is_complex(L.d.precision)) {
+    with_ctype(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      np = launch_csums<T>((const T*)psi, (const T*)L.v, L.p, L.partials, active, c->st);
+    });
+    c->stats.launches += 1;
+    return np;
+  }
   if (L.tma_ok && (psi == L.psi[0] || psi == L.psi[1])) {
     np = launch_sums_tma(L.sums_maps[psi == L.psi[1]], L.sums_maps[2], L.p, L.partials, active, c->flags + 1, c->st);
     c->stats.launches += 1;
@@ -210,6 +224,14 @@ int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* act
 
 void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int mask, const LatState* s, int id,
                       int out_idx, LatState* sw) {
+  if (is_complex(L.d.precision)) {
+    with_ctype(L.d.precision, [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      launch_cscale_parity<T>((const T*)in, (T*)out, L.d.n, mask, s, id, out_idx, sw, c->st);
+    });
+    c->stats.launches += 1;
+    return;
+  }
   with_type(L.d.precision, [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
     launch_scale_parity<T>((const T*)in, (T*)out, L.d.n, mask, s, id, out_idx, sw, c->st);
@@ -221,7 +243,7 @@ void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int ma
 void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
   int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
   launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, 0,
-                  0, nullptr, L.hist);
+                  0, nullptr, L.hist, sums_per_block(L.d.precision));
   c->stats.launches += 1;
   int mask = c->o.reimpose_parity ? L.mask : 0;
   scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], check_id, 1 - L.cur, &L.state[0]);
@@ -243,7 +265,7 @@ int read_state(fdtd_context* c, Lat& L) {
 void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditionalHandle cond) {
   int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
   launch_finalize(&L.state[0], L.partials, np, 0, 0, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, (int)ce,
-                  cond, c->flags + 1, L.hist);
+                  cond, c->flags + 1, L.hist, sums_per_block(L.d.precision));
   c->stats.launches += 1;
   int mask = c->o.reimpose_parity ? L.mask : 0;
   scale_parity_any(c, L, L.psi[L.cur], L.psi[1 - L.cur], mask, &L.state[0], -1, 1 - L.cur, &L.state[0]);
@@ -255,7 +277,7 @@ void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, 
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
   *launches = (ce + depth - 1) / depth;
-  *bytes = (double)*launches * L.n3 * (2.0 * L.es + (L.d.precision == FDTD_F64 ? 16.0 : 4.0));
+  *bytes = (double)*launches * L.n3 * (2.0 * L.es + coef_bytes(L.d.precision));
 }
 
 // Build (or reuse) the evolve graph of lattice L for its current start

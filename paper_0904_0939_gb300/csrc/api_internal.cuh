@@ -38,7 +38,24 @@ extern thread_local std::string g_create_err;  // message of a call that has no 
 
 constexpr size_t kStagingBytes = 8u << 20;
 
-inline size_t elem_bytes(int prec) { return prec == FDTD_F64 ? 8 : (prec == FDTD_F32 ? 4 : 2); }
+inline bool is_complex(int prec) { return prec == FDTD_C64 || prec == FDTD_C32; }
+// bytes of one site of a field of precision prec (complex: an (re, im) pair)
+inline size_t elem_bytes(int prec) {
+  switch (prec) {
+    case FDTD_F64: return 8;
+    case FDTD_F32: return 4;
+    case FDTD_C64: return 16;
+    case FDTD_C32: return 8;
+    default: return 2;
+  }
+}
+// bytes per site of the coefficients a step reads besides psi: V (FP32, BF16
+// storage), A and cB (FP64: two doubles; complex: two pairs)
+inline double coef_bytes(int prec) {
+  return prec == FDTD_F64 ? 16.0 : (is_complex(prec) ? 2.0 * (double)elem_bytes(prec) : 4.0);
+}
+// sums per block of the lattice's partials (S0, SH, Sr, SV; complex: SH and SV with imaginary parts)
+inline int sums_per_block(int prec) { return is_complex(prec) ? 6 : 4; }
 
 struct Lat {
   fdtd_lattice_desc d{};
@@ -165,6 +182,14 @@ void with_type(int prec, F&& f) {
     f((float*)nullptr);
   else
     f((__nv_bfloat16*)nullptr);
+}
+// the scalar type of a complex lattice's (re, im) pairs
+template <typename F>
+void with_ctype(int prec, F&& f) {
+  if (prec == FDTD_C64)
+    f((double*)nullptr);
+  else
+    f((float*)nullptr);
 }
 
 // stencil configuration, steps, checks and evolves (api_evolve.cu)

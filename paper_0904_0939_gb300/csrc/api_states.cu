@@ -43,6 +43,8 @@ int fdtd_save_psi(fdtd_handle h, int lat, const char* path) {
   if (rc) return rc;
   if (!path) return fail(h, FDTD_ERR_INVALID_ARG, "save_psi: null path");
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "save_psi: not available for complex lattices");
   if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "save_psi: no wavefunction yet");
   PsiFileHeader hd{};
   std::memcpy(hd.magic, kPsiMagic, 8);
@@ -72,6 +74,8 @@ int fdtd_load_psi(fdtd_handle h, int lat, const char* path) {
   if (rc) return rc;
   if (!path) return fail(h, FDTD_ERR_INVALID_ARG, "load_psi: null path");
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "load_psi: not available for complex lattices");
   std::FILE* f = std::fopen(path, "rb");
   if (!f) return fail(h, FDTD_ERR_IO, std::string("load_psi: cannot open ") + path);
   PsiFileHeader hd{};
@@ -182,6 +186,8 @@ int fdtd_snapshot_save(fdtd_handle h, int lat, int slot) {
   int rc = snap_check(h, lat, slot);
   if (rc) return rc;
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "snapshot_save: not available for complex lattices");
   if (!L.has_psi) return fail(h, FDTD_ERR_STATE, "snapshot_save: no wavefunction yet");
   cudaMemcpyAsync(snap_field(L, slot), L.psi[L.cur], L.n3 * L.es, cudaMemcpyDeviceToDevice, h->st);
   return cuda_check(h, "snapshot_save");
@@ -191,6 +197,8 @@ int fdtd_snapshot_load(fdtd_handle h, int lat, int slot) {
   int rc = snap_check(h, lat, slot);
   if (rc) return rc;
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "snapshot_load: not available for complex lattices");
   cudaMemcpyAsync(L.psi[L.cur], snap_field(L, slot), L.n3 * L.es, cudaMemcpyDeviceToDevice, h->st);
   L.has_psi = true;
   record_start(h, L);
@@ -202,6 +210,8 @@ int fdtd_project_out(fdtd_handle h, int lat, const int* slots, int count) {
   if (rc) return rc;
   if (count < 0 || (count > 0 && !slots)) return fail(h, FDTD_ERR_INVALID_ARG, "project_out: bad slot list");
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "project_out: not available for complex lattices");
   if (!L.has_psi || !L.has_v) return fail(h, FDTD_ERR_STATE, "project_out: set_potential and a wavefunction first");
   for (int k = 0; k < count; ++k)
     if ((rc = snap_check(h, lat, slots[k]))) return rc;
@@ -223,6 +233,8 @@ int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double* weights
   if (rc) return rc;
   if (count < 1 || !slots || !weights) return fail(h, FDTD_ERR_INVALID_ARG, "combine: bad slot or weight list");
   Lat& L = h->lats[lat];
+  if (is_complex(L.d.precision))
+    return fail(h, FDTD_ERR_INVALID_ARG, "combine: not available for complex lattices");
   if (!L.has_v) return fail(h, FDTD_ERR_STATE, "combine: set_potential first");
   for (int k = 0; k < count; ++k) {
     if ((rc = snap_check(h, lat, slots[k]))) return rc;

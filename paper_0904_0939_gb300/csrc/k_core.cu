@@ -495,6 +495,10 @@ template int launch_sums<__nv_bfloat16>(const __nv_bfloat16*, const void*, const
 // ------------------------------------------------------------------ check
 // One block: deterministic reduction of the partials, then the check of
 // Secs. III-V on thread 0.
+// NS = 4: real lattices (S0, SH, Sr, SV per block); NS = 6: complex lattices
+// (S0, Re SH, Im SH, Sr, Re SV, Im SV), whose E and <V> get imaginary parts
+// and whose convergence test takes the complex modulus of the change of E_b.
+template <int NS>
 __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __restrict__ parts, int np, int check_id,
                                                   int64_t t, double a3, double v_inf, double tol, int tol_rel,
                                                   int record, int seq_ce, cudaGraphConditionalHandle cond,
@@ -509,18 +513,20 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
     }
     return;
   }
-  __shared__ double sm[4][256];
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  __shared__ double sm[NS][256];
+  double acc[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) acc[q] = 0.0;
   for (int i = threadIdx.x; i < np; i += 256)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += parts[(size_t)i * 4 + q];
+    for (int q = 0; q < NS; ++q) acc[q] += parts[(size_t)i * NS + q];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = acc[q];
+  for (int q = 0; q < NS; ++q) sm[q][threadIdx.x] = acc[q];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + w];
+      for (int q = 0; q < NS; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
@@ -528,8 +534,12 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
     check_id = s->checks;
     t = (int64_t)check_id * seq_ce;
   }
-  double s0 = sm[0][0], sh = sm[1][0], sr = sm[2][0], sv = sm[3][0];
-  if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(sh) || !isfinite(sr) || !isfinite(sv)) {
+  const double s0 = sm[0][0];
+  const double sh = sm[1][0], shi = NS == 6 ? sm[2][0] : 0.0;
+  const double sr = sm[NS == 6 ? 3 : 2][0];
+  const double sv = sm[NS == 6 ? 4 : 3][0], svi = NS == 6 ? sm[5][0] : 0.0;
+  if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(sh) || !isfinite(sr) || !isfinite(sv) || !isfinite(shi) ||
+      !isfinite(svi)) {
     s->status = STATUS_NONFINITE;
     s->active = 0;
     s->scale_seq = -1;
@@ -543,21 +553,23 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
   s->scale_seq = check_id;
   if (seq) s->post = 1;
   if (!record) return;
-  double e = sh / s0, eb = e - v_inf;
+  double e = sh / s0, eb = e - v_inf, ei = shi / s0;
   s->s0 = s0;
   s->sh = sh;
   s->sr = sr;
   s->sv = sv;
   s->energy = e;
+  s->energy_im = ei;
   s->ebind = eb;
   s->r2 = sr / s0;
   s->vexp = sv / s0;
+  s->vexp_im = svi / s0;
   s->step = t;
   s->checks += 1;
   double d = -1.0;
   if (s->has_prev) {
-    d = fabs(eb - s->e_prev);
-    double thr = tol * (tol_rel ? fabs(eb) : 1.0);
+    d = NS == 6 ? hypot(eb - s->e_prev, ei - s->e_prev_im) : fabs(eb - s->e_prev);
+    double thr = tol * (tol_rel ? (NS == 6 ? hypot(eb, ei) : fabs(eb)) : 1.0);
     if (tol > 0.0 && d <= thr) {
       s->converged = 1;
       s->active = 0;
@@ -565,6 +577,7 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
   }
   s->delta_e = d;
   s->e_prev = eb;
+  s->e_prev_im = ei;
   s->has_prev = 1;
   if (hist) {
     double* h = hist + (size_t)((s->checks - 1) % kHistCap) * kHistFields;
@@ -585,9 +598,13 @@ __global__ void __launch_bounds__(256) k_finalize(LatState* s, const double* __r
 
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
                      double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce,
-                     cudaGraphConditionalHandle cond, const int32_t* err, double* hist) {
-  launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf, tol,
-             tol_rel, record, seq_ce, cond, err, hist);
+                     cudaGraphConditionalHandle cond, const int32_t* err, double* hist, int nsum) {
+  if (nsum == 6)
+    launch_pdl(k_finalize<6>, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf,
+               tol, tol_rel, record, seq_ce, cond, err, hist);
+  else
+    launch_pdl(k_finalize<4>, dim3(1), dim3(256), 0, st, s, partials, nparts, check_id, t, p.a * p.a * p.a, v_inf,
+               tol, tol_rel, record, seq_ce, cond, err, hist);
 }
 
 __global__ void k_state_reset(LatState* s, int mode, int seq_limit) {

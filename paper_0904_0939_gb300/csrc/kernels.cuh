@@ -16,6 +16,7 @@ struct LatState {
   double e_prev;    // binding energy of the previous check
   double s0, sh, sr, sv;
   double energy, ebind, r2, vexp, delta_e;
+  double energy_im, vexp_im, e_prev_im;  // imaginary parts (complex lattices; 0 otherwise)
   double scale;     // 1 / sqrt(S0 a^3) of the last check
   int64_t step;     // t of the last check
   int32_t has_prev, active, converged, status;
@@ -138,9 +139,13 @@ int sums_blocks(int n);
 // history ring.
 constexpr int kHistCap = 4096;
 constexpr int kHistFields = 8;
+// nsum = 4 for real lattices (S0, SH, Sr, SV per block), 6 for complex ones
+// (S0, Re SH, Im SH, Sr, Re SV, Im SV): E and <V> then get imaginary parts
+// and the convergence test uses the complex modulus of the change of E_b.
 void launch_finalize(LatState* s, const double* partials, int nparts, int check_id, int64_t t, const Params& p,
                      double v_inf, double tol, int tol_rel, int record, cudaStream_t st, int seq_ce = 0,
-                     cudaGraphConditionalHandle cond = 0, const int32_t* err = nullptr, double* hist = nullptr);
+                     cudaGraphConditionalHandle cond = 0, const int32_t* err = nullptr, double* hist = nullptr,
+                     int nsum = 4);
 
 // out = P(scale * in): renormalisation and symmetry re-imposition.  With
 // s == nullptr the factor is 1 and the call is unconditional; otherwise it
@@ -178,6 +183,26 @@ int launch_dot2(const T* phi, const T* psi, size_t count, double* partials, cuda
 void launch_ratio(const double* partials, int nparts, double* coef, cudaStream_t st);
 template <typename T>
 void launch_axpy(T* psi, const T* phi, const double* coef, double sign, double alpha, size_t count, cudaStream_t st);
+
+// ---- complex potentials (k_complex.cu) ------------------------------------------
+// Fields of complex lattices are interleaved (re, im) pairs of T (double or
+// float); A and cB are formed once per site in FP64 from V.
+int csums_blocks(int n);
+template <typename T>
+void launch_cset_potential(const void* in, int in_f64, int in_complex, size_t count, size_t off, T* v2, T* a2, T* cb2,
+                           const Params& p, int32_t* flags, cudaStream_t st);
+template <typename T>
+void launch_cstep(const T* in, T* out, const T* a2, const T* cb2, const Params& p, const int32_t* active,
+                  cudaStream_t st);
+template <typename T>
+int launch_csums(const T* psi, const T* v2, const Params& p, double* partials, const int32_t* active, cudaStream_t st);
+template <typename T>
+void launch_cscale_parity(const T* in, T* out, int n, int mask, const LatState* s, int check_id, int out_idx,
+                          LatState* sw, cudaStream_t st);
+template <typename T>
+void launch_cinit_random(T* out, int n, uint64_t seed, uint64_t lat, int dist, cudaStream_t st);
+template <typename Ti, typename To>
+void launch_cupsample(const Ti* in, int nc, To* out, cudaStream_t st);
 
 // ---- adjoint (k_adjoint.cu) ---------------------------------------------------
 // Split adjoint step: u = B lam with the g_V accumulation (pointwise), then
