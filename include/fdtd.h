@@ -373,6 +373,66 @@ FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
 FDTD_API int fdtd_observables_noalloc(const void* psi, const void* v, int dtype, int n, double length, double mass,
                                       double* out, void* stream);
 
+/* ---- z-slab decomposition (Sec. V) -------------------------------------------
+ * The paper partitions the lattice into slabs along z, one per process; each
+ * process updates its own planes, exchanges boundary planes with its
+ * neighbours, and the processes reduce their partial sums at every check.
+ * These calls are one process's side of that scheme on its GPU: the caller
+ * moves the halo planes between processes (e.g. NCCL send/recv through
+ * torch.distributed) and reduces the partial sums (an all-reduce of four
+ * doubles); the library allocates nothing.
+ *
+ * A slab of an N^3 FP32 lattice (N % 4 == 0, 8 <= N <= 2048) owns the nz_own
+ * global planes z_first .. z_first + nz_own - 1 (0-based, z the slowest
+ * index).  Its two fields psi0, psi1 and its potential v are caller-owned
+ * DEVICE buffers of N x N x (nz_own + 2 halo) floats, x fastest, plane k
+ * holding global plane z_first - halo + k: `halo` planes below and above
+ * the own planes.  V must be set on every plane that lies inside the
+ * lattice; halo planes beyond the lattice's faces are never read for psi
+ * (treated as the zero boundary of Sec. III) and must hold psi = 0.  The
+ * buffers must be 16-byte aligned and stay alive until fdtd_slab_destroy.
+ * Errors are reported through fdtd_last_error(NULL). */
+typedef struct fdtd_slab_ctx* fdtd_slab;
+
+/* Bytes of device workspace (partial sums, flags) a slab of nz_own planes needs. */
+FDTD_API int fdtd_slab_workspace_size(int n, int nz_own, size_t* bytes);
+
+/* Create the slab: 1 <= halo <= min(3, nz_own) (the deepest temporal block it will run),
+ * box length L, mass m, dtau (0 selects a^2/4; the von Neumann bound of
+ * Sec. III applies, else FDTD_ERR_UNSTABLE_DT), ws a 256-byte aligned device
+ * workspace of fdtd_slab_workspace_size() bytes, stream a cudaStream_t. */
+FDTD_API int fdtd_slab_create(int n, int z_first, int nz_own, int halo, double length, double mass, double dtau,
+                              float* psi0, float* psi1, const float* v, void* ws, size_t ws_bytes, void* stream,
+                              fdtd_slab* out);
+FDTD_API int fdtd_slab_destroy(fdtd_slab s);
+
+/* `depth` (1 <= depth <= halo) update steps of Eq. updateeq from field `src`
+ * (0 or 1) into the other field's own planes, with the same arithmetic as
+ * fdtd_evolve's FP32 stencil (bit for bit).  The src field's `depth` halo
+ * planes on each side must hold the neighbouring slabs' current planes; the
+ * destination's halo planes are not written (the caller refreshes them by
+ * the exchange).  Asynchronous on the slab's stream. */
+FDTD_API int fdtd_slab_steps(fdtd_slab s, int src, int depth);
+
+/* Partial sums of Eq. energysum over the own planes of field `src`:
+ * sums4 = {S0, SH, Sr, SV} with r measured from the lattice centre (the
+ * halo planes adjacent to the own planes must be current).  mem_kind
+ * FDTD_MEM_HOST: written to host memory after synchronising the stream;
+ * FDTD_MEM_DEVICE: four doubles of device memory, in stream order.  Returns
+ * FDTD_ERR_TIMEOUT if a bounded wait of an earlier step expired. */
+FDTD_API int fdtd_slab_sums(fdtd_slab s, int src, double* sums4, int mem_kind);
+
+/* Own planes of field dst = factor * P(own planes of field src): the
+ * renormalisation of Sec. III with the x and y symmetry operators of Sec. IV
+ * (mask bits 0-3; a z operator would need the mirror slab's planes and is
+ * refused).  src may equal dst. */
+FDTD_API int fdtd_slab_scale(fdtd_slab s, int src, int dst, double factor, int mask);
+
+/* Host arithmetic of a check from the lattice-wide sums {S0, SH, Sr, SV}
+ * (the sum over all slabs): out = {E, E_b = E - v_inf, <r^2>, <V>,
+ * sum psi^2 a^3, 1 / sqrt(S0 a^3)} for an N^3 lattice of box length L. */
+FDTD_API int fdtd_check_sums(const double* sums4, double length, int n, double v_inf, double* out);
+
 #ifdef __cplusplus
 }
 #endif

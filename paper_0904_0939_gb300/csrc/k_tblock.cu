@@ -94,6 +94,37 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   }
 }
 
+// K update steps on a z-slab of the lattice (Sec. V): a field of n x n x
+// nzbuf sites whose planes [zbase, zbase + nzo) are this slab's own and
+// whose `zbase` planes below and above are halo copies of the neighbouring
+// slabs' planes (planes outside [zlo, zhi) lie beyond the lattice's faces and
+// stay zero).  The own planes of every tile column are dealt to the blocks
+// by the balanced partition of k_step_tma.
+template <int K, int TXT>
+__global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_slab(const __grid_constant__ CUtensorMap map_psi,
+                                                                     const __grid_constant__ CUtensorMap map_v,
+                                                                     float* __restrict__ out, int n, int ntx,
+                                                                     int ncol, int nzo, int zbase, int nzbuf,
+                                                                     int zlo, int zhi, float half_dtau,
+                                                                     float one_m6c, float cc,
+                                                                     int32_t* __restrict__ err) {
+  if (*(volatile const int32_t*)err != 0) return;
+  extern __shared__ __align__(128) char smem_raw[];
+  char* smem = aligned_smem(smem_raw);
+  const int wcost = 2 * (K - 1);
+  const long long ctot = (long long)ncol * (nzo + wcost);
+  long long r = balanced_plane(ctot * blockIdx.x / gridDim.x, nzo, wcost);
+  const long long rend = balanced_plane(ctot * (blockIdx.x + 1) / gridDim.x, nzo, wcost);
+  while (r < rend) {
+    const int t = (int)(r / nzo), z0 = (int)(r - (long long)t * nzo);
+    const int z1 = (int)min((long long)nzo, z0 + (rend - r));
+    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, zbase + z0,
+                               zbase + z1, half_dtau, one_m6c, cc, err, nzbuf, zlo, zhi))
+      return;
+    r += z1 - z0;
+  }
+}
+
 __global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_sums_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                        const __grid_constant__ CUtensorMap map_v,
                                                                        int n, float a, float kfac,
@@ -226,6 +257,30 @@ void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, fl
   }
 }
 
+namespace tb {
+template <int K>
+void launch_slab_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int nzo, int zbase,
+                   int nzbuf, int zlo, int zhi, int32_t* err, cudaStream_t st) {
+  using G = Geo<K, 128>;
+  set_smem(k_step_slab<K, 128>, G::SMEM);
+  const int ntx = (p.n + 127) / 128, ncol = ntx * ((p.n + TY - 1) / TY);
+  const long long planes = (long long)ncol * nzo;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(resident_blocks<K, 128>(), planes));
+  k_step_slab<K, 128><<<blocks, G::THREADS, G::SMEM, st>>>(mpsi, mv, out, p.n, ntx, ncol, nzo, zbase, nzbuf, zlo, zhi,
+                                                           p.half_dtau_f, p.one_m6c_f, p.c_f, err);
+}
+}  // namespace tb
+
+void launch_step_slab(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
+                      int nzo, int zbase, int nzbuf, int zlo, int zhi, int32_t* err, cudaStream_t st) {
+  if (depth == 1)
+    tb::launch_slab_k<1>(map_psi_in, map_v, out, p, nzo, zbase, nzbuf, zlo, zhi, err, st);
+  else if (depth == 2)
+    tb::launch_slab_k<2>(map_psi_in, map_v, out, p, nzo, zbase, nzbuf, zlo, zhi, err, st);
+  else
+    tb::launch_slab_k<3>(map_psi_in, map_v, out, p, nzo, zbase, nzbuf, zlo, zhi, err, st);
+}
+
 int tma_sums_blocks(int n) { return tb::sums_items(n); }
 
 int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
@@ -244,8 +299,12 @@ void tma_box(int depth, int tx, int* box_w, int* box_h) {
   *box_h = tb::TY + 2 * depth;
 }
 
-// Tensor map of a dense n^3 FP32 field for box loads of box_w x box_h x 1.
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h) {
+  return encode_field_map_nz(map, base, n, n, box_w, box_h);
+}
+
+// Tensor map of a dense n x n x nz FP32 field for box loads of box_w x box_h x 1.
+int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h) {
   static void* fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -260,7 +319,7 @@ int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int 
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nz};
   cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)n * n * 4};
   cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   cuuint32_t estr[3] = {1, 1, 1};

@@ -90,6 +90,21 @@ int tma_resident_blocks(int depth, int tx);
 int tma_zchunk(int n, int depth, int tx);
 void tma_box(int depth, int tx, int* box_w, int* box_h);
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h);
+int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h);
+// `depth` steps on a z-slab field of n x n x nzbuf sites: own planes
+// [zbase, zbase + nzo), halo planes around them, planes outside [zlo, zhi)
+// beyond the lattice (tile width 128).
+void launch_step_slab(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
+                      int nzo, int zbase, int nzbuf, int zlo, int zhi, int32_t* err, cudaStream_t st);
+// slab sums and renormalisation (k_slab.cu): S0, SH, Sr, SV over the own
+// planes, z measured from the lattice centre with the slab's first own plane
+// at global plane z_first; out = factor * P_xy(in) on the own planes
+int slab_sums_blocks(int n, int nzo);
+int launch_slab_sums(const float* psi, const float* v, const Params& p, int nzo, int zbase, int z_first,
+                     double* partials, cudaStream_t st);
+void launch_slab_reduce(const double* partials, int nparts, double* out4, cudaStream_t st);
+void launch_slab_scale(const float* in, float* out, int n, int nzo, int zbase, int mask_xy, double factor,
+                       cudaStream_t st);
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                      int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st);
 int tma_sums_blocks(int n);

@@ -388,7 +388,8 @@ struct StepCtx {
   long long ooff;    // offset of this thread's output column at the plane level K writes this
                      // z-step (negative before the lattice: only planes in [z0, z1) are stored)
   size_t plane;      // n * n
-  int n, z0, z1;
+  int z0, z1;       // output planes of the item
+  int zlo, zhi;      // planes of the field inside the lattice (outside: zero at every level)
   bool owner, fix_l, fix_r, interior_row;
   bool need[K + 1];  // level l computes this column (without the z tests)
   float hd, om6c, cc;
@@ -454,12 +455,12 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
           x.sm.st4(dst, r);
           w[0][I0] = r;
         }
-      } else if (p >= x.n) {
+      } else if (p >= x.zhi) {
         if (x.need[1]) {
           x.sm.st4(dst, zero4);
           w[0][I0] = zero4;
         }
-      } else if (p >= 0 && x.need[1]) {
+      } else if (p >= x.zlo && x.need[1]) {
         const float4 r = upd();
         x.sm.st4(dst, r);
         w[0][I0] = r;
@@ -493,12 +494,12 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
           x.sm.st4(dst, r);
           w[l - 1][I0] = r;
         }
-      } else if (p >= x.n) {
+      } else if (p >= x.zhi) {
         if (x.need[l]) {
           x.sm.st4(dst, zero4);
           w[l - 1][I0] = zero4;
         }
-      } else if (p >= 0 && x.need[l]) {
+      } else if (p >= x.zlo && x.need[l]) {
         const float4 r = upd();
         x.sm.st4(dst, r);
         w[l - 1][I0] = r;
@@ -529,12 +530,18 @@ __device__ __forceinline__ void step_group(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp,
   j += 6;
 }
 
-// K update steps on one tile item.  Returns false (in every thread) if a
-// bounded wait expired.
+// K update steps on one tile item: output planes [z0, z1) of a field of
+// n x n x nz sites (nz = n: a whole lattice).  Planes outside [zlo, zhi) are
+// outside the lattice and stay zero at every level (a whole lattice: [0, n);
+// a z-slab with K-plane halos: the halo planes beyond the lattice's faces);
+// the planes beyond the field read as zero (TMA fill).  Returns false (in
+// every thread) if a bounded wait expired.
 template <int K, int TXT>
 __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
                               float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
-                              float one_m6c, float cc, int32_t* err) {
+                              float one_m6c, float cc, int32_t* err, int nz = -1, int zlo = 0, int zhi = -1) {
+  if (nz < 0) nz = n;
+  if (zhi < 0) zhi = nz;
   using G = Geo<K, TXT>;
   constexpr int C4 = G::C4;
   const int tid = threadIdx.x;
@@ -552,9 +559,10 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.fix_r = x.owner && lane == 31 && col < C4 - 1;
 #pragma unroll
   for (int l = 1; l <= K; ++l) x.need[l] = inside && (row >= l && row < G::BH - l) && (l < K || interior_col);
-  x.n = n;
   x.z0 = z0;
   x.z1 = z1;
+  x.zlo = zlo;
+  x.zhi = zhi;
   x.hd = half_dtau;
   x.om6c = one_m6c;
   x.cc = cc;
@@ -563,7 +571,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.rb = (const float*)(smem + G::RING_OFF) + row * G::BW + 4 * col;
   x.plane = (size_t)n * n;
   x.sm.set(smem, smem + (G::SMEM - 128), err);
-  x.gl.set(out, out + (size_t)n * n * n, err);
+  x.gl.set(out, out + (size_t)n * n * nz, err);
   const int j0 = z0 - K + 1, j1 = z1 + K - 2;
   // level K writes plane j - K + 1 at z-step j (only planes in [z0, z1) are
   // stored, so the offset is never dereferenced while negative)
@@ -586,7 +594,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l) w[l][0] = w[l][1] = w[l][2] = zero4;
   // steady z-steps: level K's plane j - K + 1 in [z0, z1) and level 1's
   // plane j in [0, n)
-  const int ss = z0 + K - 1, se = min(z1 + K - 2, n - 1);
+  const int ss = z0 + K - 1, se = min(z1 + K - 2, zhi - 1);
   int j = j0;
   while (j <= j1) {
     if (j >= ss && j + 5 <= se)

@@ -29,7 +29,7 @@ def test_reduce_over_ranks_gloo_two_ranks():
     import torch.multiprocessing as mp
 
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
