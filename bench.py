@@ -448,6 +448,75 @@ def backward_run(fd, dev):
     return res
 
 
+def slab_run(fd, dev, n=512, steps=300, every=100):
+    """The z-slab decomposition of Sec. V on one GPU: the 512^3 lattice cut
+    into 1, 2 and 4 slabs (halo 3, passes of three steps, halo copies
+    between the slabs' buffers, sums added on the host), 300 steps with a
+    check every 100, against the whole-lattice solver on the same start.
+    Measures the decomposition's own cost (halo planes recomputed by both
+    neighbours, halo copies, a host round trip per check); scaling over
+    GPUs is not measured here (one process per GPU would trade the halos
+    over NVLink and all-reduce four doubles per check)."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_0904_0939_gb300 import slab
+
+    L = 0.05 * n
+    v = wl.anisotropic(n, L).astype(np.float32)
+    start = np.random.default_rng(SEED).uniform(-1.0, 1.0, (n, n, n)).astype(np.float32)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    out = {"n": n, "steps": steps, "check_every": every, "halo": 3, "parts": {}}
+    w = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=every, tol=0.0))
+    w.set_potential(v)
+    w.set_psi(start)
+    w.evolve(30)  # autotuner's first-use timings
+    w.set_psi(start)
+    ms, _ = timed(lambda: w.evolve(steps))
+    e_whole = w.last_check()["energy"]
+    w.close()
+    out["whole_lattice"] = {"ms": ms, "gsite_per_s": n**3 * steps / (ms * 1e-3) / 1e9, "E": e_whole}
+    for parts in (1, 2, 4):
+        slabs = [slab.Slab(n, L, z0, k, 3) for z0, k in slab.partition(n, parts)]
+        for sl in slabs:
+            sl.load(v, which="v")
+        comm = slab.LocalComm(slabs)
+        for sl in slabs:
+            sl.load(start, 0)
+        slab.evolve(comm, n, L, 30, 10)  # warm-up
+        for sl in slabs:
+            sl.load(start, 0)
+        ms, (cur, rec, checks) = timed(lambda: slab.evolve(comm, n, L, steps, every))
+
+        def passes(k=steps // 3):
+            c = cur
+            for _ in range(k):
+                for sl in slabs:
+                    sl.steps(c, 3)
+                c = 1 - c
+                comm.exchange(c)
+
+        ms_steps, _ = timed(passes)
+        out["parts"][str(parts)] = {"ms": ms, "gsite_per_s": n**3 * steps / (ms * 1e-3) / 1e9, "checks": checks,
+                                    "passes_only_gsite_per_s": n**3 * 3 * (steps // 3) / (ms_steps * 1e-3) / 1e9,
+                                    "E": rec["E"], "E_rel_diff_vs_whole": abs(rec["E"] - e_whole) / abs(e_whole)}
+        for sl in slabs:
+            sl.close()
+        del slabs, comm
+        torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------------- CPU oracle
 
 def _omp_threads(k):
@@ -769,6 +838,7 @@ def main():
         extra["time_to_E0_coulomb_256"] = time_to_e0(fd, seed, dev)
         extra["batched_64_lattices"] = batched_run(fd, dev, seed, hbm)
         extra["theta_gradient_128_T4000"] = backward_run(fd, dev)
+        extra["z_slabs_512_one_gpu"] = slab_run(fd, dev)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()

@@ -388,7 +388,7 @@ FDTD_API int fdtd_observables_noalloc(const void* psi, const void* v, int dtype,
  * DEVICE buffers of N x N x (nz_own + 2 halo) floats, x fastest, plane k
  * holding global plane z_first - halo + k: `halo` planes below and above
  * the own planes.  V must be set on every plane that lies inside the
- * lattice; halo planes beyond the lattice's faces are never read for psi
+ * lattice, with 1 + dtau V / 2 > 0 (not checked here); halo planes beyond the lattice's faces are never read for psi
  * (treated as the zero boundary of Sec. III) and must hold psi = 0.  The
  * buffers must be 16-byte aligned and stay alive until fdtd_slab_destroy.
  * Errors are reported through fdtd_last_error(NULL). */
@@ -416,7 +416,8 @@ FDTD_API int fdtd_slab_steps(fdtd_slab s, int src, int depth);
 
 /* Partial sums of Eq. energysum over the own planes of field `src`:
  * sums4 = {S0, SH, Sr, SV} with r measured from the lattice centre (the
- * halo planes adjacent to the own planes must be current).  mem_kind
+ * halo planes adjacent to the own planes must be current), formed with the
+ * per-site arithmetic of the FP32 lattice sums of fdtd_observables.  mem_kind
  * FDTD_MEM_HOST: written to host memory after synchronising the stream;
  * FDTD_MEM_DEVICE: four doubles of device memory, in stream order.  Returns
  * FDTD_ERR_TIMEOUT if a bounded wait of an earlier step expired. */
@@ -425,7 +426,8 @@ FDTD_API int fdtd_slab_sums(fdtd_slab s, int src, double* sums4, int mem_kind);
 /* Own planes of field dst = factor * P(own planes of field src): the
  * renormalisation of Sec. III with the x and y symmetry operators of Sec. IV
  * (mask bits 0-3; a z operator would need the mirror slab's planes and is
- * refused).  src may equal dst. */
+ * refused).  src may equal dst only with mask 0 (a mirrored site is read
+ * by another thread than the one writing it). */
 FDTD_API int fdtd_slab_scale(fdtd_slab s, int src, int dst, double factor, int mask);
 
 /* Host arithmetic of a check from the lattice-wide sums {S0, SH, Sr, SV}

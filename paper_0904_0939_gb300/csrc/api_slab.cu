@@ -29,7 +29,8 @@ struct fdtd_slab_ctx {
   double* partials = nullptr;
   double* sums = nullptr;
   int nparts = 0;
-  CUtensorMap maps[3][3];  // [depth - 1][psi0, psi1, V]
+  CUtensorMap maps[3][3];  // [depth - 1][psi0, psi1, V], stencil boxes
+  CUtensorMap smaps[3];    // psi0, psi1, V with the sums box
 };
 
 namespace {
@@ -108,6 +109,11 @@ int fdtd_slab_create(int n, int z_first, int nz_own, int halo, double length, do
     tma_box(k, 128, &bw, &bh);
     for (int b = 0; b < 3; ++b) ok = ok && encode_field_map_nz(&s->maps[k - 1][b], bufs[b], n, s->nzbuf, bw, bh) == 0;
   }
+  {
+    int bw, bh;
+    tma_box(1, 64, &bw, &bh);
+    for (int b = 0; b < 3; ++b) ok = ok && encode_field_map_nz(&s->smaps[b], bufs[b], n, s->nzbuf, bw, bh) == 0;
+  }
   if (!ok) {
     delete s;
     return slab_fail("slab_create: tensor maps could not be encoded (fields must be 16-byte aligned)", FDTD_ERR_CUDA);
@@ -142,7 +148,8 @@ int fdtd_slab_steps(fdtd_slab s, int src, int depth) {
 int fdtd_slab_sums(fdtd_slab s, int src, double* sums4, int mem_kind) {
   if (!s || (src != 0 && src != 1) || !sums4 || (mem_kind != FDTD_MEM_HOST && mem_kind != FDTD_MEM_DEVICE))
     return slab_fail("slab_sums: bad handle, source index, output or mem_kind");
-  const int np = launch_slab_sums(s->psi[src], s->v, s->p, s->nzo, s->halo, s->z_first, s->partials, s->st);
+  const int np =
+      launch_slab_sums(s->smaps[src], s->smaps[2], s->p, s->nzo, s->halo, s->z_first, s->partials, s->flags + 1, s->st);
   launch_slab_reduce(s->partials, np, mem_kind == FDTD_MEM_DEVICE ? sums4 : s->sums, s->st);
   int rc = slab_cuda("slab_sums");
   if (rc) return rc;
@@ -157,8 +164,8 @@ int fdtd_slab_sums(fdtd_slab s, int src, double* sums4, int mem_kind) {
 
 int fdtd_slab_scale(fdtd_slab s, int src, int dst, double factor, int mask) {
   if (!s || (src != 0 && src != 1) || (dst != 0 && dst != 1) || !std::isfinite(factor) || mask < 0 || mask >= 16 ||
-      (mask & 3) == 3 || ((mask >> 2) & 3) == 3)
-    return slab_fail("slab_scale: bad handle, index, factor or mask (x and y symmetry only)");
+      (mask & 3) == 3 || ((mask >> 2) & 3) == 3 || (mask && src == dst))
+    return slab_fail("slab_scale: bad handle, index, factor or mask (x and y symmetry only, src != dst with a mask)");
   launch_slab_scale(s->psi[src], s->psi[dst], s->n, s->nzo, s->halo, mask, factor, s->st);
   return slab_cuda("slab_scale");
 }

@@ -1,4 +1,4 @@
-// Sums and renormalisation of a z-slab of an FP32 lattice (Sec. V: each
+// Reduction of a z-slab's partial sums and its renormalisation (Sec. V: each
 // process sums over its own planes; the partial sums are then reduced over
 // the processes, and the common factor 1/sqrt(S0 a^3) is applied by every
 // process to its own planes).  The slab field has n x n x nzbuf sites, own
@@ -12,49 +12,6 @@
 namespace fdtd {
 
 namespace {
-
-constexpr int kSlabThreads = 256;
-
-// S0 = sum psi^2, SH = sum psi (-Lap psi / (2 m a^2) + V psi), Sr = sum r^2
-// psi^2, SV = sum V psi^2 (Eq. energysum, sign of Sec. II's H) over the own
-// planes; block b takes rows b, b + nb, ... of the own planes in order,
-// FP64 accumulation, fixed-order block reduction.
-__global__ void __launch_bounds__(kSlabThreads) k_slab_sums(const float* __restrict__ psi, const float* __restrict__ v,
-                                                            int n, int nzo, int zbase, int z_first, double a,
-                                                            double kfac, double* __restrict__ partials) {
-  __shared__ double red[4][kSlabThreads];
-  double acc[4] = {0, 0, 0, 0};
-  const size_t nn = (size_t)n * n;
-  const double half = 0.5 * (double)(n - 1);
-  for (int r = blockIdx.x; r < n * nzo; r += gridDim.x) {
-    const int y = r % n, zl = zbase + r / n;
-    const double py = ((double)y - half) * a, pz = ((double)(z_first + r / n) - half) * a;
-    for (int x = threadIdx.x; x < n; x += kSlabThreads) {
-      const size_t i = ((size_t)zl * n + y) * n + x;
-      const double c = psi[i];
-      const double xm = x > 0 ? psi[i - 1] : 0.0, xp = x < n - 1 ? psi[i + 1] : 0.0;
-      const double ym = y > 0 ? psi[i - n] : 0.0, yp = y < n - 1 ? psi[i + n] : 0.0;
-      const double zm = psi[i - nn], zp = psi[i + nn];  // own or halo planes
-      const double lap = (((xm + xp) + (ym + yp)) + (zm + zp)) - 6.0 * c;
-      const double vv = v[i];
-      const double px = ((double)x - half) * a;
-      acc[0] += c * c;
-      acc[1] += c * (-kfac * lap + vv * c);
-      acc[2] += (px * px + py * py + pz * pz) * c * c;
-      acc[3] += vv * c * c;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int w = kSlabThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 4) partials[(size_t)blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
-}
 
 // out4 = the partials summed in block order (one thread: fixed order)
 __global__ void k_slab_reduce(const double* __restrict__ partials, int np, double* __restrict__ out4) {
@@ -91,16 +48,6 @@ __global__ void __launch_bounds__(256) k_slab_scale(const float* __restrict__ in
 }
 
 }  // namespace
-
-int slab_sums_blocks(int n, int nzo) { return (int)std::min<long long>((long long)n * nzo, 152 * 8); }
-
-int launch_slab_sums(const float* psi, const float* v, const Params& p, int nzo, int zbase, int z_first,
-                     double* partials, cudaStream_t st) {
-  const int nb = slab_sums_blocks(p.n, nzo);
-  k_slab_sums<<<nb, kSlabThreads, 0, st>>>(psi, v, p.n, nzo, zbase, z_first, p.a, 1.0 / (2.0 * p.mass * p.a * p.a),
-                                           partials);
-  return nb;
-}
 
 void launch_slab_reduce(const double* partials, int nparts, double* out4, cudaStream_t st) {
   k_slab_reduce<<<1, 1, 0, st>>>(partials, nparts, out4);

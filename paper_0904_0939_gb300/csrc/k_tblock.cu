@@ -125,6 +125,24 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_slab(const __grid
   }
 }
 
+// Partial sums of a z-slab's own planes [zbase, zbase + nzo) (Sec. V: each
+// process sums its own planes), cut like the lattice sums; plane zbase is
+// the lattice's plane z_first.
+__global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_slab_sums_tma(const __grid_constant__ CUtensorMap map_psi,
+                                                                            const __grid_constant__ CUtensorMap map_v,
+                                                                            int n, int nzo, int zbase, int z_first,
+                                                                            float a, float kfac,
+                                                                            double* __restrict__ partials,
+                                                                            int32_t* __restrict__ err) {
+  if (*(volatile const int32_t*)err != 0) return;
+  extern __shared__ __align__(128) char smem_raw[];
+  char* smem = aligned_smem(smem_raw);
+  const int item = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int zc = sums_zchunk_of(n, nzo), z0 = blockIdx.z * zc;
+  tma_sums_item<kSumsTX>(smem, &map_psi, &map_v, n, blockIdx.x * kSumsTX, blockIdx.y * TY, zbase + z0,
+                         zbase + min(z0 + zc, nzo), a, kfac, partials + (size_t)item * 4, err, z_first - zbase);
+}
+
 __global__ void __launch_bounds__(Geo<1, kSumsTX>::THREADS) k_sums_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                        const __grid_constant__ CUtensorMap map_v,
                                                                        int n, float a, float kfac,
@@ -282,6 +300,18 @@ void launch_step_slab(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, f
 }
 
 int tma_sums_blocks(int n) { return tb::sums_items(n); }
+int slab_sums_blocks(int n, int nzo) { return tb::sums_items_of(n, nzo); }
+
+int launch_slab_sums(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, int nzo, int zbase,
+                     int z_first, double* partials, int32_t* err, cudaStream_t st) {
+  using G = tb::Geo<1, tb::kSumsTX>;
+  tb::set_smem(tb::k_slab_sums_tma, G::SMEM);
+  const int zc = tb::sums_zchunk_of(p.n, nzo);
+  dim3 grid((p.n + tb::kSumsTX - 1) / tb::kSumsTX, (p.n + tb::TY - 1) / tb::TY, (nzo + zc - 1) / zc);
+  tb::k_slab_sums_tma<<<grid, G::THREADS, G::SMEM, st>>>(map_psi, map_v, p.n, nzo, zbase, z_first, (float)p.a,
+                                                        (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, err);
+  return (int)(grid.x * grid.y * grid.z);
+}
 
 int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
                     const int32_t* active, int32_t* err, cudaStream_t st) {

@@ -96,12 +96,14 @@ int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int 
 // beyond the lattice (tile width 128).
 void launch_step_slab(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                       int nzo, int zbase, int nzbuf, int zlo, int zhi, int32_t* err, cudaStream_t st);
-// slab sums and renormalisation (k_slab.cu): S0, SH, Sr, SV over the own
-// planes, z measured from the lattice centre with the slab's first own plane
-// at global plane z_first; out = factor * P_xy(in) on the own planes
+// slab sums (k_tblock.cu): partials of S0, SH, Sr, SV over the own planes
+// (the lattice sums' per-site arithmetic and partition), z measured from the
+// lattice centre with own plane zbase at lattice plane z_first; maps with the
+// 64-wide sums box.  Reduction and renormalisation (k_slab.cu): out4 = the
+// partials added in order; out = factor * P_xy(in) on the own planes.
 int slab_sums_blocks(int n, int nzo);
-int launch_slab_sums(const float* psi, const float* v, const Params& p, int nzo, int zbase, int z_first,
-                     double* partials, cudaStream_t st);
+int launch_slab_sums(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, int nzo, int zbase,
+                     int z_first, double* partials, int32_t* err, cudaStream_t st);
 void launch_slab_reduce(const double* partials, int nparts, double* out4, cudaStream_t st);
 void launch_slab_scale(const float* in, float* out, int n, int nzo, int zbase, int mask_xy, double factor,
                        cudaStream_t st);

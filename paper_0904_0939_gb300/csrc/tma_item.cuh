@@ -622,25 +622,31 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
 // sums a lattice (one lattice, batched, allocation-free) adds the same
 // partials in the same order: about four items per SM of a 152-SM device,
 // chunks of at least 16 planes, at most 4096 items.
+// A z-slab of nz planes of an n x n cross-section is cut the same way.
 constexpr int kSumsTX = 64;
-__host__ __device__ inline int sums_zchunk(int n) {
+__host__ __device__ inline int sums_zchunk_of(int n, int nz) {
   const int tiles = ((n + kSumsTX - 1) / kSumsTX) * ((n + TY - 1) / TY);
   int zs = (608 + tiles - 1) / tiles;
-  const int by_planes = n / 16 > 1 ? n / 16 : 1, by_count = 4096 / tiles > 1 ? 4096 / tiles : 1;
+  const int by_planes = nz / 16 > 1 ? nz / 16 : 1, by_count = 4096 / tiles > 1 ? 4096 / tiles : 1;
   zs = zs < by_planes ? zs : by_planes;
   zs = zs < by_count ? zs : by_count;
-  return (n + zs - 1) / zs;
+  return (nz + zs - 1) / zs;
 }
-__host__ __device__ inline int sums_items(int n) {
-  const int zc = sums_zchunk(n);
-  return ((n + kSumsTX - 1) / kSumsTX) * ((n + TY - 1) / TY) * ((n + zc - 1) / zc);
+__host__ __device__ inline int sums_zchunk(int n) { return sums_zchunk_of(n, n); }
+__host__ __device__ inline int sums_items_of(int n, int nz) {
+  const int zc = sums_zchunk_of(n, nz);
+  return ((n + kSumsTX - 1) / kSumsTX) * ((n + TY - 1) / TY) * ((nz + zc - 1) / zc);
 }
+__host__ __device__ inline int sums_items(int n) { return sums_items_of(n, n); }
 
-// Lattice sums over the tile interior, planes [z0, z1); the block's four
-// totals (FP64) go to dst[0..3].  Returns false if a bounded wait expired.
+// Lattice sums over the tile interior, planes [z0, z1) of the mapped field,
+// whose plane j is the lattice's plane j + zoff (zoff != 0 for a z-slab with
+// halo planes); the block's four totals (FP64) go to dst[0..3].  Returns
+// false if a bounded wait expired.
 template <int TXT>
 __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, int n, int x0,
-                              int y0, int z0, int z1, float a, float kfac, double* __restrict__ dst, int32_t* err) {
+                              int y0, int z0, int z1, float a, float kfac, double* __restrict__ dst, int32_t* err,
+                              int zoff = 0) {
   using G = Geo<1, TXT>;
   constexpr int R = G::R;
   constexpr int C4 = G::C4, BW = G::BW;
@@ -685,7 +691,7 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
     if (use) {
       const float4 ym = sm.ld4(b0 + ro - BW), yp = sm.ld4(b0 + ro + BW), zm = sm.ld4(bm + ro), zp = sm.ld4(bp + ro);
       const float4 v = sm.ld4(b0 + G::PLANE + ro);
-      const float pz = coord_f32(j, n, a);
+      const float pz = coord_f32(j + zoff, n, a);
       const float cs[4] = {c.x, c.y, c.z, c.w};
       const float xls[4] = {xl, c.x, c.y, c.z};
       const float xrs[4] = {c.y, c.z, c.w, xr};

@@ -1,12 +1,13 @@
 """The z-slab decomposition of Sec. V on one GPU: several slabs of one
 lattice in one process (halos copied between their buffers, sums added),
 each driven through the fdtd_slab_* C ABI, against the whole-lattice FP32
-solver (same stencil arithmetic: psi to 1e-6 of max |psi|, where only the
-FP32 rounding of a renormalisation factor computed from differently ordered
-FP64 sums may differ; E to 1e-10) and the FP64 oracle (2e-5, the FP32
-tolerance).  The cases cover one slab (both lattice faces in one buffer),
-two and three slabs, the thinnest slabs (nz_own = halo), passes of depth 1,
-2 and 3, partial passes before a check, and the x / y symmetry masks."""
+solver (same stencil arithmetic; psi to 1e-6 of max |psi| and E, <r^2> to
+1e-7: the slab sums share the whole-lattice sums' FP32 per-site arithmetic
+but cut the planes into other partial sums, so the energies and the
+renormalisation factors may differ by a rounding) and the FP64 oracle (2e-5, the FP32 tolerance).  The cases
+cover one slab (both lattice faces in one buffer), two and three slabs, the
+thinnest slabs (nz_own = halo), passes of depth 1, 2 and 3, partial passes
+before a check, and the x / y symmetry masks."""
 import numpy as np
 import pytest
 
@@ -69,8 +70,8 @@ def test_slabs_match_the_whole_lattice_and_the_oracle(fd, orc, n, parts, halo, m
     o = whole.last_check()
     whole.close()
     assert rel_max(got, ref32) <= 1e-6
-    assert rec["E"] == pytest.approx(o["energy"], rel=1e-10)
-    assert rec["r2"] == pytest.approx(o["r2"], rel=1e-10)
+    assert rec["E"] == pytest.approx(o["energy"], rel=1e-7)
+    assert rec["r2"] == pytest.approx(o["r2"], rel=1e-7)
 
     ref, orec, _ = orc.evolve(start, v, a, a * a / 4, steps, every, mask=mask)
     assert rel_max(got, ref) <= 2e-5
@@ -78,13 +79,16 @@ def test_slabs_match_the_whole_lattice_and_the_oracle(fd, orc, n, parts, halo, m
 
 
 def test_slab_sums_add_up_to_the_lattice_sums(fd, orc):
-    """the partial sums of three slabs of a given field, added, are the oracle's
-    lattice sums S0, SH, Sr, SV of the same (FP32-rounded) field"""
+    """the partial sums of three slabs of a given field, added, give the oracle's
+    E, <r^2>, <V> and norm of the same (FP32-rounded) field to 1e-6, the FP32
+    tolerance of the whole-lattice sums, whose per-site arithmetic they share"""
     from paper_0904_0939_gb300 import slab
 
     n, L = 48, 9.0
+    rng = np.random.default_rng(1)
     v = wl.anisotropic(n, L).astype(np.float32).astype(np.float64)
-    psi = _start(n, 9).astype(np.float32).astype(np.float64)
+    psi = np.exp(-wl.radius2(n, L)) * (1 + 0.1 * rng.standard_normal((n, n, n)))
+    psi = psi.astype(np.float32).astype(np.float64)
     slabs = [slab.Slab(n, L, z0, k, 3) for z0, k in slab.partition(n, 3)]
     try:
         for s in slabs:
@@ -95,7 +99,11 @@ def test_slab_sums_add_up_to_the_lattice_sums(fd, orc):
         for s in slabs:
             s.close()
     ref = orc.observables(psi, v, L / n)
-    np.testing.assert_allclose(total, [ref["S0"], ref["SH"], ref["Sr"], ref["SV"]], rtol=1e-12)
+    got = slab.check_values(total, L, n)
+    assert got["E"] == pytest.approx(ref["E"], rel=1e-6)
+    assert got["r2"] == pytest.approx(ref["r2"], rel=1e-6)
+    assert got["V"] == pytest.approx(ref["V"], rel=1e-6)
+    assert got["norm"] == pytest.approx(ref["S0"] * (L / n) ** 3, rel=1e-6)
 
 
 def test_slab_create_refusals(fd):
@@ -118,5 +126,8 @@ def test_slab_create_refusals(fd):
         s.steps(0, 4)  # deeper than the halo
     with pytest.raises(fd.FdtdError):
         s.scale(0, 1, 1.0, mask=0b110000)  # z symmetry needs the whole z axis
+    with pytest.raises(fd.FdtdError):
+        s.scale(1, 1, 1.0, mask=wl.ODD_X)  # mirrored in place
+    s.scale(1, 1, 2.0)  # in place without a mask
     s.close()
     torch.cuda.synchronize()
