@@ -110,10 +110,12 @@ typedef struct {
   int32_t temporal_depth; /* FP32/BF16 steps fused per stencil launch; 0 = auto */
   int32_t backward_steps; /* largest T that fdtd_backward may be asked for; 0 = none */
   int32_t batched;        /* 1: all lattices of the handle advance in one persistent launch (a
-                             cooperative kernel in a CUDA graph); with autotune and no
-                             temporal_depth, the first evolve of a set of lattice sizes times
-                             (depth 1..3) x (16/32/64 z-planes per item) on slices of
-                             2 x check_every steps of the run itself and finishes with the
+                             cooperative kernel in a CUDA graph; the update items of all
+                             active lattices are cut into one equal range per block); with
+                             autotune and no temporal_depth, the first evolve of a set of
+                             lattice sizes times (depth 1..3) x (tile width 64, 128) on
+                             update passes that write the spare fields without advancing the
+                             state, then runs the whole evolve in one launch with the
                              fastest (cached; identical results for every choice) */
   int32_t reimpose_parity;/* 1 (default): re-impose the symmetry mask at every check (Sec. IV) */
   int32_t stencil_kernel; /* 0 (default): TMA-streamed, temporally blocked kernel where it applies
@@ -154,7 +156,9 @@ typedef struct {
                              implemented).  Periodic lattices use the z-marching kernels
                              (the TMA boxes zero-fill), not batched mode and not
                              fdtd_observables_noalloc */
-  int32_t reserved[1];
+  int32_t tile_x;         /* tile width of the TMA stencil (64 or 128) when temporal_depth > 0
+                             or autotune is off; 0 = 128 for n > 64, else 64 (batched: 128 if
+                             most sites lie in lattices with n >= 96, else 64) */
 } fdtd_options;
 
 typedef struct {

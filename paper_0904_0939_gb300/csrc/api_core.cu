@@ -72,6 +72,10 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "autotune must be 0 or 1";
     return FDTD_ERR_INVALID_ARG;
   }
+  if (o.tile_x != 0 && o.tile_x != 64 && o.tile_x != 128) {
+    err = "tile_x must be 0, 64 or 128";
+    return FDTD_ERR_INVALID_ARG;
+  }
   if (o.stencil_kernel < 0 || o.stencil_kernel > 2) {
     err = "stencil_kernel must be 0, 1 or 2";
     return FDTD_ERR_INVALID_ARG;
@@ -748,9 +752,9 @@ int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
   if (rc) return rc;
   if (!depth || !zchunk) return fail(h, FDTD_ERR_INVALID_ARG, "tuned_config: null output");
   Lat& L = h->lats[lat];
-  if (h->o.batched && h->batch_depth) {  // the persistent launch's choice
+  if (h->o.batched && h->batch_depth) {  // the persistent launch's choice (balanced partition)
     *depth = h->batch_depth;
-    *zchunk = h->batch_zc;
+    *zchunk = -1;
     return FDTD_OK;
   }
   if (L.has_v && L.has_psi) choose_config(h, L);
@@ -765,7 +769,15 @@ int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y) {
   if (!tile_x || !tile_y) return fail(h, FDTD_ERR_INVALID_ARG, "tuned_kernel: null output");
   Lat& L = h->lats[lat];
   *tile_x = *tile_y = 0;
-  if (h->o.batched) return FDTD_OK;
+  if (h->o.batched) {
+    if (h->batch_depth) {
+      int bw = 0, bh = 0;
+      tma_box(h->batch_depth, h->batch_tx, &bw, &bh);
+      *tile_x = h->batch_tx;
+      *tile_y = bh - 2 * h->batch_depth;
+    }
+    return FDTD_OK;
+  }
   if (L.has_v && L.has_psi) choose_config(h, L);
   if (L.tma_ok && h->o.stencil_kernel == 0 && !L.plain && L.depth > 0) {
     int bw = 0, bh = 0;

@@ -36,7 +36,7 @@ void choose_config(fdtd_context* c, Lat& L) {
     if (!(c->o.stencil_kernel == 0 && c->o.autotune && f4)) return;
   } else if (c->o.temporal_depth > 0 || !c->o.autotune) {
     L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
-    L.tx = L.d.n > 64 ? 128 : 64;
+    L.tx = c->o.tile_x ? c->o.tile_x : (L.d.n > 64 ? 128 : 64);
     L.zc = c->o.zchunk != 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
     return;
   }
@@ -520,12 +520,12 @@ int evolve_lattices(fdtd_context* c, int64_t max_steps) {
 std::mutex g_btune_mu;
 std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_btune;
 
-// All lattices of the handle in persistent launches.  With autotuning on
-// (and no depth given) the first launches of a new set of lattice sizes are
-// slices of 2 x check_every steps, one per (depth 1..3, z-chunk 16/32/64)
-// candidate, timed with CUDA events; the fastest runs the rest in one
-// launch.  Every candidate computes the same bits, so tuning costs no extra
-// work, only launch boundaries.
+// All lattices of the handle in one persistent launch.  With autotuning on
+// (and no depth given) the first evolve of a new set of lattice sizes times
+// every (depth 1..3, tile width 64/128) candidate on update passes that
+// write the spare fields (the state does not advance, so every candidate
+// does the same work), caches the fastest and runs the evolve with it.
+// Every candidate computes the same bits.
 int evolve_batched(fdtd_context* c, int64_t max_steps) {
   const int count = (int)c->lats.size();
   if (count > batched_max_lattices()) return fail(c, FDTD_ERR_INVALID_ARG, "evolve: too many lattices for batched mode");
@@ -537,105 +537,138 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
   std::vector<int> sizes;
   for (auto& L : c->lats) sizes.push_back(L.d.n);
   const auto key = std::make_pair(dev, sizes);
-  std::vector<std::pair<int, int>> cands;  // (depth, z-chunk)
+  std::vector<std::pair<int, int>> cands;  // (depth, tile width)
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
-    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, c->o.zchunk > 0 ? c->o.zchunk : 32});
+    int tx = c->o.tile_x;
+    if (!tx) {  // 128 if most sites lie in lattices of 96 or more sites per axis
+      double big = 0.0, all = 0.0;
+      for (auto& L : c->lats) {
+        all += (double)L.n3;
+        if (L.d.n >= 96) big += (double)L.n3;
+      }
+      tx = 2.0 * big > all ? 128 : 64;
+    }
+    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, tx});
   } else {
     std::lock_guard<std::mutex> lock(g_btune_mu);
     auto it = g_btune.find(key);
     if (it != g_btune.end()) {
       cands.push_back(it->second);
     } else {
-      for (int d = 1; d <= 3; ++d)
-        for (int zc : {16, 32, 64}) cands.push_back({d, zc});
+      for (int tx : {64, 128})
+        for (int d = 1; d <= 3; ++d) cands.push_back({d, tx});
     }
   }
-  const bool tuning = cands.size() > 1;
   for (auto& L : c->lats) {
     launch_state_reset(&L.state[0], 0, c->st);
     c->stats.launches += 1;
   }
   cudaMemsetAsync(c->flags + 1, 0, sizeof(int32_t), c->st);
-  std::vector<char> table(batched_entry_bytes() * count + 64);
-  char* base = table.data() + ((64 - ((uintptr_t)table.data() & 63)) & 63);
+  // the table: tensor maps encoded once per handle, mask and field index patched per evolve
+  const size_t eb = batched_entry_bytes();
+  if (c->batch_table.size() != eb * count + 64) {
+    c->batch_table.assign(eb * count + 64, 0);
+    char* base = c->batch_table.data() + ((64 - ((uintptr_t)c->batch_table.data() & 63)) & 63);
+    for (int l = 0; l < count; ++l) {
+      Lat& L = c->lats[l];
+      if (batched_fill(base + l * eb, (const float*)L.psi[0], (const float*)L.psi[1], (const float*)L.v, L.partials,
+                       &L.state[0], L.hist, L.p, L.mask, L.cur, L.d.v_inf)) {
+        c->batch_table.clear();
+        return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
+      }
+    }
+  }
+  char* base = c->batch_table.data() + ((64 - ((uintptr_t)c->batch_table.data() & 63)) & 63);
+  for (int l = 0; l < count; ++l) batched_patch(base + l * eb, c->lats[l].mask, c->lats[l].cur);
+  cudaMemcpyAsync(c->batch_ws, base, eb * count, cudaMemcpyHostToDevice, c->st);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int64_t t = 0, steps = 0, slices = 0;
-  double best_rate = -1.0;
-  std::pair<int, int> best = cands[0];
-  std::vector<int64_t> step_at(count, 0);  // steps each lattice advanced while active
+  int64_t steps = 0;
+  int grid = 0;
   int rc = FDTD_OK;
-  auto slice = [&](std::pair<int, int> cd, int64_t t_end) -> int {
-    for (int l = 0; l < count; ++l) {
-      Lat& L = c->lats[l];
-      if (batched_fill(base + l * batched_entry_bytes(), (const float*)L.psi[0], (const float*)L.psi[1],
-                       (const float*)L.v, L.partials, &L.state[0], L.hist, L.p, L.mask, L.cur, L.d.v_inf,
-                       cd.second))
-        return fail(c, FDTD_ERR_CUDA, "evolve: could not encode the batched tensor maps");
-    }
-    cudaMemcpyAsync(c->batch_ws, base, batched_entry_bytes() * count, cudaMemcpyHostToDevice, c->st);
-    int grid = 0;
-    cudaEventRecord(e0, c->st);
-    int e = batched_launch(c->batch_ws, count, max_steps, t, t_end, t > 0, 0, (int)ce, c->o.tol, c->o.tol_relative,
-                           c->o.reimpose_parity, cd.first, c->flags + 1, c->st, &c->batch_graphs, &steps, &grid);
-    cudaEventRecord(e1, c->st);
+  auto launch = [&](std::pair<int, int> cd, int tune_passes) -> int {
+    int e = batched_launch(c->batch_ws, count, max_steps, 0, max_steps, 0, 0, (int)ce, c->o.tol, c->o.tol_relative,
+                           c->o.reimpose_parity, cd.first, cd.second, tune_passes, c->flags + 1, c->st,
+                           &c->batch_graphs, &steps, &grid);
     if (e) return fail(c, FDTD_ERR_CUDA, std::string("evolve (batched): ") + cudaGetErrorString((cudaError_t)e));
     c->stats.launches += 1;
     c->stats.graph_launches += 1;
-    ++slices;
-    int r = cuda_check(c, "evolve (batched)");
-    if (r) return r;
-    double upd = 0.0;
-    for (int l = 0; l < count; ++l) {
-      Lat& L = c->lats[l];
-      const bool was_active = L.host_state.active || t == 0;
-      if ((r = read_state(c, L))) return r;
-      if (L.host_state.status == STATUS_NONFINITE)
-        return fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
-      L.cur = L.host_state.cur;
-      if (was_active) {
-        const int64_t upto = L.host_state.active ? steps : L.host_state.step;
-        upd += (double)L.n3 * (double)std::max<int64_t>(0, upto - t);
-        step_at[l] = std::max(step_at[l], upto);
-      }
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (c->profiling) c->stats.stencil_ms += ms;
-    const double rate = ms > 0.f ? upd / ms : 0.0;
-    if (rate > best_rate) {
-      best_rate = rate;
-      best = cd;
-    }
-    t = steps;
     return FDTD_OK;
   };
-  bool any = true;
-  for (size_t i = 0; tuning && i < cands.size() && any && t < max_steps; ++i) {
-    if ((rc = slice(cands[i], std::min<int64_t>(max_steps, t + 2 * ce)))) break;
-    any = false;
-    for (auto& L : c->lats) any |= L.host_state.active != 0;
+  std::pair<int, int> best = cands[0];
+  if (cands.size() > 1) {
+    Range r("batched autotune");
+    double best_rate = -1.0;
+    double sites = 0.0;
+    for (auto& L : c->lats) sites += (double)L.n3;
+    constexpr int kPasses = 4;
+    for (auto cd : cands) {
+      int e = batched_prepare(c->batch_ws, count, cd.first, cd.second, c->flags + 1, &c->batch_graphs);
+      if (e) {
+        cudaGetLastError();
+        continue;  // a configuration that cannot be made resident is skipped
+      }
+      if ((rc = launch(cd, 1))) break;  // first launch of the graph: not timed
+      cudaEventRecord(e0, c->st);
+      if ((rc = launch(cd, kPasses))) break;
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      if ((rc = cuda_check(c, "evolve (batched autotune)"))) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double rate = ms > 0.f ? sites * cd.first * kPasses / ms : 0.0;
+      if (rate > best_rate) {
+        best_rate = rate;
+        best = cd;
+      }
+    }
+    int32_t expired = 0;  // timings of launches whose waits expired are not kept
+    if (!rc) {
+      cudaMemcpyAsync(&expired, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+      cudaStreamSynchronize(c->st);
+    }
+    if (!rc && !expired && best_rate > 0.0) {
+      std::lock_guard<std::mutex> lock(g_btune_mu);
+      g_btune[key] = best;
+    }
   }
-  if (!rc && tuning && best_rate > 0.0) {
-    std::lock_guard<std::mutex> lock(g_btune_mu);
-    g_btune[key] = best;
+  if (!rc) {
+    cudaEventRecord(e0, c->st);
+    rc = launch(best, 0);
+    cudaEventRecord(e1, c->st);
   }
-  if (!rc && any && t < max_steps) rc = slice(best, max_steps);
+  if (!rc) rc = cuda_check(c, "evolve (batched)");
+  std::vector<int64_t> step_at(count, 0);  // steps each lattice advanced while active
+  for (int l = 0; !rc && l < count; ++l) {
+    Lat& L = c->lats[l];
+    if ((rc = read_state(c, L))) break;
+    if (L.host_state.status == STATUS_NONFINITE) {
+      rc = fail(c, FDTD_ERR_NONFINITE, "non-finite or vanishing norm during evolve");
+      break;
+    }
+    L.cur = L.host_state.cur;
+    step_at[l] = L.host_state.active ? steps : L.host_state.step;
+  }
+  if (!rc && c->profiling) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->stats.stencil_ms += ms;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  // the persistent launches are the stencil launches of a batched evolve
+  // the persistent launch is the stencil launch of a batched evolve
   for (int l = 0; l < count; ++l) {
     Lat& L = c->lats[l];
     L.last_steps = L.host_state.converged ? L.host_state.step : max_steps;
     c->stats.stencil_site_updates += (int64_t)L.n3 * step_at[l];
     c->stats.stencil_bytes += (double)L.n3 * 12.0 * ((step_at[l] + best.first - 1) / best.first);
   }
-  c->stats.stencil_launches += slices;
-  if (c->profiling) c->stats.stencil_timed_launches += slices;
+  c->stats.stencil_launches += 1;
+  if (c->profiling) c->stats.stencil_timed_launches += 1;
   c->batch_depth = best.first;
-  c->batch_zc = best.second;
+  c->batch_tx = best.second;
   return FDTD_OK;
 }
 

@@ -134,6 +134,64 @@ __device__ __forceinline__ size_t site_index(int x, int y, int z, int n) {
 
 // Kahan-compensated FP32 accumulator (Kahan 1965): sum - comp carries the
 // running total to ~2^-48 relative, enough to hand over to FP64.
+// out = scale * P(in) on the float4 of sites 4 x4 .. 4 x4 + 3 of row (y, z)
+// of an n^3 FP32 field with n % 4 == 0; P the symmetry operators of the mask
+// (Sec. IV).  The mirror of an aligned float4 along x is the aligned float4
+// ending at n - 1 - 4 x4, read reversed; each site gets scale_site, the
+// expression of the one-site renormalisation, so every caller agrees bit
+// for bit.
+__device__ __forceinline__ void scale_parity_f4_at(const float* __restrict__ in, float* __restrict__ out, int n,
+                                                   int mask, float scale, int x4, int y, int z) {
+  const int mx = mask & 3, my = (mask >> 2) & 3, mz = (mask >> 4) & 3;
+  int ys = y, zs = z;
+  bool neg = false, zero = false;
+  if (my) {
+    const int mm = n - 1 - y;
+    if (y > mm) {
+      ys = mm;
+      neg ^= (my == 2);
+    } else if (y == mm && my == 2) {
+      zero = true;
+    }
+  }
+  if (mz) {
+    const int mm = n - 1 - z;
+    if (z > mm) {
+      zs = mm;
+      neg ^= (mz == 2);
+    } else if (z == mm && mz == 2) {
+      zero = true;
+    }
+  }
+  const float* row = in + ((size_t)zs * n + ys) * n;
+  const float4 a = *reinterpret_cast<const float4*>(row + 4 * x4);
+  float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (mx) {
+    const float4 b = *reinterpret_cast<const float4*>(row + (n - 4 - 4 * x4));
+    mv[0] = b.w;  // mirror of site 4 x4 + 0 is n - 1 - 4 x4
+    mv[1] = b.z;
+    mv[2] = b.y;
+    mv[3] = b.x;
+  }
+  float o[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int x = 4 * x4 + c, mm = n - 1 - x;
+    bool ng = neg, zc = zero;
+    float src = av[c];
+    if (mx) {
+      if (x > mm) {
+        src = mv[c];
+        ng ^= (mx == 2);
+      } else if (x == mm && mx == 2) {
+        zc = true;
+      }
+    }
+    o[c] = scale_site(src, scale, ng, zc);
+  }
+  *reinterpret_cast<float4*>(out + ((size_t)z * n + y) * n + 4 * x4) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
 struct Kahan {
   float sum = 0.f, comp = 0.f;
   __device__ __forceinline__ void add(float v) {

@@ -4,14 +4,26 @@
 // on the binding energy, Secs. III-V) and update steps (Eq. updateeq) --
 // until every lattice has converged or max_steps is reached.
 //
-// Work is split into phases separated by a grid-wide barrier: SUMS (one item
-// per 64 x 16 tile column of each active lattice), FINALIZE (one lattice per
-// block), SCALE (renormalise + symmetry, out of place), and STEP (one item
-// per tile x z-chunk, K update steps through the TMA pipeline of
-// tma_item.cuh).  Items are dealt to blocks round-robin over the active
-// lattices; converged lattices drop out.  The per-site arithmetic and the
-// reduction order are those of the one-lattice path, so every lattice ends
-// bit-identical to a separate fdtd_evolve of the same lattice.
+// Work is split into phases separated by a grid-wide barrier:
+//   SUMS      the lattice-sums items of every active lattice (the one-lattice
+//             partition: 64 x 16 tile columns cut into z-chunks), dealt to
+//             the blocks in equal runs of consecutive items, so that a block
+//             streams several chunks of one column in one pipeline run;
+//   FINALIZE  one lattice per block;
+//   SCALE     renormalise + symmetry, out of place, float4 sites of every
+//             checked lattice dealt grid-wide;
+//   STEP      K update steps through the TMA pipeline of tma_item.cuh: the
+//             tile columns of the active lattices are laid end to end, each
+//             costing n + 2(K - 1) z-steps, and the cost line is cut into one
+//             equal range per block (the balanced partition of the one-lattice
+//             stencil, across lattices), so a block runs few, long items.
+// Converged lattices drop out of every phase.  The per-site arithmetic and
+// the reduction order are those of the one-lattice path, so every lattice
+// ends bit-identical to a separate fdtd_evolve of the same lattice.
+//
+// A tuning mode runs a given number of STEP phases from the current fields
+// into the spare ones without advancing the state, so that candidates
+// (depth, tile width) can be timed on the same work.
 //
 // The grid barrier is a sense-reversing counter in global memory; every wait
 // on it is bounded in wall-clock time, after which the block sets the error
@@ -26,30 +38,29 @@ namespace fdtd {
 
 namespace {
 
-constexpr int kTXB = 64;      // tile width of the batched stencil items
-static_assert(kTXB == tb::kSumsTX, "the batched sums use the one-lattice sums partition");
-constexpr int kMaxLat = 256;  // lattices per batched handle
+constexpr int kSumsTXB = tb::kSumsTX;  // tile width of the sums items (the one-lattice partition)
+constexpr int kMaxLat = 256;           // lattices per batched handle
 
 }  // namespace
 
 // Device table entry of one lattice (written by the host before the launch).
 struct alignas(64) BatchLat {
-  CUtensorMap step_map[3][3];  // [depth-1][psi0, psi1, V], tile width kTXB
-  CUtensorMap sums_map[3];     // [psi0, psi1, V]
+  CUtensorMap step_map[2][3][3];  // [tile 64, 128][depth-1][psi0, psi1, V]
+  CUtensorMap sums_map[3];        // [psi0, psi1, V], the sums box
   float* psi[2];
   double* partials;
   LatState* state;
   double* hist;  // check history ring (kHistCap records)
-  int n, mask, step_zc, cur;
+  int n, mask, cur, pad0;
   float hd, om6c, cc, a_f, kfac_f;
-  int pad;
+  int pad1;
   double a3, v_inf;
 };
 
 struct BatchRun {
   int64_t max_steps, t_start, t_end;
   double tol;
-  int check_every, tol_rel, reimpose, depth, nlat, skip_first, check0, pad;
+  int check_every, tol_rel, reimpose, depth, nlat, skip_first, check0, tune_passes;
   unsigned bar_count, bar_gen;
   int64_t steps_done;
 };
@@ -108,12 +119,14 @@ __device__ bool grid_barrier(BatchRun* run, int32_t* err) {
   return bad == 0;
 }
 
-// lattice of a global item index (prefix[] has nlat + 1 entries)
-__device__ __forceinline__ int find_lattice(const int* prefix, int nlat, int item) {
+// the lattice whose range [pre[l], pre[l + 1]) holds u: the largest l with
+// pre[l] <= u (lattices with empty ranges are skipped that way)
+template <typename T>
+__device__ __forceinline__ int find_lattice(const T* pre, int nlat, T u) {
   int lo = 0, hi = nlat - 1;
   while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= item)
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= u)
       lo = mid;
     else
       hi = mid - 1;
@@ -121,9 +134,20 @@ __device__ __forceinline__ int find_lattice(const int* prefix, int nlat, int ite
   return lo;
 }
 
-// Check of Secs. III-V on the block's lattice, same order as k_finalize.
-__device__ void finalize_lattice(const BatchLat& L, int nparts, int check_id, int64_t t, const BatchRun& run) {
-  __shared__ double sm[4][256];
+// tile plane c n + clamp(u - c (n + w) - w, 0, n), c = u / (n + w): the
+// balanced partition's map from cost to tile planes of one lattice
+__device__ __forceinline__ long long cost_to_plane(long long u, int n, int w) {
+  const long long unit = n + w, c = u / unit;
+  long long o = u - c * unit - w;
+  o = o < 0 ? 0 : (o > n ? n : o);
+  return c * n + o;
+}
+
+// Check of Secs. III-V on the block's lattice, same order as k_finalize;
+// red: 1024 doubles of scratch (the block's dynamic shared memory).
+__device__ void finalize_lattice(const BatchLat& L, int nparts, int check_id, int64_t t, const BatchRun& run,
+                                 double* red) {
+  double (*sm)[256] = reinterpret_cast<double (*)[256]>(red);
   LatState* s = L.state;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < nparts; i += 256)
@@ -188,151 +212,212 @@ __device__ void finalize_lattice(const BatchLat& L, int nparts, int check_id, in
   __syncthreads();
 }
 
-template <int K>
-__device__ __forceinline__ void step_item(char* smem, const BatchLat& L, int cur, int local, int32_t* err, bool& ok) {
-  const int gx = (L.n + kTXB - 1) / kTXB, gy = (L.n + tb::TY - 1) / tb::TY;
-  const int bx = local % gx, by = (local / gx) % gy, bz = local / (gx * gy);
-  const int z0 = bz * L.step_zc;
-  ok = tb::tma_step_item<K, kTXB>(smem, &L.step_map[K - 1][cur], &L.step_map[K - 1][2], L.psi[cur ^ 1], L.n,
-                                  bx * kTXB, by * tb::TY, z0, min(z0 + L.step_zc, L.n), L.hd, L.om6c, L.cc, err) &&
-       ok;
+// Per-block views of the lattices, rebuilt by thread 0 whenever the active
+// set changes: prefix sums of the sums items and of the STEP costs of the
+// active lattices.
+struct Views {
+  int pre_sums[kMaxLat + 1];
+  long long pre_cost[kMaxLat + 1];
+  long long pre_scale[kMaxLat + 1];
+  int cur[kMaxLat], act[kMaxLat];
+  float scale[kMaxLat];
+};
+
+template <int TXT>
+__device__ void build_prefixes(Views& v, const BatchLat* __restrict__ lats, int nlat, int w) {
+  int a = 0;
+  long long b = 0;
+  for (int l = 0; l < nlat; ++l) {
+    v.pre_sums[l] = a;
+    v.pre_cost[l] = b;
+    if (!v.act[l]) continue;
+    const int n = lats[l].n;
+    a += tb::sums_items(n);
+    b += (long long)((n + TXT - 1) / TXT) * ((n + tb::TY - 1) / tb::TY) * (n + w);
+  }
+  v.pre_sums[nlat] = a;
+  v.pre_cost[nlat] = b;
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(tb::Geo<KMAX, kTXB>::THREADS) k_batched(const BatchLat* __restrict__ lats,
-                                                                          BatchRun* run, int32_t* err) {
+// One update item, kept out of line so that the phase loop's state does not
+// compete with the pipeline for registers (it is saved once per item).
+template <int K, int TXT>
+__device__ __noinline__ bool step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, float* out,
+                                       int n, int x0, int y0, int z0, int z1, float hd, float om6c, float cc,
+                                       int32_t* err) {
+  return tb::tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, hd, om6c, cc, err);
+}
+
+// A run of consecutive sums items of one tile column, out of line like the
+// update items.
+__device__ __noinline__ bool sums_run(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, int n, int x0,
+                                      int y0, int z0, int z1, float a, float kfac, double* dst, int32_t* err, int zc,
+                                      long long stride) {
+  return tb::tma_sums_item<kSumsTXB>(smem, map_psi, map_v, n, x0, y0, z0, z1, a, kfac, dst, err, 0, zc, stride);
+}
+
+// One STEP phase: k (<= KMAX) steps of every active lattice, from field
+// cur[l] into the other, over the block's range of the cost line.
+template <int KMAX, int TXT>
+__device__ bool step_phase(char* smem, const Views& v, const BatchLat* __restrict__ lats, int nlat, int k, int w,
+                           int32_t* err) {
+  const long long U = v.pre_cost[nlat];
+  const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+  if (u0 >= u1) return true;
+  constexpr int TI = TXT == 128 ? 1 : 0;
+  bool ok = true;
+  for (int l = find_lattice(v.pre_cost, nlat, u0); l < nlat && v.pre_cost[l] < u1 && ok; ++l) {
+    if (!v.act[l]) continue;
+    const BatchLat& L = lats[l];
+    const int n = L.n, gx = (n + TXT - 1) / TXT;
+    const long long base = v.pre_cost[l];
+    const long long lo = (u0 > base ? u0 : base) - base;
+    const long long hi = (u1 < v.pre_cost[l + 1] ? u1 : v.pre_cost[l + 1]) - base;
+    long long r = cost_to_plane(lo, n, w);
+    const long long rend = cost_to_plane(hi, n, w);
+    const int cur = v.cur[l];
+    while (r < rend && ok) {
+      const int t = (int)(r / n), z0 = (int)(r - (long long)t * n);
+      const int z1 = (int)((long long)n < z0 + (rend - r) ? (long long)n : z0 + (rend - r));
+      const int x0 = (t % gx) * TXT, y0 = (t / gx) * tb::TY;
+      if (k == 1)
+        ok = step_item<1, TXT>(smem, &L.step_map[TI][0][cur], &L.step_map[TI][0][2], L.psi[cur ^ 1], n, x0,
+                                       y0, z0, z1, L.hd, L.om6c, L.cc, err);
+      else if (k == 2 || KMAX == 2)
+        ok = step_item<(KMAX >= 2 ? 2 : 1), TXT>(smem, &L.step_map[TI][1][cur], &L.step_map[TI][1][2],
+                                                         L.psi[cur ^ 1], n, x0, y0, z0, z1, L.hd, L.om6c, L.cc, err);
+      else
+        ok = step_item<KMAX, TXT>(smem, &L.step_map[TI][KMAX - 1][cur], &L.step_map[TI][KMAX - 1][2],
+                                          L.psi[cur ^ 1], n, x0, y0, z0, z1, L.hd, L.om6c, L.cc, err);
+      r += z1 - z0;
+    }
+  }
+  return ok;
+}
+
+template <int KMAX, int TXT>
+__global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const BatchLat* __restrict__ lats,
+                                                                         BatchRun* run, int32_t* err) {
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = tb::aligned_smem(smem_raw);
-  __shared__ int pre_sums[kMaxLat + 1], pre_step[kMaxLat + 1], s_cur[kMaxLat], s_act[kMaxLat];
+  __shared__ Views v;
   const int nlat = run->nlat;
   const int64_t max_steps = run->max_steps;
   const int ce = run->check_every;
+  const int w = 2 * (KMAX - 1);
   if (threadIdx.x == 0) {
-    int a = 0, b = 0;
     for (int l = 0; l < nlat; ++l) {
-      pre_sums[l] = a;
-      pre_step[l] = b;
-      const int n = lats[l].n;
-      const int tiles64 = ((n + kTXB - 1) / kTXB) * ((n + tb::TY - 1) / tb::TY);
-      a += tb::sums_items(n);
-      b += tiles64 * ((n + lats[l].step_zc - 1) / lats[l].step_zc);
-      s_cur[l] = lats[l].cur;
-      s_act[l] = lats[l].state->active;  // a lattice that converged in an earlier slice stays retired
+      v.cur[l] = lats[l].cur;
+      v.act[l] = lats[l].state->active;  // a lattice that converged in an earlier launch stays retired
     }
-    pre_sums[nlat] = a;
-    pre_step[nlat] = b;
+    build_prefixes<TXT>(v, lats, nlat, w);
   }
   __syncthreads();
-  bool ok = true;
   const int64_t t_start = run->t_start, t_end = run->t_end;
+  if (run->tune_passes > 0) {  // timing: STEP phases into the spare fields, state unchanged
+    for (int p = 0; p < run->tune_passes; ++p)
+      if (!step_phase<KMAX, TXT>(smem, v, lats, nlat, KMAX, w, err) || !grid_barrier(run, err)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) run->steps_done = t_start;
+    return;
+  }
   int64_t t = t_start;
   int check_id = run->check0;
   for (;;) {
     if ((t % ce == 0 || t == max_steps) && !(run->skip_first && t == t_start)) {
-      // ---- SUMS
-      for (int it = blockIdx.x; it < pre_sums[nlat] && ok; it += gridDim.x) {
-        const int l = find_lattice(pre_sums, nlat, it);
-        if (!s_act[l]) continue;
-        const BatchLat& L = lats[l];
-        const int local = it - pre_sums[l];
-        const int gx = (L.n + kTXB - 1) / kTXB, gy = (L.n + tb::TY - 1) / tb::TY;
-        const int zc = tb::sums_zchunk(L.n), z0 = (local / (gx * gy)) * zc;
-        ok = tb::tma_sums_item<kTXB>(smem, &L.sums_map[s_cur[l]], &L.sums_map[2], L.n, (local % gx) * kTXB,
-                                     ((local / gx) % gy) * tb::TY, z0, min(z0 + zc, L.n), L.a_f, L.kfac_f,
-                                     L.partials + (size_t)local * 4, err);
+      // ---- SUMS: equal runs of consecutive sums items (chunks of one column stream as one run)
+      {
+        const int C = v.pre_sums[nlat];
+        const int c0 = (int)((long long)C * blockIdx.x / gridDim.x);
+        const int c1 = (int)((long long)C * (blockIdx.x + 1) / gridDim.x);
+        bool ok = true;
+        for (int it = c0; it < c1 && ok;) {
+          const int l = find_lattice(v.pre_sums, nlat, it);
+          const BatchLat& L = lats[l];
+          const int n = L.n, gx = (n + kSumsTXB - 1) / kSumsTXB, gy = (n + tb::TY - 1) / tb::TY;
+          const int zc = tb::sums_zchunk(n), nch = (n + zc - 1) / zc;
+          const int q = it - v.pre_sums[l], col = q / nch, ch0 = q - col * nch;
+          const int ch1 = min(nch, ch0 + (c1 - it));
+          const int tx = col % gx, ty = col / gx;
+          ok = sums_run(smem, &L.sums_map[v.cur[l]], &L.sums_map[2], n, tx * kSumsTXB, ty * tb::TY, ch0 * zc,
+                        min(ch1 * zc, n), L.a_f, L.kfac_f,
+                        L.partials + ((size_t)ch0 * gy * gx + (size_t)ty * gx + tx) * 4, err, zc,
+                        (long long)gx * gy * 4);
+          it += ch1 - ch0;
+        }
+        if (!ok || !grid_barrier(run, err)) return;
       }
-      if (!ok || !grid_barrier(run, err)) return;
       // ---- FINALIZE
       for (int l = blockIdx.x; l < nlat; l += gridDim.x) {
-        if (!s_act[l]) continue;
-        const int n = lats[l].n;
-        finalize_lattice(lats[l], tb::sums_items(n), check_id, t, *run);
+        if (!v.act[l]) continue;
+        finalize_lattice(lats[l], tb::sums_items(lats[l].n), check_id, t, *run, (double*)smem);
       }
       if (!grid_barrier(run, err)) return;
-      // ---- SCALE: out = P(scale * in) for lattices checked now (sites dealt grid-wide)
-      for (int l = 0; l < nlat; ++l) {
-        if (!s_act[l]) continue;
-        const BatchLat& L = lats[l];
-        const LatState* st = L.state;
-        if (*(volatile const int32_t*)&st->scale_seq != check_id) continue;
-        const float scale = (float)*(volatile const double*)&st->scale;
-        const int mask = run->reimpose ? L.mask : 0;
-        const int n = L.n;
-        const float* in = L.psi[s_cur[l]];
-        float* out = L.psi[s_cur[l] ^ 1];
-        // rows (y, z) dealt to the grid's warps, x along the lanes
-        const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
-        for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n * n; r += nwarps) {
-          const int y0 = r % n, z0 = r / n;
-          for (int x0 = lane; x0 < n; x0 += 32) {
-            int c[3] = {x0, y0, z0};
-            bool neg = false, zero = false;
-            for (int ax = 0; ax < 3; ++ax) {
-              int mode = (mask >> (2 * ax)) & 3;
-              if (mode == 0) continue;
-              int mm = n - 1 - c[ax];
-              if (c[ax] > mm) {
-                c[ax] = mm;
-                neg ^= (mode == 2);
-              } else if (c[ax] == mm && mode == 2) {
-                zero = true;
-              }
-            }
-            out[((size_t)z0 * n + y0) * n + x0] = scale_site(in[site_index(c[0], c[1], c[2], n)], scale, neg, zero);
+      // ---- SCALE: out = P(scale * in) for the lattices checked now, float4 sites dealt grid-wide
+      if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int l = 0; l < nlat; ++l) {
+          v.pre_scale[l] = a;
+          const LatState* st = lats[l].state;
+          if (v.act[l] && *(volatile const int32_t*)&st->scale_seq == check_id) {
+            v.scale[l] = (float)*(volatile const double*)&st->scale;
+            a += (long long)lats[l].n * lats[l].n * (lats[l].n >> 2);
           }
+        }
+        v.pre_scale[nlat] = a;
+      }
+      __syncthreads();
+      {
+        const long long T4 = v.pre_scale[nlat];
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < T4; g += stride) {
+          const int l = find_lattice(v.pre_scale, nlat, g);
+          const BatchLat& L = lats[l];
+          const int n = L.n, n4 = n >> 2;
+          const long long i4 = g - v.pre_scale[l];
+          const long long row = i4 / n4;
+          const int x4 = (int)(i4 - row * n4), y = (int)(row % n), z = (int)(row / n);
+          scale_parity_f4_at(L.psi[v.cur[l]], L.psi[v.cur[l] ^ 1], n, run->reimpose ? L.mask : 0, v.scale[l], x4, y, z);
         }
       }
       if (!grid_barrier(run, err)) return;
       // every block updates its view of the lattices identically
       if (threadIdx.x == 0) {
         for (int l = 0; l < nlat; ++l) {
-          if (!s_act[l]) continue;
+          if (!v.act[l]) continue;
           const LatState* st = lats[l].state;
-          if (*(volatile const int32_t*)&st->scale_seq == check_id) s_cur[l] ^= 1;
-          s_act[l] = *(volatile const int32_t*)&st->active;
-          if (blockIdx.x == 0) lats[l].state->cur = s_cur[l];
+          if (*(volatile const int32_t*)&st->scale_seq == check_id) v.cur[l] ^= 1;
+          v.act[l] = *(volatile const int32_t*)&st->active;
+          if (blockIdx.x == 0) lats[l].state->cur = v.cur[l];
         }
+        build_prefixes<TXT>(v, lats, nlat, w);
       }
       __syncthreads();
       ++check_id;
-      int any = 0;
-      for (int l = 0; l < nlat; ++l) any |= s_act[l];
-      if (t >= t_end || !any) break;
+      if (t >= t_end || v.pre_sums[nlat] == 0) break;
     }
     // ---- STEP: up to the next check, KMAX steps per phase
     const int64_t nc = (t / ce + 1) * ce;
     const int64_t next = nc < t_end ? nc : t_end;
     while (t < next) {
       const int k = (int)((next - t) < KMAX ? (next - t) : KMAX);
-      for (int it = blockIdx.x; it < pre_step[nlat] && ok; it += gridDim.x) {
-        const int l = find_lattice(pre_step, nlat, it);
-        if (!s_act[l]) continue;
-        const int local = it - pre_step[l];
-        if (k == 1)
-          step_item<1>(smem, lats[l], s_cur[l], local, err, ok);
-        else if (k == 2)
-          step_item<(KMAX >= 2 ? 2 : 1)>(smem, lats[l], s_cur[l], local, err, ok);
-        else
-          step_item<KMAX>(smem, lats[l], s_cur[l], local, err, ok);
-      }
-      if (!ok || !grid_barrier(run, err)) return;
+      if (!step_phase<KMAX, TXT>(smem, v, lats, nlat, k, w, err) || !grid_barrier(run, err)) return;
       if (threadIdx.x == 0)
         for (int l = 0; l < nlat; ++l)
-          if (s_act[l]) s_cur[l] ^= 1;
+          if (v.act[l]) v.cur[l] ^= 1;
       __syncthreads();
       t += k;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     run->steps_done = t;
-    for (int l = 0; l < nlat; ++l) lats[l].state->cur = s_cur[l];
+    for (int l = 0; l < nlat; ++l) lats[l].state->cur = v.cur[l];
   }
 }
 
-template <int KMAX>
+template <int KMAX, int TXT>
 size_t batched_smem() {
-  size_t a = tb::Geo<KMAX, kTXB>::SMEM;
-  size_t b = tb::Geo<1, kTXB>::SMEM + 8 * 4 * (tb::Geo<KMAX, kTXB>::THREADS / 32);  // sums item + reduction
+  size_t a = tb::Geo<KMAX, TXT>::SMEM;
+  size_t b = tb::Geo<1, kSumsTXB>::SMEM + 8 * 4 * (tb::Geo<KMAX, TXT>::THREADS / 32);  // sums item + reduction
   return a > b ? a : b;
 }
 
@@ -343,16 +428,17 @@ size_t batched_smem() {
 int batched_max_lattices() { return kMaxLat; }
 
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
-                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf, int zc) {
+                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf) {
   BatchLat& B = *(BatchLat*)host_entry;
   int bw, bh;
   const float* bufs[3] = {psi0, psi1, v};
-  for (int k = 1; k <= 3; ++k) {
-    tma_box(k, kTXB, &bw, &bh);
-    for (int b = 0; b < 3; ++b)
-      if (encode_field_map(&B.step_map[k - 1][b], bufs[b], p.n, bw, bh)) return -1;
-  }
-  tma_box(1, kTXB, &bw, &bh);
+  for (int ti = 0; ti < 2; ++ti)
+    for (int k = 1; k <= 3; ++k) {
+      tma_box(k, ti ? 128 : 64, &bw, &bh);
+      for (int b = 0; b < 3; ++b)
+        if (encode_field_map(&B.step_map[ti][k - 1][b], bufs[b], p.n, bw, bh)) return -1;
+    }
+  tma_box(1, kSumsTXB, &bw, &bh);
   for (int b = 0; b < 3; ++b)
     if (encode_field_map(&B.sums_map[b], bufs[b], p.n, bw, bh)) return -1;
   B.psi[0] = (float*)psi0;
@@ -362,7 +448,6 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
   B.hist = hist;
   B.n = p.n;
   B.mask = mask;
-  B.step_zc = zc < p.n ? zc : p.n;
   B.cur = cur;
   B.hd = p.half_dtau_f;
   B.om6c = p.one_m6c_f;
@@ -374,20 +459,87 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
   return 0;
 }
 
+void batched_patch(void* host_entry, int mask, int cur) {
+  BatchLat& B = *(BatchLat*)host_entry;
+  B.mask = mask;
+  B.cur = cur;
+}
+
 size_t batched_entry_bytes() { return sizeof(BatchLat); }
 size_t batched_run_offset(int count) { return (size_t)count * sizeof(BatchLat); }
 
 void BatchedGraphs::release() {
-  for (int d = 0; d < 4; ++d) {
-    if (exec[d]) cudaGraphExecDestroy(exec[d]);
-    exec[d] = nullptr;
-    grid[d] = 0;
+  for (int t = 0; t < 2; ++t)
+    for (int d = 0; d < 4; ++d) {
+      if (exec[t][d]) cudaGraphExecDestroy(exec[t][d]);
+      exec[t][d] = nullptr;
+      grid[t][d] = 0;
+    }
+}
+
+int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* err, BatchedGraphs* graphs) {
+  depth = depth < 1 ? 1 : (depth > 3 ? 3 : depth);
+  const int ti = tile_x == 128 ? 1 : 0;
+  if (graphs->exec[ti][depth]) return 0;
+  // capture the cooperative launch once: grid = resident blocks of the whole device
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const BatchLat* tab = (const BatchLat*)dev_table;
+  BatchRun* drun = (BatchRun*)((char*)dev_table + batched_run_offset(count));
+  void* args[3] = {(void*)&tab, (void*)&drun, (void*)&err};
+  auto capture = [&](auto kern, int threads, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem, cs);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs->exec[ti][depth], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      graphs->exec[ti][depth] = nullptr;
+      return e;
+    }
+    graphs->grid[ti][depth] = grid;
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (ti == 0) {
+    if (depth == 1)
+      e = capture(k_batched<1, 64>, tb::Geo<1, 64>::THREADS, batched_smem<1, 64>());
+    else if (depth == 2)
+      e = capture(k_batched<2, 64>, tb::Geo<2, 64>::THREADS, batched_smem<2, 64>());
+    else
+      e = capture(k_batched<3, 64>, tb::Geo<3, 64>::THREADS, batched_smem<3, 64>());
+  } else {
+    if (depth == 1)
+      e = capture(k_batched<1, 128>, tb::Geo<1, 128>::THREADS, batched_smem<1, 128>());
+    else if (depth == 2)
+      e = capture(k_batched<2, 128>, tb::Geo<2, 128>::THREADS, batched_smem<2, 128>());
+    else
+      e = capture(k_batched<3, 128>, tb::Geo<3, 128>::THREADS, batched_smem<3, 128>());
   }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return (int)e;
+  }
+  return 0;
 }
 
 int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_start, int64_t t_end, int skip_first,
-                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int32_t* err,
-                   cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done, int* grid_out) {
+                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int tile_x,
+                   int tune_passes, int32_t* err, cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done,
+                   int* grid_out) {
   BatchRun run{};
   run.max_steps = max_steps;
   run.t_start = t_start;
@@ -400,56 +552,16 @@ int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_star
   run.reimpose = reimpose;
   run.depth = depth;
   run.nlat = count;
+  run.tune_passes = tune_passes;
   BatchRun* drun = (BatchRun*)((char*)dev_table + batched_run_offset(count));
   cudaMemcpyAsync(drun, &run, sizeof(run), cudaMemcpyHostToDevice, st);
+  int e = batched_prepare(dev_table, count, depth, tile_x, err, graphs);
+  if (e) return e;
   depth = depth < 1 ? 1 : (depth > 3 ? 3 : depth);
-  if (!graphs->exec[depth]) {
-    // capture the cooperative launch once: grid = resident blocks of the whole device
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const BatchLat* tab = (const BatchLat*)dev_table;
-    void* args[3] = {(void*)&tab, (void*)&drun, (void*)&err};
-    auto capture = [&](auto kern, int threads, size_t smem) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-      if (per_sm < 1) return cudaErrorInvalidConfiguration;
-      const int grid = per_sm * sms;
-      cudaStream_t cs;
-      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-      if (e != cudaSuccess) return e;
-      cudaGraph_t g = nullptr;
-      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        cudaError_t el = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem, cs);
-        e = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = el;
-      }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs->exec[depth], g, 0);
-      if (g) cudaGraphDestroy(g);
-      cudaStreamDestroy(cs);
-      if (e != cudaSuccess) {
-        graphs->exec[depth] = nullptr;
-        return e;
-      }
-      graphs->grid[depth] = grid;
-      return cudaSuccess;
-    };
-    cudaError_t e;
-    if (depth == 1)
-      e = capture(k_batched<1>, tb::Geo<1, kTXB>::THREADS, batched_smem<1>());
-    else if (depth == 2)
-      e = capture(k_batched<2>, tb::Geo<2, kTXB>::THREADS, batched_smem<2>());
-    else
-      e = capture(k_batched<3>, tb::Geo<3, kTXB>::THREADS, batched_smem<3>());
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return (int)e;
-    }
-  }
-  *grid_out = graphs->grid[depth];
-  cudaError_t e = cudaGraphLaunch(graphs->exec[depth], st);
-  if (e != cudaSuccess) return (int)e;
+  const int ti = tile_x == 128 ? 1 : 0;
+  *grid_out = graphs->grid[ti][depth];
+  cudaError_t ce = cudaGraphLaunch(graphs->exec[ti][depth], st);
+  if (ce != cudaSuccess) return (int)ce;
   cudaMemcpyAsync(steps_done, &drun->steps_done, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   return 0;
 }

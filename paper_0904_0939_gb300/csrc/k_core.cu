@@ -698,56 +698,8 @@ __global__ void __launch_bounds__(256) k_scale_parity_f4(const float* __restrict
   }
   const int x4 = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
   if (sw && (x4 | y | z) == 0) sw->cur = out_idx;
-  const int n4 = n >> 2;
-  if (x4 >= n4 || y >= n) return;
-  const int mx = mask & 3, my = (mask >> 2) & 3, mz = (mask >> 4) & 3;
-  int ys = y, zs = z;
-  bool neg = false, zero = false;
-  if (my) {
-    const int mm = n - 1 - y;
-    if (y > mm) {
-      ys = mm;
-      neg ^= (my == 2);
-    } else if (y == mm && my == 2) {
-      zero = true;
-    }
-  }
-  if (mz) {
-    const int mm = n - 1 - z;
-    if (z > mm) {
-      zs = mm;
-      neg ^= (mz == 2);
-    } else if (z == mm && mz == 2) {
-      zero = true;
-    }
-  }
-  const float* row = in + ((size_t)zs * n + ys) * n;
-  const float4 a = *reinterpret_cast<const float4*>(row + 4 * x4);
-  float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {0.f, 0.f, 0.f, 0.f};
-  if (mx) {
-    const float4 b = *reinterpret_cast<const float4*>(row + (n - 4 - 4 * x4));
-    mv[0] = b.w;  // mirror of site 4 x4 + 0 is n - 1 - 4 x4
-    mv[1] = b.z;
-    mv[2] = b.y;
-    mv[3] = b.x;
-  }
-  float o[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int x = 4 * x4 + c, mm = n - 1 - x;
-    bool ng = neg, zc = zero;
-    float src = av[c];
-    if (mx) {
-      if (x > mm) {
-        src = mv[c];
-        ng ^= (mx == 2);
-      } else if (x == mm && mx == 2) {
-        zc = true;
-      }
-    }
-    o[c] = scale_site(src, scale, ng, zc);
-  }
-  *reinterpret_cast<float4*>(out + ((size_t)z * n + y) * n + 4 * x4) = make_float4(o[0], o[1], o[2], o[3]);
+  if (x4 >= (n >> 2) || y >= n) return;
+  scale_parity_f4_at(in, out, n, mask, scale, x4, y, z);
 }
 
 static int grid_for(size_t total, int threads) {

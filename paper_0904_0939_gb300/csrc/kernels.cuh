@@ -118,25 +118,34 @@ int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const 
 size_t batched_workspace_bytes(const fdtd_lattice_desc* d, int count);
 int batched_max_lattices();
 size_t batched_entry_bytes();
-// zc: z-planes per step item (the tile is 64 x 16 sites in x-y).
+// Encodes the lattice's tensor maps (both tile widths, every depth, the
+// sums box) into its table entry; batched_patch updates the fields that
+// change between launches.
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
-                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf, int zc);
-// Instantiated CUDA graphs of the persistent launch, one per depth, owned
-// by the handle (the kernel's arguments are the fixed table, run record and
-// error flag, so a graph is reused by every evolve of the handle).
+                 LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf);
+void batched_patch(void* host_entry, int mask, int cur);
+// Instantiated CUDA graphs of the persistent launch, one per (tile width,
+// depth), owned by the handle (the kernel's arguments are the fixed table,
+// run record and error flag, so a graph is reused by every evolve).
 struct BatchedGraphs {
-  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
-  int grid[4] = {0, 0, 0, 0};
+  cudaGraphExec_t exec[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+  int grid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   void release();
 };
+// Capture and instantiate the graph of (depth, tile_x) if not done yet.
+int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* err, BatchedGraphs* graphs);
 // One cooperative launch (through the cached graph) that runs every check
 // and step of every lattice from step t_start to t_end (a multiple of
 // check_every, or max_steps): the check at t_start is made unless
 // skip_first, the one at t_end always; checks are numbered from check0.
-// Returns 0 or a cudaError_t value.  *steps_done is written asynchronously.
+// With tune_passes > 0 it instead runs that many update passes of `depth`
+// steps from the current fields into the spare ones (the state does not
+// advance).  Returns 0 or a cudaError_t value.  *steps_done is written
+// asynchronously.
 int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_start, int64_t t_end, int skip_first,
-                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int32_t* err,
-                   cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done, int* grid_out);
+                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int tile_x,
+                   int tune_passes, int32_t* err, cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done,
+                   int* grid_out);
 
 // Lattice sums S0, SH, Sr, SV into per-block partials; returns block count.
 template <typename T>

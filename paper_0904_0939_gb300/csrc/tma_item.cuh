@@ -641,12 +641,16 @@ __host__ __device__ inline int sums_items(int n) { return sums_items_of(n, n); }
 
 // Lattice sums over the tile interior, planes [z0, z1) of the mapped field,
 // whose plane j is the lattice's plane j + zoff (zoff != 0 for a z-slab with
-// halo planes); the block's four totals (FP64) go to dst[0..3].  Returns
+// halo planes); the block's four totals (FP64) go to dst[0..3].  With
+// zc > 0 the planes are cut at the multiples of zc (z0 must be one) and
+// each piece's totals go to dst + c * dst_stride (c = 0, 1, ... in z order):
+// several consecutive sums items of one tile column in one pipeline run,
+// each piece's totals equal to those of a separate item over it.  Returns
 // false if a bounded wait expired.
 template <int TXT>
 __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, int n, int x0,
                               int y0, int z0, int z1, float a, float kfac, double* __restrict__ dst, int32_t* err,
-                              int zoff = 0) {
+                              int zoff = 0, int zc = 0, long long dst_stride = 0) {
   using G = Geo<1, TXT>;
   constexpr int R = G::R;
   constexpr int C4 = G::C4, BW = G::BW;
@@ -668,6 +672,26 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
 #pragma unroll
   for (int i = 0; i < 4; ++i) px[i] = coord_f32(xg + i, n, a);
   Kahan s0, sh, sr, sv;
+  // fixed-order block reduction of the four accumulators into d[0..3]
+  // (every thread; the caller's last barrier separates it from the
+  // previous reduction's reads)
+  double* red = (double*)(smem + G::RED_OFF);
+  auto reduce_to = [&](double* d) {
+    double v4[4] = {s0.value(), sh.value(), sr.value(), sv.value()};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], off);
+    if (lane == 0 && tid < G::THREADS)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[(tid >> 5) * 4 + q] = v4[q];
+    __syncthreads();
+    if (tid < 4) {
+      double acc = 0.0;
+      for (int w = 0; w < G::THREADS / 32; ++w) acc += red[w * 4 + tid];
+      d[tid] = acc;
+    }
+  };
   Pipe<1, TXT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
@@ -719,24 +743,17 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
       return false;
     }
     sj = slot_add<R>(sj, 1);
+    if (zc > 0 && j < j1 && (j + 1) % zc == 0) {  // a piece ends inside the run
+      reduce_to(dst);
+      dst += dst_stride;
+      s0 = Kahan{};
+      sh = Kahan{};
+      sr = Kahan{};
+      sv = Kahan{};
+    }
   }
   sm.flush();
-  // fixed-order block reduction
-  double v4[4] = {s0.value(), sh.value(), sr.value(), sv.value()};
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], off);
-  double* red = (double*)(smem + G::RED_OFF);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) red[(tid >> 5) * 4 + q] = v4[q];
-  __syncthreads();
-  if (tid < 4) {
-    double acc = 0.0;
-    for (int w = 0; w < G::THREADS / 32; ++w) acc += red[w * 4 + tid];
-    dst[tid] = acc;
-  }
+  reduce_to(dst);
   pp.finish(false);
   __syncthreads();
   return true;

@@ -57,10 +57,10 @@ def small_batch():
     return lats, pots, masks, seeds
 
 
-@pytest.mark.parametrize("depth", [1, 2, 3])
-def test_batched_bit_identical_to_separate_runs(fd, depth):
+@pytest.mark.parametrize("depth,tile", [(1, 64), (2, 64), (3, 64), (1, 128), (2, 128), (3, 128)])
+def test_batched_bit_identical_to_separate_runs(fd, depth, tile):
     lats, pots, masks, seeds = small_batch()
-    a = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=depth)
+    a = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=depth, tile_x=tile)
     b = run_batch(fd, lats, pots, masks, seeds, False, 3000, temporal_depth=depth)
     for (pa, oa), (pb, ob) in zip(a, b):
         assert oa["steps"] == ob["steps"] and oa["converged"] == ob["converged"]
@@ -68,16 +68,15 @@ def test_batched_bit_identical_to_separate_runs(fd, depth):
         np.testing.assert_array_equal(pa, pb)
 
 
-def test_batched_autotuned_slices_match_one_launch(fd):
-    """With autotuning the first batched evolve runs its (depth, z-chunk)
-    candidates on slices of 2 x check_every steps of the run itself and
-    finishes with the fastest, each launch a cooperative kernel in a CUDA
-    graph: the result equals one launch at a fixed configuration bit for
-    bit, lattices that converge during the tuning slices stay retired, and
+def test_batched_autotuned_launch_matches_a_fixed_configuration(fd):
+    """With autotuning the first batched evolve times its (depth, tile
+    width) candidates on update passes into the spare fields, which leave
+    the state where it was, and then runs the whole evolve in one launch:
+    the result equals one launch at a fixed configuration bit for bit, and
     the second evolve of the same sizes launches once with the cached
     choice."""
     lats, pots, masks, seeds = small_batch()
-    fixed = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=2, zchunk=32, check_every=50)
+    fixed = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=2, tile_x=64, check_every=50)
     kw = dict(check_every=50, tol=1e-6, tol_relative=1, batched=1)
     s = fd.Solver([fd.Lattice(l.n, l.length, fd.F32) for l in lats], fd.default_options(**kw))
     for rep in range(2):
@@ -87,17 +86,38 @@ def test_batched_autotuned_slices_match_one_launch(fd):
         s.reset_stats()
         s.evolve(3000)
         launches = s.stats()["graph_launches"]
-        assert launches == (1 if rep else 10) or (rep == 0 and 1 < launches <= 10)
+        # six candidates, each launched untimed and timed, then the run; later: the run only
+        assert launches == (1 if rep else 13), (rep, launches)
         for i, (pf, of) in enumerate(fixed):
             o = s.last_check(lat=i)
             assert o["steps"] == of["steps"] and o["energy"] == of["energy"], (rep, i)
             np.testing.assert_array_equal(s.get_psi(lat=i, dtype=np.float32), pf)
-            h = s.history(lat=i)  # the check records of the persistent launch, across its slices
+            h = s.history(lat=i)  # the check records of the persistent launch
             assert len(h) == o["checks"] and h[-1, 0] == o["steps"] and h[-1, 1] == o["energy"]
             assert np.all(np.diff(h[:, 0]) > 0)
     depth, zc = s.tuned_config()
-    assert depth in (1, 2, 3) and zc in (16, 32, 64)
+    tx, ty = s.tuned_kernel()
+    assert depth in (1, 2, 3) and zc == -1 and tx in (64, 128) and ty == 16
     s.close()
+
+
+def test_batched_lattices_converging_at_different_steps(fd):
+    """Lattices that converge early drop out of the cost line of the update
+    passes, which is cut anew after every check: eight lattices of the C4
+    mix's sizes with tolerances that retire them hundreds of steps apart end
+    bit-identical to separate runs, at both tile widths."""
+    lats = [wl.Lattice(n, 0.25 * n) for n in (48, 64, 96, 48, 128, 64, 160, 96)]
+    pots = [wl.harmonic(l.n, l.length, w) for l, w in zip(lats, (1.0, 1.7, 0.6, 2.0, 0.8, 1.2, 1.0, 1.5))]
+    masks = [0, wl.ODD_X, wl.SYMMETRIC_ALL, wl.ODD_Z, 0, wl.ODD_Y, 0, wl.ODD_X]
+    seeds = list(range(8))
+    b = run_batch(fd, lats, pots, masks, seeds, False, 1500, temporal_depth=3)
+    steps = {o["steps"] for _, o in b}
+    assert len(steps) > 1  # the lattices retire at different checks
+    for tile in (64, 128):
+        a = run_batch(fd, lats, pots, masks, seeds, True, 1500, temporal_depth=3, tile_x=tile)
+        for (pa, oa), (pb, ob) in zip(a, b):
+            assert oa["steps"] == ob["steps"] and oa["energy"] == ob["energy"], tile
+            np.testing.assert_array_equal(pa, pb)
 
 
 def test_batched_fixed_steps_match_oracle(fd, orc):

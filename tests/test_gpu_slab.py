@@ -4,10 +4,11 @@ each driven through the fdtd_slab_* C ABI, against the whole-lattice FP32
 solver (same stencil arithmetic; psi to 1e-6 of max |psi| and E, <r^2> to
 1e-7: the slab sums share the whole-lattice sums' FP32 per-site arithmetic
 but cut the planes into other partial sums, so the energies and the
-renormalisation factors may differ by a rounding) and the FP64 oracle (2e-5, the FP32 tolerance).  The cases
-cover one slab (both lattice faces in one buffer), two and three slabs, the
-thinnest slabs (nz_own = halo), passes of depth 1, 2 and 3, partial passes
-before a check, and the x / y symmetry masks."""
+renormalisation factors may differ by a rounding) and the FP64 oracle (2e-5,
+the FP32 tolerance).  The cases cover one slab (both lattice faces in one
+buffer), two and three slabs, the thinnest slabs (nz_own = halo), passes of
+depth 1, 2 and 3, partial passes before a check, and the x / y symmetry
+masks."""
 import numpy as np
 import pytest
 
