@@ -43,6 +43,30 @@ __device__ __forceinline__ long long balanced_plane(long long u, int n, int wcos
   o = o < 0 ? 0 : (o > n ? n : o);
   return c * n + o;
 }
+// One pipeline item.  The 128-wide depth-3 items (768 threads, at most 80
+// registers each) run out of line, so that the partition's state does not
+// compete with the pipeline for registers (it is saved once per item); the
+// others, with registers to spare, stay inline.
+template <int K, int TXT>
+__device__ __noinline__ bool step_item_ool(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
+                                           float* out, int n, int x0, int y0, int z0, int z1, float half_dtau,
+                                           float one_m6c, float cc, int32_t* err, int nz, int zlo, int zhi) {
+  return tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
+                               zhi);
+}
+template <int K, int TXT>
+__device__ __forceinline__ bool step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
+                                          float* out, int n, int x0, int y0, int z0, int z1, float half_dtau,
+                                          float one_m6c, float cc, int32_t* err, int nz = -1, int zlo = 0,
+                                          int zhi = -1) {
+  if constexpr (TXT == 128 && K == 3)
+    return step_item_ool<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
+                                 zhi);
+  else
+    return tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
+                                 zhi);
+}
+
 template <int K, int TXT>
 __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                     const __grid_constant__ CUtensorMap map_v,
@@ -87,8 +111,8 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   while (r < rend) {
     const int t = (int)(r / top), z0 = (int)(r - (long long)t * top);
     const int z1 = (int)min((long long)top, z0 + (rend - r));
-    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, base + z0,
-                               base + z1, half_dtau, one_m6c, cc, err))
+    if (!step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, base + z0, base + z1,
+                           half_dtau, one_m6c, cc, err))
       return;
     r += z1 - z0;
   }
@@ -118,8 +142,8 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_slab(const __grid
   while (r < rend) {
     const int t = (int)(r / nzo), z0 = (int)(r - (long long)t * nzo);
     const int z1 = (int)min((long long)nzo, z0 + (rend - r));
-    if (!tma_step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, zbase + z0,
-                               zbase + z1, half_dtau, one_m6c, cc, err, nzbuf, zlo, zhi))
+    if (!step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, zbase + z0,
+                           zbase + z1, half_dtau, one_m6c, cc, err, nzbuf, zlo, zhi))
       return;
     r += z1 - z0;
   }
