@@ -797,6 +797,9 @@ def main():
         torch.cuda.synchronize()
 
     clocks = Clocks(local)
+    # a profiler started with profiling off (ncu --profile-from-start off)
+    # collects exactly the timed steps' launches
+    torch.cuda.profiler.start()
     tot_ms, tot_upd, tot_launch = 0.0, 0, 0
     fine = {"ms": 0.0, "bytes": 0.0, "upd": 0, "launches": 0, "timed": 0}
     tot = None
@@ -818,6 +821,7 @@ def main():
                        ("launches", "fine_launches"), ("timed", "fine_timed")):
             fine[k] += tot[src]
     barrier()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
 
     # end to end: host-resident V, copies and read-back inside the region

@@ -22,7 +22,9 @@ std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int, bool, bo
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
   const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
-  const bool f4 = L.d.precision == FDTD_F32 && L.d.n % 4 == 0;  // the direct kernel applies
+  // the direct kernel applies (FP32 or BF16 storage, n % 4 == 0)
+  const bool f4 = (L.d.precision == FDTD_F32 || L.d.precision == FDTD_BF16) && L.d.n % 4 == 0;
+  const bool bf16 = L.d.precision == FDTD_BF16;
   L.plain = false;
   L.direct = false;
   if (!tma) {
@@ -77,8 +79,12 @@ void choose_config(fdtd_context* c, Lat& L) {
   {
     double rate = time_it(
         [&]() {
-          launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p,
-                                 nullptr, c->st);
+          if (bf16)
+            launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
+                                           (const float*)L.v, L.p, nullptr, c->st);
+          else
+            launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p,
+                                   nullptr, c->st);
         },
         1);
     best = rate;
@@ -89,8 +95,12 @@ void choose_config(fdtd_context* c, Lat& L) {
   {
     double rate = time_it(
         [&]() {
-          launch_direct_f32((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, nullptr,
-                            c->st);
+          if (bf16)
+            launch_direct<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
+                                         (const float*)L.v, L.p, nullptr, c->st);
+          else
+            launch_direct<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p,
+                                 nullptr, c->st);
         },
         1);
     if (rate > best) {
@@ -185,6 +195,9 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
       else
         launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
                                c->st);
+    } else if (L.direct) {
+      launch_direct<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
+                                   (const float*)L.v, L.p, active, c->st);
     } else {
       launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
                                      (const float*)L.v, L.p, active, c->st);

@@ -154,22 +154,54 @@ template void launch_step_f32<float>(const float*, float*, const float*, const P
 template void launch_step_f32<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
                                              const int32_t*, cudaStream_t);
 
-// ------------------------------------------------------------------ direct FP32 stencil
+// ------------------------------------------------------------------ direct stencil
 // One thread per four consecutive x sites (n % 4 == 0) and every neighbour an
 // independent load instead of a z-march: on lattices too small to give a
 // z-marching grid many planes per block, each thread's loads no longer wait
-// on one another plane by plane.  The per-site arithmetic is k_step_f32's
-// (same bits).
-template <bool P>
-__global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ in, float* __restrict__ out,
-                                                    const float* __restrict__ v, int n, float half_dtau,
-                                                    float one_m6c, float cc, const int32_t* __restrict__ active) {
+// on one another plane by plane.  FP32 or BF16 storage (four BF16 sites are
+// one 8-byte load); the per-site arithmetic and the rounding of the stored
+// value are k_step_f32's (same bits).
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+  __device__ __forceinline__ static float4 ld(const float* base, size_t q) {
+    return __ldg(reinterpret_cast<const float4*>(base) + q);
+  }
+  __device__ __forceinline__ static void st(float* base, size_t q, float4 o) {
+    reinterpret_cast<float4*>(base)[q] = o;
+  }
+};
+template <>
+struct Quad<__nv_bfloat16> {
+  __device__ __forceinline__ static float4 ld(const __nv_bfloat16* base, size_t q) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(base) + q);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat16* base, size_t q, float4 o) {
+    __nv_bfloat162 a, b;
+    a.x = Store<__nv_bfloat16>::from(o.x);
+    a.y = Store<__nv_bfloat16>::from(o.y);
+    b.x = Store<__nv_bfloat16>::from(o.z);
+    b.y = Store<__nv_bfloat16>::from(o.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned*>(&a);
+    u.y = *reinterpret_cast<const unsigned*>(&b);
+    reinterpret_cast<uint2*>(base)[q] = u;
+  }
+};
+
+template <typename T, bool P>
+__global__ void __launch_bounds__(256) k_direct(const T* __restrict__ in, T* __restrict__ out,
+                                                const float* __restrict__ v, int n, float half_dtau, float one_m6c,
+                                                float cc, const int32_t* __restrict__ active) {
   pdl_wait();
   pdl_trigger();
   if (active && *active == 0) return;
   const int n4 = n >> 2;
   const size_t total = (size_t)n4 * n * n;
-  const float4* in4 = reinterpret_cast<const float4*>(in);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   auto wrap = [n](int q) { return q < 0 ? q + n : (q >= n ? q - n : q); };
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
@@ -183,18 +215,18 @@ __global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ in
       } else if ((unsigned)yy >= (unsigned)n || (unsigned)zz >= (unsigned)n) {
         return zero4;
       }
-      return __ldg(in4 + ((size_t)zz * n + yy) * n4 + x4);
+      return Quad<T>::ld(in, ((size_t)zz * n + yy) * n4 + x4);
     };
-    const float4 c = __ldg(in4 + q);
+    const float4 c = Quad<T>::ld(in, q);
     const float4 ym = at(y - 1, z), yp = at(y + 1, z), zm = at(y, z - 1), zp = at(y, z + 1);
-    const float* rp = in + row * n;
+    const T* rp = in + row * n;
     float xl, xr;
     if constexpr (P) {
-      xl = __ldg(rp + (x4 == 0 ? n - 1 : 4 * x4 - 1));
-      xr = __ldg(rp + (x4 == n4 - 1 ? 0 : 4 * x4 + 4));
+      xl = Store<T>::ld(rp + (x4 == 0 ? n - 1 : 4 * x4 - 1));
+      xr = Store<T>::ld(rp + (x4 == n4 - 1 ? 0 : 4 * x4 + 4));
     } else {
-      xl = x4 > 0 ? __ldg(rp + 4 * x4 - 1) : 0.f;
-      xr = x4 < n4 - 1 ? __ldg(rp + 4 * x4 + 4) : 0.f;
+      xl = x4 > 0 ? Store<T>::ld(rp + 4 * x4 - 1) : 0.f;
+      xr = x4 < n4 - 1 ? Store<T>::ld(rp + 4 * x4 + 4) : 0.f;
     }
     const float4 vv = __ldg(reinterpret_cast<const float4*>(v) + q);
     auto site = [&](float cv, float s, float vs) { return update_f32(cv, s, coef_f32(vs, half_dtau, one_m6c), cc); };
@@ -203,7 +235,7 @@ __global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ in
     o.y = site(c.y, nbr_sum(c.x, c.z, ym.y, yp.y, zm.y, zp.y), vv.y);
     o.z = site(c.z, nbr_sum(c.y, c.w, ym.z, yp.z, zm.z, zp.z), vv.z);
     o.w = site(c.w, nbr_sum(c.z, xr, ym.w, yp.w, zm.w, zp.w), vv.w);
-    reinterpret_cast<float4*>(out)[q] = o;
+    Quad<T>::st(out, q, o);
   }
 }
 
@@ -213,10 +245,18 @@ static int grid_f4(int n) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 64));
 }
 
+template <typename T>
+void launch_direct(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st) {
+  launch_pdl(p.periodic ? k_direct<T, true> : k_direct<T, false>, dim3(grid_f4(p.n)), dim3(256), 0, st, in, out, v,
+             p.n, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
+}
+template void launch_direct<float>(const float*, float*, const float*, const Params&, const int32_t*, cudaStream_t);
+template void launch_direct<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, const float*, const Params&,
+                                           const int32_t*, cudaStream_t);
+
 void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, const int32_t* active,
                        cudaStream_t st) {
-  launch_pdl(p.periodic ? k_direct_f32<true> : k_direct_f32<false>, dim3(grid_f4(p.n)), dim3(256), 0, st, in, out, v,
-             p.n, p.half_dtau_f, p.one_m6c_f, p.c_f, active);
+  launch_direct<float>(in, out, v, p, active, st);
 }
 
 // One whole FP32 adjoint step, four x sites per thread (n % 4 == 0), no

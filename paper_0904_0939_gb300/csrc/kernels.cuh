@@ -241,6 +241,8 @@ void launch_adjoint_stencil(const T* u, const T* lam, T* lam_out, const void* v,
                             cudaStream_t st);
 // FP32 one-step stencil without z-march, four x sites per thread
 // (n % 4 == 0): launch_step_f32's step, same bits
+template <typename T>
+void launch_direct(const T* in, T* out, const float* v, const Params& p, const int32_t* active, cudaStream_t st);
 void launch_direct_f32(const float* in, float* out, const float* v, const Params& p, const int32_t* active,
                        cudaStream_t st);
 // one whole FP32 adjoint step the same way (n % 4 == 0): u = B lam on load,

@@ -386,6 +386,28 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
 
 
+@pytest.mark.parametrize("n", [32, 68, 132])
+def test_bf16_direct_kernel_matches_zmarch(fd, n):
+    """BF16 storage: the direct four-site kernel (stencil_kernel 2), the
+    z-marching kernel (stencil_kernel 1) and the autotuner's choice give the
+    same bits after 100 steps with checks (same FP32 arithmetic, same BF16
+    rounding of each stored value)."""
+    L = 0.3 * n
+    rng = np.random.default_rng(n + 1)
+    v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
+    outs = {}
+    for name, kw in (("plain", dict(stencil_kernel=1)), ("direct", dict(stencil_kernel=2)), ("auto", {})):
+        s = solver(fd, n, L, fd.BF16, check_every=50, **kw)
+        s.set_potential(v)
+        s.init_symmetric(17, wl.ODD_Y)
+        s.evolve(100)
+        outs[name] = (s.get_psi(dtype=np.float32), s.last_check()["energy"])
+        s.close()
+    for name in ("direct", "auto"):
+        np.testing.assert_array_equal(outs[name][0], outs["plain"][0], err_msg=name)
+        assert outs[name][1] == outs["plain"][1]
+
+
 # ------------------------------------------------------------------ evolve graph
 
 @pytest.mark.parametrize("prec,n,kw", [("F32", 64, {}), ("F32", 36, {}), ("F32", 48, dict(temporal_depth=3)),
