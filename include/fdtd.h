@@ -418,6 +418,14 @@ FDTD_API int fdtd_slab_destroy(fdtd_slab s);
  * the exchange).  Asynchronous on the slab's stream. */
 FDTD_API int fdtd_slab_steps(fdtd_slab s, int src, int depth);
 
+/* The same steps for own planes z_begin .. z_end - 1 only (0-based within
+ * the own planes; 0 <= z_begin <= z_end <= nz_own).  The paper's inside-out
+ * order (Sec. V): update the planes the neighbours need first, start their
+ * exchange, then update the interior while the messages are in flight.  The
+ * result equals fdtd_slab_steps over any cover of the own planes by
+ * disjoint ranges. */
+FDTD_API int fdtd_slab_steps_range(fdtd_slab s, int src, int depth, int z_begin, int z_end);
+
 /* Partial sums of Eq. energysum over the own planes of field `src`:
  * sums4 = {S0, SH, Sr, SV} with r measured from the lattice centre (the
  * halo planes adjacent to the own planes must be current), formed with the

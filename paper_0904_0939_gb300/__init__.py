@@ -86,7 +86,8 @@ EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_
             "fdtd_tuned_kernel",
             "fdtd_check_history", "fdtd_save_psi", "fdtd_load_psi", "fdtd_bounds_violations",
             "fdtd_snapshot_save", "fdtd_snapshot_load", "fdtd_project_out", "fdtd_combine",
-            "fdtd_slab_workspace_size", "fdtd_slab_create", "fdtd_slab_destroy", "fdtd_slab_steps", "fdtd_slab_sums",
+            "fdtd_slab_workspace_size", "fdtd_slab_create", "fdtd_slab_destroy", "fdtd_slab_steps",
+            "fdtd_slab_steps_range", "fdtd_slab_sums",
             "fdtd_slab_scale", "fdtd_check_sums"]
 
 

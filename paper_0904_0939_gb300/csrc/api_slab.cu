@@ -134,15 +134,23 @@ int fdtd_slab_destroy(fdtd_slab s) {
   return FDTD_OK;
 }
 
-int fdtd_slab_steps(fdtd_slab s, int src, int depth) {
+int fdtd_slab_steps_range(fdtd_slab s, int src, int depth, int z_begin, int z_end) {
   if (!s || (src != 0 && src != 1) || depth < 1 || depth > s->halo)
     return slab_fail("slab_steps: bad handle, source index or depth (1 <= depth <= halo)");
+  if (z_begin < 0 || z_end > s->nzo || z_begin > z_end)
+    return slab_fail("slab_steps_range: need 0 <= z_begin <= z_end <= nz_own");
+  if (z_begin == z_end) return FDTD_OK;
   // planes below the lattice's bottom face and above its top face stay zero
   const int zlo = s->z_first == 0 ? s->halo : 0;
   const int zhi = s->z_first + s->nzo == s->n ? s->halo + s->nzo : s->nzbuf;
-  launch_step_slab(s->maps[depth - 1][src], s->maps[depth - 1][2], s->psi[1 - src], s->p, depth, s->nzo, s->halo,
-                   s->nzbuf, zlo, zhi, s->flags + 1, s->st);
+  launch_step_slab(s->maps[depth - 1][src], s->maps[depth - 1][2], s->psi[1 - src], s->p, depth, z_end - z_begin,
+                   s->halo + z_begin, s->nzbuf, zlo, zhi, s->flags + 1, s->st);
   return slab_cuda("slab_steps");
+}
+
+int fdtd_slab_steps(fdtd_slab s, int src, int depth) {
+  if (!s) return slab_fail("slab_steps: null handle");
+  return fdtd_slab_steps_range(s, src, depth, 0, s->nzo);
 }
 
 int fdtd_slab_sums(fdtd_slab s, int src, double* sums4, int mem_kind) {

@@ -35,11 +35,12 @@ lib.fdtd_slab_create.argtypes = [_i32, _i32, _i32, _i32, _d, _d, _d, _vp, _vp, _
                                  ctypes.POINTER(_vp)]
 lib.fdtd_slab_destroy.argtypes = [_vp]
 lib.fdtd_slab_steps.argtypes = [_vp, _i32, _i32]
+lib.fdtd_slab_steps_range.argtypes = [_vp, _i32, _i32, _i32, _i32]
 lib.fdtd_slab_sums.argtypes = [_vp, _i32, ctypes.POINTER(_d), _i32]
 lib.fdtd_slab_scale.argtypes = [_vp, _i32, _i32, _d, _i32]
 lib.fdtd_check_sums.argtypes = [ctypes.POINTER(_d), _d, _i32, _d, ctypes.POINTER(_d)]
-for _f in ("fdtd_slab_workspace_size", "fdtd_slab_create", "fdtd_slab_destroy", "fdtd_slab_steps", "fdtd_slab_sums",
-           "fdtd_slab_scale", "fdtd_check_sums"):
+for _f in ("fdtd_slab_workspace_size", "fdtd_slab_create", "fdtd_slab_destroy", "fdtd_slab_steps",
+           "fdtd_slab_steps_range", "fdtd_slab_sums", "fdtd_slab_scale", "fdtd_check_sums"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -113,8 +114,11 @@ class Slab:
     def own(self, buf: int):
         return self.psi[buf][self.halo:self.halo + self.nz_own]
 
-    def steps(self, src: int, depth: int):
-        _check(lib.fdtd_slab_steps(self.handle, src, depth))
+    def steps(self, src: int, depth: int, z_begin: int = 0, z_end: int | None = None):
+        """`depth` steps from field src into the other field's own planes
+        z_begin .. z_end - 1 (default: all own planes)."""
+        z_end = self.nz_own if z_end is None else z_end
+        _check(lib.fdtd_slab_steps_range(self.handle, src, depth, z_begin, z_end))
 
     def sums(self, src: int) -> np.ndarray:
         out = (ctypes.c_double * 4)()
@@ -150,6 +154,12 @@ class LocalComm:
             lower.psi[buf][h + lower.nz_own:h + lower.nz_own + h].copy_(upper.psi[buf][h:2 * h])
             upper.psi[buf][0:h].copy_(lower.psi[buf][lower.nz_own:lower.nz_own + h])
 
+    def exchange_start(self, buf: int):
+        self.exchange(buf)  # copies on the slabs' stream, in order
+
+    def exchange_wait(self):
+        pass
+
     def allreduce(self, parts):
         return np.sum(np.asarray(parts), axis=0)
 
@@ -163,7 +173,11 @@ class TorchComm:
         self.slabs = [slab]
         self.rank, self.world, self.group = rank, world, group
 
-    def exchange(self, buf: int):
+    def exchange_start(self, buf: int):
+        """Post the sends of this slab's boundary planes of field `buf` and
+        the receives into its halo planes; on NCCL they run on the
+        communicator's stream after the work already queued on the current
+        stream, so kernels queued afterwards overlap them."""
         import torch.distributed as dist
 
         s = self.slabs[0]
@@ -171,14 +185,21 @@ class TorchComm:
         f = s.psi[buf]
         ops = []
         if self.rank > 0:  # below: send my first own planes, receive its last ones into my lower halo
-            ops.append(dist.P2POp(dist.isend, f[h:2 * h].contiguous(), self.rank - 1, self.group))
+            ops.append(dist.P2POp(dist.isend, f[h:2 * h], self.rank - 1, self.group))
             ops.append(dist.P2POp(dist.irecv, f[0:h], self.rank - 1, self.group))
         if self.rank < self.world - 1:
-            ops.append(dist.P2POp(dist.isend, f[k:k + h].contiguous(), self.rank + 1, self.group))
+            ops.append(dist.P2POp(dist.isend, f[k:k + h], self.rank + 1, self.group))
             ops.append(dist.P2POp(dist.irecv, f[h + k:h + k + h], self.rank + 1, self.group))
-        if ops:
-            for req in dist.batch_isend_irecv(ops):
-                req.wait()
+        self._reqs = dist.batch_isend_irecv(ops) if ops else []
+
+    def exchange_wait(self):
+        for req in getattr(self, "_reqs", []):
+            req.wait()
+        self._reqs = []
+
+    def exchange(self, buf: int):
+        self.exchange_start(buf)
+        self.exchange_wait()
 
     def allreduce(self, parts):
         import torch
@@ -190,13 +211,17 @@ class TorchComm:
 
 
 def evolve(comm, n: int, length: float, max_steps: int, check_every: int = 100, tol: float = 0.0,
-           tol_relative: bool = True, mask_xy: int = 0, v_inf: float = 0.0, cur: int = 0):
+           tol_relative: bool = True, mask_xy: int = 0, v_inf: float = 0.0, cur: int = 0,
+           inside_out: bool = True):
     """The evolution of Secs. III-V over the slabs of `comm`, starting from
     field `cur` of every slab: a check at t = 0, check_every, ... and at
     max_steps (lattice-wide sums, renormalisation, the x/y symmetry mask,
     the convergence test on E_b); between checks, passes of `halo` steps
-    each followed by a halo exchange.  Returns (cur, record of the last
-    check, number of checks)."""
+    each followed by a halo exchange.  With inside_out (and slabs of at
+    least three halos) a pass is the paper's inside-out order: the `halo`
+    planes at each end of every slab first, their exchange started, then
+    the interior planes while it is in flight, then the wait.  Returns
+    (cur, record of the last check, number of checks)."""
     slabs = comm.slabs
     depth = min(s.halo for s in slabs)
     comm.exchange(cur)
@@ -219,10 +244,19 @@ def evolve(comm, n: int, length: float, max_steps: int, check_every: int = 100, 
         if t == max_steps:
             break
         k = min(depth, max_steps - t, check_every - t % check_every)
-        for s in slabs:
-            s.steps(cur, k)
+        if inside_out and all(s.nz_own >= 3 * s.halo for s in slabs):
+            for s in slabs:  # the planes the neighbours need
+                s.steps(cur, k, 0, s.halo)
+                s.steps(cur, k, s.nz_own - s.halo, s.nz_own)
+            comm.exchange_start(1 - cur)
+            for s in slabs:  # the interior, while the halos travel
+                s.steps(cur, k, s.halo, s.nz_own - s.halo)
+            comm.exchange_wait()
+        else:
+            for s in slabs:
+                s.steps(cur, k)
+            comm.exchange(1 - cur)
         cur = 1 - cur
-        comm.exchange(cur)
         t += k
     rec["steps"] = t
     return cur, rec, checks

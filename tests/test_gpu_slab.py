@@ -79,6 +79,32 @@ def test_slabs_match_the_whole_lattice_and_the_oracle(fd, orc, n, parts, halo, m
     assert rec["E"] == pytest.approx(orec["E"], rel=1e-5)
 
 
+@pytest.mark.parametrize("parts,halo", [(2, 3), (3, 2)])
+def test_inside_out_passes_match_plain_passes(fd, parts, halo):
+    """The inside-out pass (both ends of every slab, their exchange, then the
+    interior) gives the same bits as whole-slab passes, and as the whole
+    lattice's stencil."""
+    from paper_0904_0939_gb300 import slab
+
+    n, L = 48, 12.0
+    v = wl.anisotropic(n, L)
+    start = _start(n, 3)
+    out = {}
+    for inside_out in (True, False):
+        slabs = [slab.Slab(n, L, z0, k, halo) for z0, k in slab.partition(n, parts)]
+        try:
+            for s in slabs:
+                s.load(v, which="v")
+                s.load(start, 0)
+            cur, rec, _ = slab.evolve(slab.LocalComm(slabs), n, L, 170, 50, inside_out=inside_out)
+            out[inside_out] = (slab.gather(slabs, cur), rec["E"])
+        finally:
+            for s in slabs:
+                s.close()
+    np.testing.assert_array_equal(out[True][0], out[False][0])
+    assert out[True][1] == out[False][1]
+
+
 def test_slab_sums_add_up_to_the_lattice_sums(fd, orc):
     """the partial sums of three slabs of a given field, added, give the oracle's
     E, <r^2>, <V> and norm of the same (FP32-rounded) field to 1e-6, the FP32
@@ -125,6 +151,11 @@ def test_slab_create_refusals(fd):
     s = slab.Slab(32, 8.0, 0, 16, 3)
     with pytest.raises(fd.FdtdError):
         s.steps(0, 4)  # deeper than the halo
+    with pytest.raises(fd.FdtdError):
+        s.steps(0, 3, 5, 4)  # an inverted plane range
+    with pytest.raises(fd.FdtdError):
+        s.steps(0, 3, 0, 17)  # beyond the own planes
+    s.steps(0, 3, 4, 4)  # an empty range does nothing
     with pytest.raises(fd.FdtdError):
         s.scale(0, 1, 1.0, mask=0b110000)  # z symmetry needs the whole z axis
     with pytest.raises(fd.FdtdError):

@@ -61,12 +61,15 @@ class NumpySlab:
         out[~self.inside] = 0.0
         return out
 
-    def steps(self, src, depth):
+    def steps(self, src, depth, z_begin=0, z_end=None):
+        import torch
+
+        z_end = self.nz_own if z_end is None else z_end
         f = self.psi[src].numpy().copy()
         for _ in range(depth):
             f = self._step(f)
         h = self.halo
-        self.psi[1 - src][h:h + self.nz_own] = __import__("torch").from_numpy(f[h:h + self.nz_own])
+        self.psi[1 - src][h + z_begin:h + z_end] = torch.from_numpy(f[h + z_begin:h + z_end])
 
     def sums(self, src):
         f = self.psi[src].numpy()
@@ -107,7 +110,7 @@ class NumpySlab:
         self.psi[dst][h:h + self.nz_own] = torch.from_numpy(factor * c)
 
 
-CASE = dict(n=12, length=6.0, steps=50, check_every=20, halo=3)
+CASE = dict(n=20, length=8.0, steps=50, check_every=20, halo=3)
 
 
 def _problem():
@@ -115,7 +118,7 @@ def _problem():
     return wl.anisotropic(n, L), np.random.default_rng(8).uniform(-1, 1, (n, n, n))
 
 
-def _worker(rank, world, port, mask, out):
+def _worker(rank, world, port, mask, inside_out, out):
     import torch.distributed as dist
 
     from paper_0904_0939_gb300 import slab
@@ -127,20 +130,25 @@ def _worker(rank, world, port, mask, out):
     s = NumpySlab(n, L, z_first, nz_own, CASE["halo"], v)
     s.load(start, 0)
     comm = slab.TorchComm(s, rank, world)
-    cur, rec, checks = slab.evolve(comm, n, L, CASE["steps"], CASE["check_every"], mask_xy=mask)
+    cur, rec, checks = slab.evolve(comm, n, L, CASE["steps"], CASE["check_every"], mask_xy=mask,
+                                   inside_out=inside_out)
     dist.barrier()
     dist.destroy_process_group()
     out[rank] = (z_first, s.own(cur).numpy().copy(), rec, checks)
 
 
-@pytest.mark.parametrize("world,mask", [(2, 0), (3, wl.ODD_X)])
-def test_slab_evolution_over_gloo_ranks_matches_the_oracle(orc, world, mask):
+@pytest.mark.parametrize("world,mask,inside_out", [(2, 0, True), (2, 0, False), (3, wl.ODD_X, False)])
+def test_slab_evolution_over_gloo_ranks_matches_the_oracle(orc, world, mask, inside_out):
+    """world 2: slabs of ten planes, so the inside-out order updates three
+    planes at each end, exchanges them and updates the four interior planes
+    while they travel; world 3: slabs of seven and six planes, too thin for
+    it, so each pass is followed by its exchange"""
     import torch.multiprocessing as mp
 
     port = _free_port()
     with mp.get_context("spawn").Manager() as m:
         out = m.dict()
-        mp.spawn(_worker, args=(world, port, mask, out), nprocs=world, join=True)
+        mp.spawn(_worker, args=(world, port, mask, inside_out, out), nprocs=world, join=True)
         res = dict(out)
     field = np.concatenate([res[r][1] for r in range(world)], axis=0)
     n, L = CASE["n"], CASE["length"]
