@@ -533,6 +533,12 @@ int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem
     // done above
   } else if (mem_kind == FDTD_MEM_DEVICE) {
     conv(v, L.n3, 0);
+  } else if (vf && dtype == FDTD_F32) {
+    // FP32 into an FP32/BF16 lattice's FP32 V: one copy straight into place
+    // (full host-link bandwidth from pinned memory), then the checks
+    cudaMemcpyAsync(vf, v, L.n3 * sizeof(float), cudaMemcpyHostToDevice, h->st);
+    launch_guard_potential_f32(vf, L.n3, L.p, h->flags, h->st);
+    h->stats.launches += 1;
   } else {
     const size_t chunk = kStagingBytes / isz;
     for (size_t off = 0; off < L.n3; off += chunk) {

@@ -1017,6 +1017,24 @@ void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, 
   k_set_potential<Ti><<<grid_for(count, 256), 256, 0, st>>>(in, count, offset, vf, vd, coefA, coefCB, 0.5 * p.dtau,
                                                            p.c, flags);
 }
+// The checks of k_set_potential on an FP32 potential already in place (copied
+// straight from the caller's buffer): non-finite values (flag 1) and
+// 1 + dtau V / 2 <= 0 in FP64 or FP32 (flag 2).
+__global__ void k_guard_potential_f32(const float* __restrict__ vf, size_t count, double half_dtau, int32_t* flags) {
+  int bad = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float vv = vf[i];
+    const double v = (double)vv;
+    if (!isfinite(v)) bad |= 1;
+    if (!(1.0 + half_dtau * v > 0.0)) bad |= 2;
+    if (!(1.0f + (float)half_dtau * vv > 0.0f)) bad |= 2;
+  }
+  if (bad) atomicOr(flags, bad);
+}
+void launch_guard_potential_f32(const float* vf, size_t count, const Params& p, int32_t* flags, cudaStream_t st) {
+  k_guard_potential_f32<<<grid_for(count, 256), 256, 0, st>>>(vf, count, 0.5 * p.dtau, flags);
+}
+
 template void launch_set_potential<double>(const double*, size_t, size_t, float*, double*, double*, double*,
                                            const Params&, int32_t*, cudaStream_t);
 template void launch_set_potential<float>(const float*, size_t, size_t, float*, double*, double*, double*,

@@ -193,6 +193,8 @@ void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t st);
 // V (FP64 or FP32 input) -> lattice storage; flags[0] |= 1 nonfinite,
 // flags[0] |= 2 unstable (1 + dtau V / 2 <= 0).  For FP64 lattices also
 // A = (1-h)/(1+h) and cB = c / (1+h).
+// checks of an FP32 potential copied into place (flags as launch_set_potential)
+void launch_guard_potential_f32(const float* vf, size_t count, const Params& p, int32_t* flags, cudaStream_t st);
 template <typename Ti>
 void launch_set_potential(const Ti* in, size_t count, size_t offset, float* vf, double* vd, double* coefA,
                           double* coefCB, const Params& p, int32_t* flags, cudaStream_t st);

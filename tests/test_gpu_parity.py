@@ -254,15 +254,23 @@ def test_multires_reaches_same_energy_in_fewer_fine_steps(fd, orc):
 
 # ------------------------------------------------------------------ errors
 
-def test_input_guards(fd):
+@pytest.mark.parametrize("vdtype", [np.float64, np.float32])
+def test_input_guards(fd, vdtype):
+    """FP64 host input goes through the staging conversion, FP32 host input
+    into an FP32 lattice is copied straight into place and checked there:
+    both refuse non-finite values and 1 + dtau V / 2 <= 0."""
     s = solver(fd, 8, 4.0, fd.F32)
-    v = np.zeros((8, 8, 8))
+    v = np.zeros((8, 8, 8), dtype=vdtype)
     v[1, 2, 3] = np.nan
     with pytest.raises(fd.FdtdError) as e:
         s.set_potential(v)
     assert e.value.code == fd.ERR_NONFINITE
+    v[1, 2, 3] = np.inf
+    with pytest.raises(fd.FdtdError) as e:
+        s.set_potential(v)
+    assert e.value.code == fd.ERR_NONFINITE
     a = 4.0 / 8
-    v = np.full((8, 8, 8), -2.5 / (a * a / 4))  # 1 + dtau V / 2 < 0
+    v = np.full((8, 8, 8), -2.5 / (a * a / 4), dtype=vdtype)  # 1 + dtau V / 2 < 0
     with pytest.raises(fd.FdtdError) as e:
         s.set_potential(v)
     assert e.value.code == fd.ERR_UNSTABLE_DT
