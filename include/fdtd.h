@@ -113,7 +113,7 @@ typedef struct {
                              cooperative kernel in a CUDA graph; the update items of all
                              active lattices are cut into one equal range per block); with
                              autotune and no temporal_depth, the first evolve of a set of
-                             lattice sizes times (depth 1..3) x (tile width 64, 128) on
+                             lattice sizes times (depth 1..3) x (tiles 64x16, 128x16, 64x32) on
                              update passes that write the spare fields without advancing the
                              state, then runs the whole evolve in one launch with the
                              fastest (cached; identical results for every choice) */
@@ -159,6 +159,8 @@ typedef struct {
   int32_t tile_x;         /* tile width of the TMA stencil (64 or 128) when temporal_depth > 0
                              or autotune is off; 0 = 128 for n > 64, else 64 (batched: 128 if
                              most sites lie in lattices with n >= 96, else 64) */
+  int32_t tile_y;         /* batched mode, with temporal_depth > 0 or autotune off: 32 selects
+                             64 x 32 tiles (tile_x 0 or 64); 0 or 16: tiles 16 high */
 } fdtd_options;
 
 typedef struct {
@@ -285,13 +287,14 @@ FDTD_API int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double
  * the TMA kernel;
  * zchunk = 0 (depth 1) when the one-step
  * z-marching kernel is in use.  For a batched handle after an evolve: the
- * depth and z-planes per item of its persistent launch. */
+ * depth of its persistent launch and zchunk = -1 (the balanced partition). */
 FDTD_API int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk);
 
 /* The tile of that TMA stencil: tile_x x tile_y output sites of one z-plane
- * per block and step (tile_x 64 or 128, tile_y 16).  Both are 0 when the
- * one-step kernel is in use (FP64, BF16, periodic lattices, stencil_kernel
- * 1 or 2, or the autotuner's choice) and for a batched handle. */
+ * per block and step (tile_x 64 or 128, tile_y 16; a batched handle after
+ * an evolve: its persistent launch's tile, also 64 x 32).  Both are 0 when
+ * the one-step kernel is in use (FP64, BF16, periodic lattices,
+ * stencil_kernel 1 or 2, or the autotuner's choice). */
 FDTD_API int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y);
 
 /* Checkpoint files (Sec. VII.G: a run saves its wavefunction, and a later

@@ -59,7 +59,7 @@ class Options(ctypes.Structure):
                 ("stencil_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("zchunk", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
                 ("snapshots", ctypes.c_int32), ("graphs", ctypes.c_int32), ("boundary", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32)]
 
 
 class Obs(ctypes.Structure):

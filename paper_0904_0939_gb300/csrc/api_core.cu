@@ -76,6 +76,10 @@ int check_options(const fdtd_options& o, std::string& err) {
     err = "tile_x must be 0, 64 or 128";
     return FDTD_ERR_INVALID_ARG;
   }
+  if ((o.tile_y != 0 && o.tile_y != 16 && o.tile_y != 32) || (o.tile_y == 32 && o.tile_x == 128)) {
+    err = "tile_y must be 0, 16 or 32 (32 with 64-wide tiles only)";
+    return FDTD_ERR_INVALID_ARG;
+  }
   if (o.stencil_kernel < 0 || o.stencil_kernel > 2) {
     err = "stencil_kernel must be 0, 1 or 2";
     return FDTD_ERR_INVALID_ARG;
@@ -777,10 +781,8 @@ int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y) {
   *tile_x = *tile_y = 0;
   if (h->o.batched) {
     if (h->batch_depth) {
-      int bw = 0, bh = 0;
-      tma_box(h->batch_depth, h->batch_tx, &bw, &bh);
-      *tile_x = h->batch_tx;
-      *tile_y = bh - 2 * h->batch_depth;
+      *tile_x = batched_tile_x(h->batch_kind);
+      *tile_y = batched_tile_y(h->batch_kind);
     }
     return FDTD_OK;
   }

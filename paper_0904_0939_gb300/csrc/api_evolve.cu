@@ -535,7 +535,7 @@ std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_btune;
 
 // All lattices of the handle in one persistent launch.  With autotuning on
 // (and no depth given) the first evolve of a new set of lattice sizes times
-// every (depth 1..3, tile width 64/128) candidate on update passes that
+// every (depth 1..3, tile 64x16 / 128x16 / 64x32) candidate on update passes that
 // write the spare fields (the state does not advance, so every candidate
 // does the same work), caches the fastest and runs the evolve with it.
 // Every candidate computes the same bits.
@@ -550,26 +550,30 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
   std::vector<int> sizes;
   for (auto& L : c->lats) sizes.push_back(L.d.n);
   const auto key = std::make_pair(dev, sizes);
-  std::vector<std::pair<int, int>> cands;  // (depth, tile width)
+  std::vector<std::pair<int, int>> cands;  // (depth, tile kind: 64x16, 128x16, 64x32)
   if (c->o.temporal_depth > 0 || !c->o.autotune) {
-    int tx = c->o.tile_x;
-    if (!tx) {  // 128 if most sites lie in lattices of 96 or more sites per axis
+    int kind;
+    if (c->o.tile_y == 32) {
+      kind = 2;
+    } else if (c->o.tile_x) {
+      kind = c->o.tile_x == 128 ? 1 : 0;
+    } else {  // 128 wide if most sites lie in lattices of 96 or more sites per axis
       double big = 0.0, all = 0.0;
       for (auto& L : c->lats) {
         all += (double)L.n3;
         if (L.d.n >= 96) big += (double)L.n3;
       }
-      tx = 2.0 * big > all ? 128 : 64;
+      kind = 2.0 * big > all ? 1 : 0;
     }
-    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, tx});
+    cands.push_back({c->o.temporal_depth > 0 ? c->o.temporal_depth : 2, kind});
   } else {
     std::lock_guard<std::mutex> lock(g_btune_mu);
     auto it = g_btune.find(key);
     if (it != g_btune.end()) {
       cands.push_back(it->second);
     } else {
-      for (int tx : {64, 128})
-        for (int d = 1; d <= 3; ++d) cands.push_back({d, tx});
+      for (int kind = 0; kind < kBatchedTileKinds; ++kind)
+        for (int d = 1; d <= 3; ++d) cands.push_back({d, kind});
     }
   }
   for (auto& L : c->lats) {
@@ -681,7 +685,7 @@ int evolve_batched(fdtd_context* c, int64_t max_steps) {
   c->stats.stencil_launches += 1;
   if (c->profiling) c->stats.stencil_timed_launches += 1;
   c->batch_depth = best.first;
-  c->batch_tx = best.second;
+  c->batch_kind = best.second;
   return FDTD_OK;
 }
 

@@ -141,7 +141,7 @@ struct fdtd_context {
   size_t ev_used = 0;
   int check_seq = 0;
   fdtd::BatchedGraphs batch_graphs;     // graphs of the batched persistent launch
-  int batch_depth = 0, batch_tx = 0;  // configuration of the last batched evolve
+  int batch_depth = 0, batch_kind = 0;  // configuration of the last batched evolve (depth, tile kind)
   std::vector<char> batch_table;      // host copy of the batched driver's table (maps encoded once)
   cudaStream_t cap_st = nullptr;  // private stream the evolve graphs are captured on
   cudaEvent_t ev_in = nullptr;    // orders the lattices' graph loops after the handle's stream

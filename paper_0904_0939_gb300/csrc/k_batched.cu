@@ -30,6 +30,8 @@
 // flag and leaves (the others then give up at their next wait).
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tma_item.cuh"
@@ -44,8 +46,8 @@ constexpr int kMaxLat = 256;           // lattices per batched handle
 }  // namespace
 
 // Device table entry of one lattice (written by the host before the launch).
-struct alignas(64) BatchLat {
-  CUtensorMap step_map[2][3][3];  // [tile 64, 128][depth-1][psi0, psi1, V]
+struct alignas(128) BatchLat {
+  CUtensorMap step_map[3][3][3];  // [tile 64x16, 128x16, 64x32][depth-1][psi0, psi1, V]
   CUtensorMap sums_map[3];        // [psi0, psi1, V], the sums box
   float* psi[2];
   double* partials;
@@ -223,7 +225,7 @@ struct Views {
   float scale[kMaxLat];
 };
 
-template <int TXT>
+template <int TXT, int TYT>
 __device__ void build_prefixes(Views& v, const BatchLat* __restrict__ lats, int nlat, int w) {
   int a = 0;
   long long b = 0;
@@ -233,7 +235,7 @@ __device__ void build_prefixes(Views& v, const BatchLat* __restrict__ lats, int 
     if (!v.act[l]) continue;
     const int n = lats[l].n;
     a += tb::sums_items(n);
-    b += (long long)((n + TXT - 1) / TXT) * ((n + tb::TY - 1) / tb::TY) * (n + w);
+    b += (long long)((n + TXT - 1) / TXT) * ((n + TYT - 1) / TYT) * (n + w);
   }
   v.pre_sums[nlat] = a;
   v.pre_cost[nlat] = b;
@@ -241,11 +243,11 @@ __device__ void build_prefixes(Views& v, const BatchLat* __restrict__ lats, int 
 
 // One update item, kept out of line so that the phase loop's state does not
 // compete with the pipeline for registers (it is saved once per item).
-template <int K, int TXT>
+template <int K, int TXT, int TYT>
 __device__ __noinline__ bool step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, float* out,
                                        int n, int x0, int y0, int z0, int z1, float hd, float om6c, float cc,
                                        int32_t* err) {
-  return tb::tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, hd, om6c, cc, err);
+  return tb::tma_step_item<K, TXT, TYT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, hd, om6c, cc, err);
 }
 
 // A run of consecutive sums items of one tile column, out of line like the
@@ -258,13 +260,13 @@ __device__ __noinline__ bool sums_run(char* smem, const CUtensorMap* map_psi, co
 
 // One STEP phase: k (<= KMAX) steps of every active lattice, from field
 // cur[l] into the other, over the block's range of the cost line.
-template <int KMAX, int TXT>
+template <int KMAX, int TXT, int TYT>
 __device__ bool step_phase(char* smem, const Views& v, const BatchLat* __restrict__ lats, int nlat, int k, int w,
                            int32_t* err) {
   const long long U = v.pre_cost[nlat];
   const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
   if (u0 >= u1) return true;
-  constexpr int TI = TXT == 128 ? 1 : 0;
+  constexpr int TI = TXT == 128 ? 1 : (TYT == 32 ? 2 : 0);
   bool ok = true;
   for (int l = find_lattice(v.pre_cost, nlat, u0); l < nlat && v.pre_cost[l] < u1 && ok; ++l) {
     if (!v.act[l]) continue;
@@ -279,15 +281,15 @@ __device__ bool step_phase(char* smem, const Views& v, const BatchLat* __restric
     while (r < rend && ok) {
       const int t = (int)(r / n), z0 = (int)(r - (long long)t * n);
       const int z1 = (int)((long long)n < z0 + (rend - r) ? (long long)n : z0 + (rend - r));
-      const int x0 = (t % gx) * TXT, y0 = (t / gx) * tb::TY;
+      const int x0 = (t % gx) * TXT, y0 = (t / gx) * TYT;
       if (k == 1)
-        ok = step_item<1, TXT>(smem, &L.step_map[TI][0][cur], &L.step_map[TI][0][2], L.psi[cur ^ 1], n, x0,
+        ok = step_item<1, TXT, TYT>(smem, &L.step_map[TI][0][cur], &L.step_map[TI][0][2], L.psi[cur ^ 1], n, x0,
                                        y0, z0, z1, L.hd, L.om6c, L.cc, err);
       else if (k == 2 || KMAX == 2)
-        ok = step_item<(KMAX >= 2 ? 2 : 1), TXT>(smem, &L.step_map[TI][1][cur], &L.step_map[TI][1][2],
+        ok = step_item<(KMAX >= 2 ? 2 : 1), TXT, TYT>(smem, &L.step_map[TI][1][cur], &L.step_map[TI][1][2],
                                                          L.psi[cur ^ 1], n, x0, y0, z0, z1, L.hd, L.om6c, L.cc, err);
       else
-        ok = step_item<KMAX, TXT>(smem, &L.step_map[TI][KMAX - 1][cur], &L.step_map[TI][KMAX - 1][2],
+        ok = step_item<KMAX, TXT, TYT>(smem, &L.step_map[TI][KMAX - 1][cur], &L.step_map[TI][KMAX - 1][2],
                                           L.psi[cur ^ 1], n, x0, y0, z0, z1, L.hd, L.om6c, L.cc, err);
       r += z1 - z0;
     }
@@ -295,8 +297,8 @@ __device__ bool step_phase(char* smem, const Views& v, const BatchLat* __restric
   return ok;
 }
 
-template <int KMAX, int TXT>
-__global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const BatchLat* __restrict__ lats,
+template <int KMAX, int TXT, int TYT>
+__global__ void __launch_bounds__(tb::Geo<KMAX, TXT, TYT>::THREADS) k_batched(const BatchLat* __restrict__ lats,
                                                                          BatchRun* run, int32_t* err) {
   extern __shared__ __align__(128) char smem_raw[];
   char* smem = tb::aligned_smem(smem_raw);
@@ -310,13 +312,13 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const B
       v.cur[l] = lats[l].cur;
       v.act[l] = lats[l].state->active;  // a lattice that converged in an earlier launch stays retired
     }
-    build_prefixes<TXT>(v, lats, nlat, w);
+    build_prefixes<TXT, TYT>(v, lats, nlat, w);
   }
   __syncthreads();
   const int64_t t_start = run->t_start, t_end = run->t_end;
   if (run->tune_passes > 0) {  // timing: STEP phases into the spare fields, state unchanged
     for (int p = 0; p < run->tune_passes; ++p)
-      if (!step_phase<KMAX, TXT>(smem, v, lats, nlat, KMAX, w, err) || !grid_barrier(run, err)) return;
+      if (!step_phase<KMAX, TXT, TYT>(smem, v, lats, nlat, KMAX, w, err) || !grid_barrier(run, err)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) run->steps_done = t_start;
     return;
   }
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const B
           v.act[l] = *(volatile const int32_t*)&st->active;
           if (blockIdx.x == 0) lats[l].state->cur = v.cur[l];
         }
-        build_prefixes<TXT>(v, lats, nlat, w);
+        build_prefixes<TXT, TYT>(v, lats, nlat, w);
       }
       __syncthreads();
       ++check_id;
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const B
     const int64_t next = nc < t_end ? nc : t_end;
     while (t < next) {
       const int k = (int)((next - t) < KMAX ? (next - t) : KMAX);
-      if (!step_phase<KMAX, TXT>(smem, v, lats, nlat, k, w, err) || !grid_barrier(run, err)) return;
+      if (!step_phase<KMAX, TXT, TYT>(smem, v, lats, nlat, k, w, err) || !grid_barrier(run, err)) return;
       if (threadIdx.x == 0)
         for (int l = 0; l < nlat; ++l)
           if (v.act[l]) v.cur[l] ^= 1;
@@ -414,10 +416,10 @@ __global__ void __launch_bounds__(tb::Geo<KMAX, TXT>::THREADS) k_batched(const B
   }
 }
 
-template <int KMAX, int TXT>
+template <int KMAX, int TXT, int TYT>
 size_t batched_smem() {
-  size_t a = tb::Geo<KMAX, TXT>::SMEM;
-  size_t b = tb::Geo<1, kSumsTXB>::SMEM + 8 * 4 * (tb::Geo<KMAX, TXT>::THREADS / 32);  // sums item + reduction
+  size_t a = tb::Geo<KMAX, TXT, TYT>::SMEM;
+  size_t b = tb::Geo<1, kSumsTXB>::SMEM + 8 * 4 * (tb::Geo<KMAX, TXT, TYT>::THREADS / 32);  // sums item + reduction
   return a > b ? a : b;
 }
 
@@ -432,11 +434,11 @@ int batched_fill(void* host_entry, const float* psi0, const float* psi1, const f
   BatchLat& B = *(BatchLat*)host_entry;
   int bw, bh;
   const float* bufs[3] = {psi0, psi1, v};
-  for (int ti = 0; ti < 2; ++ti)
+  for (int kind = 0; kind < kBatchedTileKinds; ++kind)
     for (int k = 1; k <= 3; ++k) {
-      tma_box(k, ti ? 128 : 64, &bw, &bh);
+      tma_box(k, batched_tile_x(kind), &bw, &bh, batched_tile_y(kind));
       for (int b = 0; b < 3; ++b)
-        if (encode_field_map(&B.step_map[ti][k - 1][b], bufs[b], p.n, bw, bh)) return -1;
+        if (encode_field_map(&B.step_map[kind][k - 1][b], bufs[b], p.n, bw, bh)) return -1;
     }
   tma_box(1, kSumsTXB, &bw, &bh);
   for (int b = 0; b < 3; ++b)
@@ -469,7 +471,7 @@ size_t batched_entry_bytes() { return sizeof(BatchLat); }
 size_t batched_run_offset(int count) { return (size_t)count * sizeof(BatchLat); }
 
 void BatchedGraphs::release() {
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < kBatchedTileKinds; ++t)
     for (int d = 0; d < 4; ++d) {
       if (exec[t][d]) cudaGraphExecDestroy(exec[t][d]);
       exec[t][d] = nullptr;
@@ -477,9 +479,9 @@ void BatchedGraphs::release() {
     }
 }
 
-int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* err, BatchedGraphs* graphs) {
+int batched_prepare(void* dev_table, int count, int depth, int kind, int32_t* err, BatchedGraphs* graphs) {
   depth = depth < 1 ? 1 : (depth > 3 ? 3 : depth);
-  const int ti = tile_x == 128 ? 1 : 0;
+  const int ti = kind < 0 || kind >= kBatchedTileKinds ? 0 : kind;
   if (graphs->exec[ti][depth]) return 0;
   // capture the cooperative launch once: grid = resident blocks of the whole device
   int dev = 0, sms = 0, per_sm = 0;
@@ -513,22 +515,19 @@ int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* 
     graphs->grid[ti][depth] = grid;
     return cudaSuccess;
   };
+  auto by_depth = [&](auto tx_c, auto ty_c) {
+    constexpr int TXT = decltype(tx_c)::value, TYT = decltype(ty_c)::value;
+    if (depth == 1) return capture(k_batched<1, TXT, TYT>, tb::Geo<1, TXT, TYT>::THREADS, batched_smem<1, TXT, TYT>());
+    if (depth == 2) return capture(k_batched<2, TXT, TYT>, tb::Geo<2, TXT, TYT>::THREADS, batched_smem<2, TXT, TYT>());
+    return capture(k_batched<3, TXT, TYT>, tb::Geo<3, TXT, TYT>::THREADS, batched_smem<3, TXT, TYT>());
+  };
   cudaError_t e;
-  if (ti == 0) {
-    if (depth == 1)
-      e = capture(k_batched<1, 64>, tb::Geo<1, 64>::THREADS, batched_smem<1, 64>());
-    else if (depth == 2)
-      e = capture(k_batched<2, 64>, tb::Geo<2, 64>::THREADS, batched_smem<2, 64>());
-    else
-      e = capture(k_batched<3, 64>, tb::Geo<3, 64>::THREADS, batched_smem<3, 64>());
-  } else {
-    if (depth == 1)
-      e = capture(k_batched<1, 128>, tb::Geo<1, 128>::THREADS, batched_smem<1, 128>());
-    else if (depth == 2)
-      e = capture(k_batched<2, 128>, tb::Geo<2, 128>::THREADS, batched_smem<2, 128>());
-    else
-      e = capture(k_batched<3, 128>, tb::Geo<3, 128>::THREADS, batched_smem<3, 128>());
-  }
+  if (ti == 0)
+    e = by_depth(std::integral_constant<int, 64>{}, std::integral_constant<int, 16>{});
+  else if (ti == 1)
+    e = by_depth(std::integral_constant<int, 128>{}, std::integral_constant<int, 16>{});
+  else
+    e = by_depth(std::integral_constant<int, 64>{}, std::integral_constant<int, 32>{});
   if (e != cudaSuccess) {
     cudaGetLastError();
     return (int)e;
@@ -537,7 +536,7 @@ int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* 
 }
 
 int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_start, int64_t t_end, int skip_first,
-                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int tile_x,
+                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int kind,
                    int tune_passes, int32_t* err, cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done,
                    int* grid_out) {
   BatchRun run{};
@@ -555,10 +554,10 @@ int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_star
   run.tune_passes = tune_passes;
   BatchRun* drun = (BatchRun*)((char*)dev_table + batched_run_offset(count));
   cudaMemcpyAsync(drun, &run, sizeof(run), cudaMemcpyHostToDevice, st);
-  int e = batched_prepare(dev_table, count, depth, tile_x, err, graphs);
+  int e = batched_prepare(dev_table, count, depth, kind, err, graphs);
   if (e) return e;
   depth = depth < 1 ? 1 : (depth > 3 ? 3 : depth);
-  const int ti = tile_x == 128 ? 1 : 0;
+  const int ti = kind < 0 || kind >= kBatchedTileKinds ? 0 : kind;
   *grid_out = graphs->grid[ti][depth];
   cudaError_t ce = cudaGraphLaunch(graphs->exec[ti][depth], st);
   if (ce != cudaSuccess) return (int)ce;

@@ -348,9 +348,9 @@ int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const 
   return (int)(grid.x * grid.y * grid.z);
 }
 
-void tma_box(int depth, int tx, int* box_w, int* box_h) {
+void tma_box(int depth, int tx, int* box_w, int* box_h, int ty) {
   *box_w = tx + 2 * tb::HX;
-  *box_h = tb::TY + 2 * depth;
+  *box_h = ty + 2 * depth;
 }
 
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h) {

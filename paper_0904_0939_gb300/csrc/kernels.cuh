@@ -88,7 +88,8 @@ int auto_depth(int n, int precision);
 long long tma_tile_planes(int n, int tx);
 int tma_resident_blocks(int depth, int tx);
 int tma_zchunk(int n, int depth, int tx);
-void tma_box(int depth, int tx, int* box_w, int* box_h);
+// TMA box of a tile item: (tx + 8) x (ty + 2 depth) sites.
+void tma_box(int depth, int tx, int* box_w, int* box_h, int ty = 16);
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h);
 int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h);
 // `depth` steps on a z-slab field of n x n x nzbuf sites: own planes
@@ -124,16 +125,20 @@ size_t batched_entry_bytes();
 int batched_fill(void* host_entry, const float* psi0, const float* psi1, const float* v, double* partials,
                  LatState* state, double* hist, const Params& p, int mask, int cur, double v_inf);
 void batched_patch(void* host_entry, int mask, int cur);
-// Instantiated CUDA graphs of the persistent launch, one per (tile width,
+// Tile kinds of the batched update items: 64 x 16, 128 x 16, 64 x 32 sites.
+constexpr int kBatchedTileKinds = 3;
+inline int batched_tile_x(int kind) { return kind == 1 ? 128 : 64; }
+inline int batched_tile_y(int kind) { return kind == 2 ? 32 : 16; }
+// Instantiated CUDA graphs of the persistent launch, one per (tile kind,
 // depth), owned by the handle (the kernel's arguments are the fixed table,
 // run record and error flag, so a graph is reused by every evolve).
 struct BatchedGraphs {
-  cudaGraphExec_t exec[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
-  int grid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  cudaGraphExec_t exec[kBatchedTileKinds][4] = {};
+  int grid[kBatchedTileKinds][4] = {};
   void release();
 };
-// Capture and instantiate the graph of (depth, tile_x) if not done yet.
-int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* err, BatchedGraphs* graphs);
+// Capture and instantiate the graph of (depth, tile kind) if not done yet.
+int batched_prepare(void* dev_table, int count, int depth, int kind, int32_t* err, BatchedGraphs* graphs);
 // One cooperative launch (through the cached graph) that runs every check
 // and step of every lattice from step t_start to t_end (a multiple of
 // check_every, or max_steps): the check at t_start is made unless
@@ -143,7 +148,7 @@ int batched_prepare(void* dev_table, int count, int depth, int tile_x, int32_t* 
 // advance).  Returns 0 or a cudaError_t value.  *steps_done is written
 // asynchronously.
 int batched_launch(void* dev_table, int count, int64_t max_steps, int64_t t_start, int64_t t_end, int skip_first,
-                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int tile_x,
+                   int check0, int check_every, double tol, int tol_rel, int reimpose, int depth, int kind,
                    int tune_passes, int32_t* err, cudaStream_t st, BatchedGraphs* graphs, int64_t* steps_done,
                    int* grid_out);
 

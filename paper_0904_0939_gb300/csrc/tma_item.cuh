@@ -47,13 +47,13 @@ constexpr unsigned long long kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per 
 // Level 1's planes are triple-buffered (a thread writes the next one before
 // the other threads have finished reading the previous step's), the planes
 // of levels 2..K-1 double-buffered (written after the step's wait).
-template <int K, int TXT>
+template <int K, int TXT, int TYT = TY>
 struct Geo {
   static constexpr int TX = TXT;
   static constexpr int BW = TX + 2 * HX;
   static constexpr int C4 = BW / 4;                          // float4 columns per box row
   static constexpr int LW = BW + 8;                          // level-plane pitch: 4-float guards
-  static constexpr int BH = TY + 2 * K;
+  static constexpr int BH = TYT + 2 * K;
   static constexpr int USED = C4 * BH;                       // threads that own a box column
   static constexpr int THREADS = (USED + 31) / 32 * 32;      // whole warps
   static constexpr int R = RING;                             // ring slots
@@ -256,9 +256,9 @@ __device__ __forceinline__ float4 update4(float4 c, float xl, float xr, float4 y
 // also use the block's step barrier (an mbarrier counting every thread):
 // a thread arrives after its last level-plane store of a z-step and waits
 // for that phase in the middle of the next z-step.
-template <int K, int TXT>
+template <int K, int TXT, int TYT = TY>
 struct Pipe {
-  using G = Geo<K, TXT>;
+  using G = Geo<K, TXT, TYT>;
   static constexpr int R = G::R;
   static constexpr int D = G::D;
   char* smem;
@@ -379,9 +379,9 @@ struct Pipe {
 // Per-thread constants of a step item: the shared-memory bases every access
 // adds a compile-time offset to, the output column, and which levels this
 // thread's column computes.
-template <int K, int TXT>
+template <int K, int TXT, int TYT = TY>
 struct StepCtx {
-  using G = Geo<K, TXT>;
+  using G = Geo<K, TXT, TYT>;
   const float* rb;   // ring + this thread's offset in a box
   float* lb;         // level planes + this thread's offset in a level plane
   float* out;        // the output field
@@ -417,10 +417,10 @@ struct StepCtx {
 // compute) or below it in z (p < 0 comes first in an item); above it
 // (p >= n, block-uniform) zeros are written.  The last level computes only
 // the planes it stores.
-template <int K, int TXT, int U, bool STEADY>
-__device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int j, int jlast,
+template <int K, int TXT, int TYT, int U, bool STEADY>
+__device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, TXT, TYT>& pp, int j, int jlast,
                                                float4 (&w)[K > 1 ? K - 1 : 1][3]) {
-  using G = Geo<K, TXT>;
+  using G = Geo<K, TXT, TYT>;
   constexpr int R = G::R;
   static_assert(R == 6, "the step assumes a six-slot ring");
   constexpr int SJ = (U + 1) % R;  // slot of plane j
@@ -512,21 +512,21 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT>& x, Pipe<K, TXT>&
 
 // Six z-steps from j (j - j0 a multiple of 6); a partial group stops after
 // step j1.
-template <int K, int TXT, bool STEADY>
-__device__ __forceinline__ void step_group(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp, int& j, int j1,
+template <int K, int TXT, int TYT, bool STEADY>
+__device__ __forceinline__ void step_group(StepCtx<K, TXT, TYT>& x, Pipe<K, TXT, TYT>& pp, int& j, int j1,
                                            float4 (&w)[K > 1 ? K - 1 : 1][3]) {
   const int jl = j1 + 1;
-  step_iteration<K, TXT, 0, STEADY>(x, pp, j, jl, w);
+  step_iteration<K, TXT, TYT, 0, STEADY>(x, pp, j, jl, w);
   if (!STEADY && j + 1 > j1) { j += 1; return; }
-  step_iteration<K, TXT, 1, STEADY>(x, pp, j + 1, jl, w);
+  step_iteration<K, TXT, TYT, 1, STEADY>(x, pp, j + 1, jl, w);
   if (!STEADY && j + 2 > j1) { j += 2; return; }
-  step_iteration<K, TXT, 2, STEADY>(x, pp, j + 2, jl, w);
+  step_iteration<K, TXT, TYT, 2, STEADY>(x, pp, j + 2, jl, w);
   if (!STEADY && j + 3 > j1) { j += 3; return; }
-  step_iteration<K, TXT, 3, STEADY>(x, pp, j + 3, jl, w);
+  step_iteration<K, TXT, TYT, 3, STEADY>(x, pp, j + 3, jl, w);
   if (!STEADY && j + 4 > j1) { j += 4; return; }
-  step_iteration<K, TXT, 4, STEADY>(x, pp, j + 4, jl, w);
+  step_iteration<K, TXT, TYT, 4, STEADY>(x, pp, j + 4, jl, w);
   if (!STEADY && j + 5 > j1) { j += 5; return; }
-  step_iteration<K, TXT, 5, STEADY>(x, pp, j + 5, jl, w);
+  step_iteration<K, TXT, TYT, 5, STEADY>(x, pp, j + 5, jl, w);
   j += 6;
 }
 
@@ -536,17 +536,17 @@ __device__ __forceinline__ void step_group(StepCtx<K, TXT>& x, Pipe<K, TXT>& pp,
 // a z-slab with K-plane halos: the halo planes beyond the lattice's faces);
 // the planes beyond the field read as zero (TMA fill).  Returns false (in
 // every thread) if a bounded wait expired.
-template <int K, int TXT>
+template <int K, int TXT, int TYT = TY>
 __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
                               float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
                               float one_m6c, float cc, int32_t* err, int nz = -1, int zlo = 0, int zhi = -1) {
   if (nz < 0) nz = n;
   if (zhi < 0) zhi = nz;
-  using G = Geo<K, TXT>;
+  using G = Geo<K, TXT, TYT>;
   constexpr int C4 = G::C4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  StepCtx<K, TXT> x;
+  StepCtx<K, TXT, TYT> x;
   x.owner = tid < G::USED;
   const int row = x.owner ? tid / C4 : 0;
   const int col = x.owner ? tid % C4 : 0;
@@ -554,7 +554,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   const int yg = y0 - K + row;
   const bool inside = x.owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
   const bool interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
-  x.interior_row = x.owner && (row >= K) && (row < K + TY);
+  x.interior_row = x.owner && (row >= K) && (row < K + TYT);
   x.fix_l = x.owner && lane == 0 && col > 0;
   x.fix_r = x.owner && lane == 31 && col < C4 - 1;
 #pragma unroll
@@ -579,7 +579,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.ooff = (long long)yg * n + xg + (long long)(j0 - K + 1) * (long long)x.plane;
 
   for (int i = tid; i < G::NLEV * G::LPLANE; i += blockDim.x) lev[i] = 0.f;
-  Pipe<K, TXT> pp;
+  Pipe<K, TXT, TYT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
   pp.mv = map_v;
@@ -598,9 +598,9 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   int j = j0;
   while (j <= j1) {
     if (j >= ss && j + 5 <= se)
-      step_group<K, TXT, true>(x, pp, j, j1, w);
+      step_group<K, TXT, TYT, true>(x, pp, j, j1, w);
     else
-      step_group<K, TXT, false>(x, pp, j, j1, w);
+      step_group<K, TXT, TYT, false>(x, pp, j, j1, w);
     // an expired wait seen early ends the loop; the decision that counts is
     // taken below, after a barrier, the same in every thread
     if (*(volatile const int*)pp.flag) break;

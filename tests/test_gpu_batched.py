@@ -57,10 +57,11 @@ def small_batch():
     return lats, pots, masks, seeds
 
 
-@pytest.mark.parametrize("depth,tile", [(1, 64), (2, 64), (3, 64), (1, 128), (2, 128), (3, 128)])
+@pytest.mark.parametrize("depth,tile", [(1, (64, 16)), (2, (64, 16)), (3, (64, 16)), (1, (128, 16)), (2, (128, 16)),
+                                        (3, (128, 16)), (1, (64, 32)), (2, (64, 32)), (3, (64, 32))])
 def test_batched_bit_identical_to_separate_runs(fd, depth, tile):
     lats, pots, masks, seeds = small_batch()
-    a = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=depth, tile_x=tile)
+    a = run_batch(fd, lats, pots, masks, seeds, True, 3000, temporal_depth=depth, tile_x=tile[0], tile_y=tile[1])
     b = run_batch(fd, lats, pots, masks, seeds, False, 3000, temporal_depth=depth)
     for (pa, oa), (pb, ob) in zip(a, b):
         assert oa["steps"] == ob["steps"] and oa["converged"] == ob["converged"]
@@ -86,8 +87,8 @@ def test_batched_autotuned_launch_matches_a_fixed_configuration(fd):
         s.reset_stats()
         s.evolve(3000)
         launches = s.stats()["graph_launches"]
-        # six candidates, each launched untimed and timed, then the run; later: the run only
-        assert launches == (1 if rep else 13), (rep, launches)
+        # nine candidates, each launched untimed and timed, then the run; later: the run only
+        assert launches == (1 if rep else 19), (rep, launches)
         for i, (pf, of) in enumerate(fixed):
             o = s.last_check(lat=i)
             assert o["steps"] == of["steps"] and o["energy"] == of["energy"], (rep, i)
@@ -97,7 +98,7 @@ def test_batched_autotuned_launch_matches_a_fixed_configuration(fd):
             assert np.all(np.diff(h[:, 0]) > 0)
     depth, zc = s.tuned_config()
     tx, ty = s.tuned_kernel()
-    assert depth in (1, 2, 3) and zc == -1 and tx in (64, 128) and ty == 16
+    assert depth in (1, 2, 3) and zc == -1 and (tx, ty) in ((64, 16), (128, 16), (64, 32))
     s.close()
 
 
@@ -105,7 +106,7 @@ def test_batched_lattices_converging_at_different_steps(fd):
     """Lattices that converge early drop out of the cost line of the update
     passes, which is cut anew after every check: eight lattices of the C4
     mix's sizes with tolerances that retire them hundreds of steps apart end
-    bit-identical to separate runs, at both tile widths."""
+    bit-identical to separate runs, with every tile shape."""
     lats = [wl.Lattice(n, 0.25 * n) for n in (48, 64, 96, 48, 128, 64, 160, 96)]
     pots = [wl.harmonic(l.n, l.length, w) for l, w in zip(lats, (1.0, 1.7, 0.6, 2.0, 0.8, 1.2, 1.0, 1.5))]
     masks = [0, wl.ODD_X, wl.SYMMETRIC_ALL, wl.ODD_Z, 0, wl.ODD_Y, 0, wl.ODD_X]
@@ -113,8 +114,8 @@ def test_batched_lattices_converging_at_different_steps(fd):
     b = run_batch(fd, lats, pots, masks, seeds, False, 1500, temporal_depth=3)
     steps = {o["steps"] for _, o in b}
     assert len(steps) > 1  # the lattices retire at different checks
-    for tile in (64, 128):
-        a = run_batch(fd, lats, pots, masks, seeds, True, 1500, temporal_depth=3, tile_x=tile)
+    for tile in ((64, 16), (128, 16), (64, 32)):
+        a = run_batch(fd, lats, pots, masks, seeds, True, 1500, temporal_depth=3, tile_x=tile[0], tile_y=tile[1])
         for (pa, oa), (pb, ob) in zip(a, b):
             assert oa["steps"] == ob["steps"] and oa["energy"] == ob["energy"], tile
             np.testing.assert_array_equal(pa, pb)
