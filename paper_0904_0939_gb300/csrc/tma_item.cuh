@@ -103,6 +103,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that may suspend the thread until the phase completes or about
+// suspend_ns have passed, instead of returning at once: a waiting warp then
+// takes no issue slots from the warps that are working.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, unsigned parity, unsigned suspend_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(suspend_ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
   asm volatile(
@@ -129,18 +143,19 @@ __device__ __forceinline__ long long wait_budget_ns(const int32_t* err) {
 // Wait bounded in wall-clock time (budget from wait_budget_ns, read once per
 // item so that the wait itself touches no global memory on its fast path);
 // gives up early once any block has reported an expired wait in *err.
+// After a first plain try_wait the thread waits suspended, at most
+// kSuspendNs per try, and checks the flag and the clock between tries.
 // Returns false if it gave up.
+constexpr unsigned kSuspendNs = 100000;  // 0.1 ms, well inside every budget
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, const int32_t* err,
                                                   long long budget) {
   if (budget < 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (*(volatile const int32_t*)err != 0) return false;
-      if (global_ns() - t0 > (unsigned long long)budget) return false;
-    }
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity, kSuspendNs)) return true;
+    if (*(volatile const int32_t*)err != 0) return false;
+    if (global_ns() - t0 > (unsigned long long)budget) return false;
   }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
