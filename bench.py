@@ -60,8 +60,8 @@ C2_SECTORS = (("1s", 0b010101), ("2p_x", 0b000010))
 STENCIL_SOURCES = ("paper_0904_0939_gb300/csrc/tma_item.cuh", "paper_0904_0939_gb300/csrc/k_tblock.cu",
                    "paper_0904_0939_gb300/csrc/common.cuh")
 TRAFFIC = {
-    ("634ba54e45ff3283", 512, 3, -1, 128, 16): 1_763_400_192 + 521_928_704,
-    ("634ba54e45ff3283", 512, 3, -2, 128, 16): 1_193_885_952 + 514_115_584,
+    ("91485138563ad8f7", 512, 3, -1, 128, 16): 1_763_243_264 + 521_579_008,
+    ("91485138563ad8f7", 512, 3, -2, 128, 16): 1_193_608_448 + 514_116_608,
 }
 PARTITIONS = {-1: "balanced one-wave partition", -2: "columns-first partition"}
 
