@@ -459,9 +459,12 @@ def slab_run(fd, dev, n=512, steps=300, every=100):
     between the slabs' buffers, sums added on the host), 300 steps with a
     check every 100, against the whole-lattice solver on the same start.
     Measures the decomposition's own cost (halo planes recomputed by both
-    neighbours, halo copies, a host round trip per check); scaling over
-    GPUs is not measured here (one process per GPU would trade the halos
-    over NVLink and all-reduce four doubles per check)."""
+    neighbours, halo copies, a host round trip per check), with whole-slab
+    passes (the default in one process) and in the inside-out order (three
+    launches per slab and pass; what one process per GPU runs, where the
+    exchange overlaps the interior); scaling over GPUs is not measured here
+    (one process per GPU would trade the halos over NVLink and all-reduce
+    four doubles per check)."""
     import numpy as np
     import torch
 
@@ -512,8 +515,12 @@ def slab_run(fd, dev, n=512, steps=300, every=100):
                 comm.exchange(c)
 
         ms_steps, _ = timed(passes)
+        for sl in slabs:
+            sl.load(start, 0)
+        ms_io, _ = timed(lambda: slab.evolve(comm, n, L, steps, every, inside_out=True))
         out["parts"][str(parts)] = {"ms": ms, "gsite_per_s": n**3 * steps / (ms * 1e-3) / 1e9, "checks": checks,
                                     "passes_only_gsite_per_s": n**3 * 3 * (steps // 3) / (ms_steps * 1e-3) / 1e9,
+                                    "inside_out_gsite_per_s": n**3 * steps / (ms_io * 1e-3) / 1e9,
                                     "E": rec["E"], "E_rel_diff_vs_whole": abs(rec["E"] - e_whole) / abs(e_whole)}
         for sl in slabs:
             sl.close()

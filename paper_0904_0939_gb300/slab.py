@@ -142,7 +142,10 @@ class Slab:
 
 class LocalComm:
     """Several slabs of one lattice in one process: halos copied between the
-    slabs' buffers, sums added."""
+    slabs' buffers, sums added.  The copies run in stream order, so there is
+    nothing for the inside-out pass order to overlap."""
+
+    overlaps = False
 
     def __init__(self, slabs):
         self.slabs = list(slabs)
@@ -168,6 +171,8 @@ class TorchComm:
     """One slab per process: halos by torch.distributed send/recv with the
     neighbouring ranks, sums by an all-reduce (the process group's backend:
     NCCL for CUDA tensors, gloo for CPU tensors)."""
+
+    overlaps = True
 
     def __init__(self, slab, rank: int, world: int, group=None):
         self.slabs = [slab]
@@ -212,7 +217,7 @@ class TorchComm:
 
 def evolve(comm, n: int, length: float, max_steps: int, check_every: int = 100, tol: float = 0.0,
            tol_relative: bool = True, mask_xy: int = 0, v_inf: float = 0.0, cur: int = 0,
-           inside_out: bool = True):
+           inside_out: bool | None = None):
     """The evolution of Secs. III-V over the slabs of `comm`, starting from
     field `cur` of every slab: a check at t = 0, check_every, ... and at
     max_steps (lattice-wide sums, renormalisation, the x/y symmetry mask,
@@ -220,8 +225,11 @@ def evolve(comm, n: int, length: float, max_steps: int, check_every: int = 100, 
     each followed by a halo exchange.  With inside_out (and slabs of at
     least three halos) a pass is the paper's inside-out order: the `halo`
     planes at each end of every slab first, their exchange started, then
-    the interior planes while it is in flight, then the wait.  Returns
-    (cur, record of the last check, number of checks)."""
+    the interior planes while it is in flight, then the wait; by default
+    when the communicator's exchange can overlap the update (TorchComm).
+    Returns (cur, record of the last check, number of checks)."""
+    if inside_out is None:
+        inside_out = getattr(comm, "overlaps", False)
     slabs = comm.slabs
     depth = min(s.halo for s in slabs)
     comm.exchange(cur)
