@@ -98,6 +98,13 @@ def test_host_side_validation(fd):
     assert "check_every" in fd.last_error(None)
     rc, _ = _size(fd, [fd.Lattice(32, 10.0, fd.F32, dtau=a * a / 3 * 1.0001)])
     assert "von Neumann" in fd.last_error(None)
+    # tile shapes: 64 or 128 wide, 16 or 32 high, 32 only with 64-wide tiles
+    for kw, ok in ((dict(tile_x=64, tile_y=32), True), (dict(tile_x=128), True), (dict(tile_y=16), True),
+                   (dict(tile_x=96), False), (dict(tile_y=8), False), (dict(tile_x=128, tile_y=32), False)):
+        rc, _ = _size(fd, [fd.Lattice(32, 10.0, fd.F32)], **kw)
+        assert (rc == fd.OK) == ok, kw
+        if not ok:
+            assert rc == fd.ERR_INVALID_ARG and "tile" in fd.last_error(None)
 
 
 def test_create_rejects_bad_workspace(fd):
