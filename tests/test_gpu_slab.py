@@ -105,6 +105,47 @@ def test_inside_out_passes_match_plain_passes(fd, parts, halo):
     assert out[True][1] == out[False][1]
 
 
+def test_two_slabs_at_512_match_the_whole_lattice(fd):
+    """The benchmark's lattice size: 512^3 cut into two slabs (inside-out
+    passes), 30 steps with a check every 10, against the whole-lattice solver
+    on the same start, compared on the device: psi to 1e-6 of max |psi|, E to
+    1e-7."""
+    import torch
+
+    from paper_0904_0939_gb300 import slab
+
+    n, L = 512, 25.6
+    dev = torch.device("cuda")
+    v = wl.anisotropic_device(n, L, dev, dtype=torch.float32)
+    g = torch.Generator(device=dev).manual_seed(5)
+    start = torch.rand((n, n, n), generator=g, device=dev, dtype=torch.float32) * 2 - 1
+    whole = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=10, tol=0.0))
+    whole.set_potential(v)
+    whole.set_psi(start)
+    whole.evolve(30)
+    ref = torch.empty_like(start)
+    whole.get_psi(out=ref)
+    e_ref = whole.last_check()["energy"]
+    whole.close()
+    slabs = [slab.Slab(n, L, z0, k, 3) for z0, k in slab.partition(n, 2)]
+    try:
+        for s in slabs:
+            h, k = s.halo, s.nz_own
+            lo, hi = max(0, s.z_first - h), min(n, s.z_first + k + h)
+            b0 = lo - (s.z_first - h)
+            s.v[b0:b0 + hi - lo].copy_(v[lo:hi])
+            s.psi[0].zero_()
+            s.psi[0][b0:b0 + hi - lo].copy_(start[lo:hi])
+        cur, rec, _ = slab.evolve(slab.LocalComm(slabs), n, L, 30, 10, inside_out=True)
+        got = torch.cat([s.own(cur) for s in slabs], dim=0)
+        err = float((got - ref).abs().max() / ref.abs().max())
+    finally:
+        for s in slabs:
+            s.close()
+    assert err <= 1e-6
+    assert rec["E"] == pytest.approx(e_ref, rel=1e-7)
+
+
 def test_slab_sums_add_up_to_the_lattice_sums(fd, orc):
     """the partial sums of three slabs of a given field, added, give the oracle's
     E, <r^2>, <V> and norm of the same (FP32-rounded) field to 1e-6, the FP32
