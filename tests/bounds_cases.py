@@ -9,6 +9,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import numpy as np  # noqa: E402
+import torch  # noqa: E402
 
 import paper_0904_0939_gb300 as fd  # noqa: E402
 import workloads as wl  # noqa: E402
@@ -42,10 +43,30 @@ for n in (8, 12, 20, 36, 44, 68, 132):
     s.evolve(60)  # autotuned: every candidate runs once
     run(s)
 lats = [fd.Lattice(n, 0.4 * n, fd.F32) for n in (8, 12, 20, 36, 68)]
-s = fd.Solver(lats, fd.default_options(check_every=10, tol=1e-4, tol_relative=1, batched=1))
-for i, l in enumerate(lats):
-    s.set_potential(wl.harmonic(l.n, l.length).astype(np.float32), lat=i)
-    s.init_symmetric(3, wl.ODD_X, lat=i)
-s.evolve(200)  # batched, with its tuning slices
-run(s)
+for kw in (dict(), dict(temporal_depth=3, tile_x=64), dict(temporal_depth=2, tile_x=128),
+           dict(temporal_depth=3, tile_x=64, tile_y=32), dict(temporal_depth=1, tile_x=64, tile_y=32)):
+    s = fd.Solver(lats, fd.default_options(check_every=10, tol=1e-4, tol_relative=1, batched=1, **kw))
+    for i, l in enumerate(lats):
+        s.set_potential(wl.harmonic(l.n, l.length).astype(np.float32), lat=i)
+        s.init_symmetric(3, wl.ODD_X, lat=i)
+    s.evolve(200)  # batched: with its timed tuning passes, then every tile shape in a whole run
+    run(s)
+# z-slabs: the slab stencil over own-plane ranges, the slab sums; a slab's
+# count of accesses outside the allocation is the fourth word of its workspace
+from paper_0904_0939_gb300 import slab  # noqa: E402
+
+for n, parts, halo in ((36, 2, 3), (44, 3, 2), (20, 2, 1), (12, 4, 3)):
+    L = 0.4 * n
+    v = wl.anisotropic(n, L)
+    start = np.random.default_rng(n).uniform(-1.0, 1.0, (n, n, n))
+    for inside_out in (True, False):
+        slabs = [slab.Slab(n, L, z0, k, halo) for z0, k in slab.partition(n, parts)]
+        for sl in slabs:
+            sl.load(v, which="v")
+            sl.load(start, 0)
+        slab.evolve(slab.LocalComm(slabs), n, L, 23, 10, inside_out=inside_out)
+        for sl in slabs:
+            bad += int(sl.ws.view(torch.int32)[3].item())
+            sl.close()
+        cases += 1
 print(json.dumps({"violations": bad, "cases": cases}))
