@@ -449,6 +449,20 @@ int fdtd_create(const fdtd_lattice_desc* d, int count, const fdtd_options* o, vo
       tma_box(1, 64, &bw, &bh);
       for (int b = 0; b < 3; ++b) ok = ok && encode_field_map(&L.sums_maps[b], bufs[b], L.d.n, bw, bh) == 0;
       L.tma_ok = ok;
+    } else if (L.d.precision == FDTD_BF16 && L.d.n % 8 == 0 && L.d.n >= 8 && !L.p.periodic) {
+      // BF16 storage: the temporally blocked stencil with BF16 psi boxes
+      // (x start a multiple of 8 sites) and FP32 V boxes
+      bool ok = true;
+      int bw, bh;
+      for (int ti = 0; ti < 2; ++ti)
+        for (int k = 1; k <= blocked_max_depth(); ++k) {
+          tma_box_bf16(k, ti ? 128 : 64, &bw, &bh);
+          for (int b = 0; b < 2; ++b)
+            ok = ok && encode_field_map_bf16(&L.maps[ti][k - 1][b], (const __nv_bfloat16*)L.psi[b], L.d.n, bw, bh) == 0;
+          tma_box(k, ti ? 128 : 64, &bw, &bh);
+          ok = ok && encode_field_map(&L.maps[ti][k - 1][2], (const float*)L.v, L.d.n, bw, bh) == 0;
+        }
+      L.tma16 = ok;
     }
   }
   if (cuda_check(c, "create")) {
@@ -787,7 +801,7 @@ int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y) {
     return FDTD_OK;
   }
   if (L.has_v && L.has_psi) choose_config(h, L);
-  if (L.tma_ok && h->o.stencil_kernel == 0 && !L.plain && L.depth > 0) {
+  if ((L.tma_ok || L.tma16) && h->o.stencil_kernel == 0 && !L.plain && L.depth > 0) {
     int bw = 0, bh = 0;
     tma_box(L.depth, L.tx, &bw, &bh);
     *tile_x = L.tx;

@@ -19,9 +19,23 @@ namespace api {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int, bool, bool>> g_tune;
 
+// depth of the blocked stencil when none is timed or forced
+int blocked_depth(int n) { return n >= 96 ? 3 : 2; }
+
+// One launch of the TMA stencil, psi[cur] -> psi[1 - cur] (FP32 or BF16 psi)
+void launch_step_tma_any(const Lat& L, int ti, int d, int tx, int zc, const int32_t* active, int32_t* err,
+                         cudaStream_t st) {
+  if (L.tma16)
+    launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (__nv_bfloat16*)L.psi[1 - L.cur], L.p, d, tx, zc,
+                    active, err, st);
+  else
+    launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx, zc, active,
+                    err, st);
+}
+
 void choose_config(fdtd_context* c, Lat& L) {
   if (L.depth) return;
-  const bool tma = L.tma_ok && c->o.stencil_kernel == 0;
+  const bool tma = (L.tma_ok || L.tma16) && c->o.stencil_kernel == 0;
   // the direct kernel applies (FP32 or BF16 storage, n % 4 == 0)
   const bool f4 = (L.d.precision == FDTD_F32 || L.d.precision == FDTD_BF16) && L.d.n % 4 == 0;
   const bool bf16 = L.d.precision == FDTD_BF16;
@@ -37,9 +51,9 @@ void choose_config(fdtd_context* c, Lat& L) {
     // times the two one-step kernels when none is forced
     if (!(c->o.stencil_kernel == 0 && c->o.autotune && f4)) return;
   } else if (c->o.temporal_depth > 0 || !c->o.autotune) {
-    L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : auto_depth(L.d.n, L.d.precision);
+    L.depth = c->o.temporal_depth > 0 ? c->o.temporal_depth : blocked_depth(L.d.n);
     L.tx = c->o.tile_x ? c->o.tile_x : (L.d.n > 64 ? 128 : 64);
-    L.zc = c->o.zchunk != 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx);
+    L.zc = c->o.zchunk != 0 ? c->o.zchunk : tma_zchunk(L.d.n, L.depth, L.tx, bf16);
     return;
   }
   int dev = 0;
@@ -61,7 +75,7 @@ void choose_config(fdtd_context* c, Lat& L) {
   cudaEventCreate(&e1);
   const int n = L.d.n;
   double best = 0.0;
-  int bd = tma ? auto_depth(n, L.d.precision) : 1, bt = n > 64 ? 128 : 64, bz = tma ? tma_zchunk(n, bd, bt) : 0;
+  int bd = tma ? blocked_depth(n) : 1, bt = n > 64 ? 128 : 64, bz = tma ? tma_zchunk(n, bd, bt, bf16) : 0;
   bool bp = !tma, bdir = false;
   auto time_it = [&](auto&& launch, int depth) {
     launch();
@@ -122,7 +136,7 @@ void choose_config(fdtd_context* c, Lat& L) {
         const int zc = (n + div - 1) / div;
         if (zc >= (d == 1 ? 2 : std::max(8, 4 * d))) spans.push_back(zc);
       }
-      const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx);
+      const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(d, tx, bf16);
       for (int m = 1; m <= 3; ++m) spans.push_back((int)std::max(1LL, (total + m * slots - 1) / (m * slots)));
       spans.push_back(-1);  // the balanced one-wave partition
       spans.push_back(-2);  // columns first (neighbouring tiles in step)
@@ -131,8 +145,7 @@ void choose_config(fdtd_context* c, Lat& L) {
       for (int zc : spans) {
         double rate = time_it(
             [&]() {
-              launch_step_tma(L.maps[ti][d - 1][L.cur], L.maps[ti][d - 1][2], (float*)L.psi[1 - L.cur], L.p, d, tx,
-                              zc, nullptr, c->flags + 1, c->st);
+              launch_step_tma_any(L, ti, d, tx, zc, nullptr, c->flags + 1, c->st);
             },
             d);
         if (rate > best) {
@@ -152,9 +165,9 @@ void choose_config(fdtd_context* c, Lat& L) {
   cudaMemcpy(&err, c->flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (err) {  // the timed launches did no work: keep the heuristic, cache nothing
     if (tma) {
-      L.depth = auto_depth(n, L.d.precision);
+      L.depth = blocked_depth(n);
       L.tx = n > 64 ? 128 : 64;
-      L.zc = tma_zchunk(n, L.depth, L.tx);
+      L.zc = tma_zchunk(n, L.depth, L.tx, bf16);
     }
     return;
   }
@@ -172,7 +185,7 @@ void choose_config(fdtd_context* c, Lat& L) {
 void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0) {
   const int prec = L.d.precision;
   choose_config(c, L);
-  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+  const bool tma = (L.tma_ok || L.tma16) && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
@@ -195,6 +208,10 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
       else
         launch_step_f32<float>((const float*)L.psi[L.cur], (float*)L.psi[1 - L.cur], (const float*)L.v, L.p, active,
                                c->st);
+    } else if (tma) {
+      launch_step_tma(L.maps[L.tx == 128][k - 1][L.cur], L.maps[L.tx == 128][k - 1][2],
+                      (__nv_bfloat16*)L.psi[1 - L.cur], L.p, k, L.tx, k == depth ? L.zc : 0, active, c->flags + 1,
+                      c->st);
     } else if (L.direct) {
       launch_direct<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
                                    (const float*)L.v, L.p, active, c->st);
@@ -287,7 +304,7 @@ void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditional
 
 // Stencil launches and algorithmic bytes of one check_every-step segment.
 void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, double* bytes) {
-  const bool tma = L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+  const bool tma = (L.tma_ok || L.tma16) && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
   *launches = (ce + depth - 1) / depth;
   *bytes = (double)*launches * L.n3 * (2.0 * L.es + coef_bytes(L.d.precision));
@@ -306,8 +323,8 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   if (L.graph_exec[b] && std::equal(key, key + 6, L.graph_key[b])) return true;
   release_graph(L, b);
   Range r("evolve graph build");
-  if (L.tma_ok && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
-    (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx);  // occupancy query outside the capture
+  if ((L.tma_ok || L.tma16) && c->o.stencil_kernel == 0 && !L.plain && ce % L.depth)
+    (void)tma_zchunk(L.d.n, (int)(ce % L.depth), L.tx, L.tma16);  // occupancy query outside the capture
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
   cudaGraphConditionalHandle cond;

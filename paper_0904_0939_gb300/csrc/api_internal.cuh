@@ -96,7 +96,8 @@ struct Lat {
   LatState host_state{};
   // TMA descriptors of psi[0], psi[1], V: stencil boxes per tile width
   // (64, 128) and depth 1..3, and the sums boxes
-  bool tma_ok = false;
+  bool tma_ok = false;   // FP32 lattice with TMA maps (stencil, sums, batched)
+  bool tma16 = false;    // BF16 lattice with TMA stencil maps (BF16 psi boxes, FP32 V boxes)
   CUtensorMap maps[2][3][3];
   CUtensorMap sums_maps[3];
   // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet);

@@ -47,30 +47,29 @@ __device__ __forceinline__ long long balanced_plane(long long u, int n, int wcos
 // registers each) run out of line, so that the partition's state does not
 // compete with the pipeline for registers (it is saved once per item); the
 // others, with registers to spare, stay inline.
-template <int K, int TXT>
-__device__ __noinline__ bool step_item_ool(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
-                                           float* out, int n, int x0, int y0, int z0, int z1, float half_dtau,
-                                           float one_m6c, float cc, int32_t* err, int nz, int zlo, int zhi) {
-  return tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
-                               zhi);
+template <int K, int TXT, typename PT = float>
+__device__ __noinline__ bool step_item_ool(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, PT* out,
+                                           int n, int x0, int y0, int z0, int z1, float half_dtau, float one_m6c,
+                                           float cc, int32_t* err, int nz, int zlo, int zhi) {
+  return tma_step_item<K, TXT, TY, PT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz,
+                                       zlo, zhi);
 }
-template <int K, int TXT>
-__device__ __forceinline__ bool step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
-                                          float* out, int n, int x0, int y0, int z0, int z1, float half_dtau,
-                                          float one_m6c, float cc, int32_t* err, int nz = -1, int zlo = 0,
-                                          int zhi = -1) {
+template <int K, int TXT, typename PT = float>
+__device__ __forceinline__ bool step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v, PT* out,
+                                          int n, int x0, int y0, int z0, int z1, float half_dtau, float one_m6c,
+                                          float cc, int32_t* err, int nz = -1, int zlo = 0, int zhi = -1) {
   if constexpr (TXT == 128 && K == 3)
-    return step_item_ool<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
-                                 zhi);
+    return step_item_ool<K, TXT, PT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz,
+                                     zlo, zhi);
   else
-    return tma_step_item<K, TXT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err, nz, zlo,
-                                 zhi);
+    return tma_step_item<K, TXT, TY, PT>(smem, map_psi, map_v, out, n, x0, y0, z0, z1, half_dtau, one_m6c, cc, err,
+                                         nz, zlo, zhi);
 }
 
-template <int K, int TXT>
+template <int K, int TXT, typename PT = float>
 __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_constant__ CUtensorMap map_psi,
                                                                     const __grid_constant__ CUtensorMap map_v,
-                                                                    float* __restrict__ out, int n, int ntx,
+                                                                    PT* __restrict__ out, int n, int ntx,
                                                                     long long total, int span, int wcost,
                                                                     int zsplit, float half_dtau,
                                                                     float one_m6c, float cc,
@@ -111,8 +110,8 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_tma(const __grid_
   while (r < rend) {
     const int t = (int)(r / top), z0 = (int)(r - (long long)t * top);
     const int z1 = (int)min((long long)top, z0 + (rend - r));
-    if (!step_item<K, TXT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, base + z0, base + z1,
-                           half_dtau, one_m6c, cc, err))
+    if (!step_item<K, TXT, PT>(smem, &map_psi, &map_v, out, n, (t % ntx) * TXT, (t / ntx) * TY, base + z0,
+                               base + z1, half_dtau, one_m6c, cc, err))
       return;
     r += z1 - z0;
   }
@@ -206,19 +205,19 @@ long long tile_planes(int n) {
   return (long long)((n + TXT - 1) / TXT) * ((n + TY - 1) / TY) * n;
 }
 
-template <int K, int TXT>
+template <int K, int TXT, typename PT = float>
 int resident_blocks();
 
 // span > 0: equal spans; span == -2: columns first; other span <= 0: the balanced
 // partition over one wave
-template <int K, int TXT>
-void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const Params& p, int span,
+template <int K, int TXT, typename PT = float>
+void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, PT* out, const Params& p, int span,
               const int32_t* active, int32_t* err, cudaStream_t st) {
-  using G = Geo<K, TXT>;
-  set_smem(k_step_tma<K, TXT>, G::SMEM);
+  using G = Geo<K, TXT, TY, PT>;
+  set_smem(k_step_tma<K, TXT, PT>, G::SMEM);
   const long long total = tile_planes<K, TXT>(p.n);
   const unsigned blocks = span > 0 ? (unsigned)((total + span - 1) / span)
-                                   : (unsigned)std::min<long long>(resident_blocks<K, TXT>(), total);
+                                   : (unsigned)std::min<long long>(resident_blocks<K, TXT, PT>(), total);
   const int w = 2 * (K - 1);
   int zsplit = 0;
   if (span == -2) {
@@ -228,24 +227,24 @@ void launch_k(const CUtensorMap& mpsi, const CUtensorMap& mv, float* out, const 
     zsplit = (int)std::min<long long>(p.n, C * (p.n + w) / std::max(1u, blocks));
     if ((long long)blocks <= C || zsplit < 1 || zsplit >= p.n) span = -1;
   }
-  launch_pdl(k_step_tma<K, TXT>, dim3(blocks), dim3(G::THREADS), G::SMEM, st, mpsi, mv, out, p.n,
+  launch_pdl(k_step_tma<K, TXT, PT>, dim3(blocks), dim3(G::THREADS), G::SMEM, st, mpsi, mv, out, p.n,
              (p.n + TXT - 1) / TXT, total, span > 0 ? span : (span == -2 ? -2 : 0), w, zsplit, p.half_dtau_f,
              p.one_m6c_f, p.c_f, active, err);
 }
 
 // Blocks of k_step_tma<K, TXT> resident on the whole device at once
 // (queried once per device).
-template <int K, int TXT>
+template <int K, int TXT, typename PT>
 int resident_blocks() {
-  using G = Geo<K, TXT>;
+  using G = Geo<K, TXT, TY, PT>;
   static int cache[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && cache[dev] > 0) return cache[dev];
-  set_smem(k_step_tma<K, TXT>, G::SMEM);
+  set_smem(k_step_tma<K, TXT, PT>, G::SMEM);
   int sms = 0, occ = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tma<K, TXT>, G::THREADS, G::SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tma<K, TXT, PT>, G::THREADS, G::SMEM);
   const int r = std::max(1, sms) * std::max(1, occ);
   if (dev < 64) cache[dev] = r;
   return r;
@@ -266,37 +265,55 @@ long long tma_tile_planes(int n, int tx) {
   return tx == 64 ? tb::tile_planes<1, 64>(n) : tb::tile_planes<1, 128>(n);
 }
 
-int tma_resident_blocks(int depth, int tx) {
-  if (tx == 64) return depth == 1 ? tb::resident_blocks<1, 64>()
-                                   : depth == 2 ? tb::resident_blocks<2, 64>() : tb::resident_blocks<3, 64>();
-  return depth == 1 ? tb::resident_blocks<1, 128>()
-                    : depth == 2 ? tb::resident_blocks<2, 128>() : tb::resident_blocks<3, 128>();
+namespace {
+template <typename PT>
+int resident_of(int depth, int tx) {
+  if (tx == 64)
+    return depth == 1 ? tb::resident_blocks<1, 64, PT>()
+                      : depth == 2 ? tb::resident_blocks<2, 64, PT>() : tb::resident_blocks<3, 64, PT>();
+  return depth == 1 ? tb::resident_blocks<1, 128, PT>()
+                    : depth == 2 ? tb::resident_blocks<2, 128, PT>() : tb::resident_blocks<3, 128, PT>();
+}
+template <typename PT>
+void launch_step_any(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, PT* out, const Params& p, int depth,
+                     int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st) {
+  if (zc == 0) zc = tma_zchunk(p.n, depth, tx, sizeof(PT) == 2);  // zc -2: columns first, other zc < 0: balanced
+  if (tx == 64) {
+    if (depth == 1)
+      tb::launch_k<1, 64, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+    else if (depth == 2)
+      tb::launch_k<2, 64, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+    else
+      tb::launch_k<3, 64, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+  } else {
+    if (depth == 1)
+      tb::launch_k<1, 128, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+    else if (depth == 2)
+      tb::launch_k<2, 128, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+    else
+      tb::launch_k<3, 128, PT>(map_psi_in, map_v, out, p, zc, active, err, st);
+  }
+}
+}  // namespace
+
+int tma_resident_blocks(int depth, int tx, bool bf16) {
+  return bf16 ? resident_of<__nv_bfloat16>(depth, tx) : resident_of<float>(depth, tx);
 }
 
-int tma_zchunk(int n, int depth, int tx) {
+int tma_zchunk(int n, int depth, int tx, bool bf16) {
   // one wave of equal spans over the resident blocks
-  const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(depth, tx);
+  const long long total = tma_tile_planes(n, tx), slots = tma_resident_blocks(depth, tx, bf16);
   return (int)std::max(1LL, (total + slots - 1) / slots);
 }
 
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                      int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st) {
-  if (zc == 0) zc = tma_zchunk(p.n, depth, tx);  // zc -2: columns first, other zc < 0: balanced
-  if (tx == 64) {
-    if (depth == 1)
-      tb::launch_k<1, 64>(map_psi_in, map_v, out, p, zc, active, err, st);
-    else if (depth == 2)
-      tb::launch_k<2, 64>(map_psi_in, map_v, out, p, zc, active, err, st);
-    else
-      tb::launch_k<3, 64>(map_psi_in, map_v, out, p, zc, active, err, st);
-  } else {
-    if (depth == 1)
-      tb::launch_k<1, 128>(map_psi_in, map_v, out, p, zc, active, err, st);
-    else if (depth == 2)
-      tb::launch_k<2, 128>(map_psi_in, map_v, out, p, zc, active, err, st);
-    else
-      tb::launch_k<3, 128>(map_psi_in, map_v, out, p, zc, active, err, st);
-  }
+  launch_step_any<float>(map_psi_in, map_v, out, p, depth, tx, zc, active, err, st);
+}
+
+void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, __nv_bfloat16* out, const Params& p,
+                     int depth, int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st) {
+  launch_step_any<__nv_bfloat16>(map_psi_in, map_v, out, p, depth, tx, zc, active, err, st);
 }
 
 namespace tb {
@@ -357,8 +374,11 @@ int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int 
   return encode_field_map_nz(map, base, n, n, box_w, box_h);
 }
 
-// Tensor map of a dense n x n x nz FP32 field for box loads of box_w x box_h x 1.
-int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h) {
+namespace {
+// Tensor map of a dense n x n x nz field of `esize`-byte elements for box
+// loads of box_w x box_h x 1 (zero fill outside the field).
+int encode_map(CUtensorMap* map, CUtensorMapDataType dtype, int esize, const void* base, int n, int nz, int box_w,
+               int box_h) {
   static void* fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -374,15 +394,32 @@ int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int 
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nz};
-  cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)n * n * 4};
+  cuuint64_t strides[2] = {(cuuint64_t)n * esize, (cuuint64_t)n * n * esize};
   cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   // 64 B L2 promotion: a box row (tx + 8 floats) starts 16 B before a tile
   // boundary, and wider promotion fetches up to twice the row from HBM
-  CUresult r = ((Encode)fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = ((Encode)fn)(map, dtype, 3, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -2;
+}
+}  // namespace
+
+// Tensor map of a dense n x n x nz FP32 field for box loads of box_w x box_h x 1.
+int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, n, nz, box_w, box_h);
+}
+
+// The same for a BF16 field (n % 8 == 0, so that rows are 16-byte multiples).
+int encode_field_map_bf16(CUtensorMap* map, const __nv_bfloat16* base, int n, int box_w, int box_h) {
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, n, n, box_w, box_h);
+}
+
+// TMA box of a BF16 psi field for a tile item: (tx + 16) x (ty + 2 depth).
+void tma_box_bf16(int depth, int tx, int* box_w, int* box_h, int ty) {
+  *box_w = tx + 16;
+  *box_h = ty + 2 * depth;
 }
 
 }  // namespace fdtd

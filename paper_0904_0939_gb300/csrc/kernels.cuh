@@ -86,12 +86,16 @@ bool tma_supported(int n, int precision);
 int blocked_max_depth();
 int auto_depth(int n, int precision);
 long long tma_tile_planes(int n, int tx);
-int tma_resident_blocks(int depth, int tx);
-int tma_zchunk(int n, int depth, int tx);
+int tma_resident_blocks(int depth, int tx, bool bf16 = false);
+int tma_zchunk(int n, int depth, int tx, bool bf16 = false);
 // TMA box of a tile item: (tx + 8) x (ty + 2 depth) sites.
 void tma_box(int depth, int tx, int* box_w, int* box_h, int ty = 16);
 int encode_field_map(CUtensorMap* map, const float* base, int n, int box_w, int box_h);
 int encode_field_map_nz(CUtensorMap* map, const float* base, int n, int nz, int box_w, int box_h);
+// BF16 psi fields (n % 8 == 0): the box is (tx + 16) x (ty + 2 depth), its x
+// start a multiple of 8 sites
+int encode_field_map_bf16(CUtensorMap* map, const __nv_bfloat16* base, int n, int box_w, int box_h);
+void tma_box_bf16(int depth, int tx, int* box_w, int* box_h, int ty = 16);
 // `depth` steps on a z-slab field of n x n x nzbuf sites: own planes
 // [zbase, zbase + nzo), halo planes around them, planes outside [zlo, zhi)
 // beyond the lattice (tile width 128).
@@ -110,6 +114,8 @@ void launch_slab_scale(const float* in, float* out, int n, int nzo, int zbase, i
                        cudaStream_t st);
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, float* out, const Params& p, int depth,
                      int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st);
+void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, __nv_bfloat16* out, const Params& p,
+                     int depth, int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st);
 int tma_sums_blocks(int n);
 int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
                     const int32_t* active, int32_t* err, cudaStream_t st);

@@ -47,7 +47,7 @@ constexpr unsigned long long kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s per 
 // Level 1's planes are triple-buffered (a thread writes the next one before
 // the other threads have finished reading the previous step's), the planes
 // of levels 2..K-1 double-buffered (written after the step's wait).
-template <int K, int TXT, int TYT = TY>
+template <int K, int TXT, int TYT = TY, typename PT = float>
 struct Geo {
   static constexpr int TX = TXT;
   static constexpr int BW = TX + 2 * HX;
@@ -63,8 +63,16 @@ struct Geo {
   static constexpr int LPLANE = LW * BH;
   static constexpr int NLEV = K > 1 ? 3 + 2 * (K - 2) : 0;  // level planes
   static constexpr size_t RING_OFF = 128;                    // guard before the ring
-  static constexpr size_t SLOT_BYTES = 2 * (size_t)PLANE * 4;
-  static constexpr unsigned TX_BYTES = 2u * BW * BH * 4;     // bytes the two box loads deliver
+  // psi box: FP32 like V, or BF16 with an 8-site x margin (a TMA box must
+  // start at an x whose byte offset is a multiple of 16); the threads'
+  // columns sit XOFF sites into it
+  static constexpr int PS = (int)sizeof(PT);
+  static constexpr int HXP = PS == 4 ? HX : 8;
+  static constexpr int BWP = TX + 2 * HXP;
+  static constexpr int XOFF = HXP - HX;
+  static constexpr size_t PSI_BYTES = ((size_t)BWP * BH * PS + 127) / 128 * 128;
+  static constexpr size_t SLOT_BYTES = PSI_BYTES + (size_t)PLANE * 4;  // psi box, then the V box
+  static constexpr unsigned TX_BYTES = (unsigned)(BWP * BH * PS + BW * BH * 4);  // bytes the two box loads deliver
   static constexpr size_t LEVEL_OFF = RING_OFF + R * SLOT_BYTES + 128;
   static constexpr size_t BAR_OFF = LEVEL_OFF + (size_t)NLEV * LPLANE * 4;
   static constexpr size_t CBAR_OFF = BAR_OFF + 8 * R;        // the step barrier of the block
@@ -232,6 +240,45 @@ struct Chk {
 #endif
     *reinterpret_cast<float4*>(p) = v;
   }
+  // BF16 storage: four sites (8 bytes) widened to FP32, one site, and four
+  // FP32 values rounded to BF16 and stored
+  __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+#ifdef FDTD_CHECK_BOUNDS
+    const bool good = ok(p, 8);
+    const uint2 u = *reinterpret_cast<const uint2*>(good ? (const char*)p : lo);
+#else
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+#endif
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+#ifdef FDTD_CHECK_BOUNDS
+    if (!good) return make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ __forceinline__ float ld1(const __nv_bfloat16* p) {
+#ifdef FDTD_CHECK_BOUNDS
+    const bool good = ok(p, 2);
+    const float v = __bfloat162float(*(good ? p : (const __nv_bfloat16*)lo));
+    return good ? v : 0.f;
+#else
+    return __bfloat162float(*p);
+#endif
+  }
+  __device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
+#ifdef FDTD_CHECK_BOUNDS
+    if (!ok(p, 8)) return;
+#endif
+    __nv_bfloat162 a, b;
+    a.x = __float2bfloat16_rn(v.x);
+    a.y = __float2bfloat16_rn(v.y);
+    b.x = __float2bfloat16_rn(v.z);
+    b.y = __float2bfloat16_rn(v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned*>(&a);
+    u.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
   // add this thread's count of accesses outside the allocation to *bad
   __device__ __forceinline__ void flush() {
 #ifdef FDTD_CHECK_BOUNDS
@@ -271,9 +318,9 @@ __device__ __forceinline__ float4 update4(float4 c, float xl, float xr, float4 y
 // also use the block's step barrier (an mbarrier counting every thread):
 // a thread arrives after its last level-plane store of a z-step and waits
 // for that phase in the middle of the next z-step.
-template <int K, int TXT, int TYT = TY>
+template <int K, int TXT, int TYT = TY, typename PT = float>
 struct Pipe {
-  using G = Geo<K, TXT, TYT>;
+  using G = Geo<K, TXT, TYT, PT>;
   static constexpr int R = G::R;
   static constexpr int D = G::D;
   char* smem;
@@ -291,11 +338,11 @@ struct Pipe {
   int timeout = 0;
 
   __device__ __forceinline__ void issue(int q, int s) {
-    float* box = ring + s * (G::SLOT_BYTES / 4);
+    char* box = (char*)ring + s * G::SLOT_BYTES;
     uint64_t* bar = bars + s;
     mbar_expect_tx(bar, G::TX_BYTES);
-    tma_load_3d(box, mpsi, x0 - HX, y0 - K, q, bar);
-    tma_load_3d(box + G::PLANE, mv, x0 - HX, y0 - K, q, bar);
+    tma_load_3d(box, mpsi, x0 - G::HXP, y0 - K, q, bar);
+    tma_load_3d(box + G::PSI_BYTES, mv, x0 - HX, y0 - K, q, bar);
     outstanding |= 1u << s;
   }
   __device__ __forceinline__ void wait(int s) {
@@ -391,15 +438,30 @@ struct Pipe {
   }
 };
 
+// The value a BF16 field stores for each of four FP32 results (FP32 storage:
+// the results themselves), so that a temporally blocked BF16 item rounds
+// every level as a one-step kernel rounds every stored step.
+template <typename PT>
+__device__ __forceinline__ float4 stored4(float4 r) {
+  if constexpr (sizeof(PT) == 4) {
+    return r;
+  } else {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(r.x)), __bfloat162float(__float2bfloat16_rn(r.y)),
+                       __bfloat162float(__float2bfloat16_rn(r.z)), __bfloat162float(__float2bfloat16_rn(r.w)));
+  }
+}
+
 // Per-thread constants of a step item: the shared-memory bases every access
 // adds a compile-time offset to, the output column, and which levels this
 // thread's column computes.
-template <int K, int TXT, int TYT = TY>
+template <int K, int TXT, int TYT = TY, typename PT = float>
 struct StepCtx {
-  using G = Geo<K, TXT, TYT>;
-  const float* rb;   // ring + this thread's offset in a box
+  using G = Geo<K, TXT, TYT, PT>;
+  const float* rb;   // ring + this thread's offset in a box (FP32 psi: the psi box, V at + PLANE;
+                     // BF16 psi: the V box)
+  const PT* rp;      // BF16 psi: ring + this thread's offset in the psi box
   float* lb;         // level planes + this thread's offset in a level plane
-  float* out;        // the output field
+  PT* out;           // the output field
   long long ooff;    // offset of this thread's output column at the plane level K writes this
                      // z-step (negative before the lattice: only planes in [z0, z1) are stored)
   size_t plane;      // n * n
@@ -432,23 +494,32 @@ struct StepCtx {
 // compute) or below it in z (p < 0 comes first in an item); above it
 // (p >= n, block-uniform) zeros are written.  The last level computes only
 // the planes it stores.
-template <int K, int TXT, int TYT, int U, bool STEADY>
-__device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, TXT, TYT>& pp, int j, int jlast,
+template <int K, int TXT, int TYT, typename PT, int U, bool STEADY>
+__device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe<K, TXT, TYT, PT>& pp, int j, int jlast,
                                                float4 (&w)[K > 1 ? K - 1 : 1][3]) {
-  using G = Geo<K, TXT, TYT>;
+  using G = Geo<K, TXT, TYT, PT>;
   constexpr int R = G::R;
   static_assert(R == 6, "the step assumes a six-slot ring");
   constexpr int SJ = (U + 1) % R;  // slot of plane j
   constexpr int I0 = U % 3, I1 = (U + 1) % 3, I2 = (U + 2) % 3;
   constexpr int SL = G::SLOT_BYTES / 4;
   constexpr int BW = G::BW, LW = G::LW;
+  // psi in the ring: slot stride and row pitch in PT elements; V at VOFF
+  // floats from x.rb in every slot
+  constexpr int SLP = (int)(G::SLOT_BYTES / G::PS), PW = G::PS == 4 ? BW : G::BWP;
+  constexpr int VOFF = G::PS == 4 ? G::PLANE : 0;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   pp.wait((SJ + 1) % R);  // plane j + 1
   // ---- level 1: plane j from the ring
   {
     const int p = j;
     constexpr int S0 = SJ, SM = (SJ + R - 1) % R, SP = (SJ + 1) % R;
-    const float* b0 = x.rb + S0 * SL;
+    const PT* pr0;
+    if constexpr (G::PS == 4)
+      pr0 = x.rb;
+    else
+      pr0 = x.rp;
+    const PT* b0 = pr0 + S0 * SLP;
     float4 c = x.owner ? x.sm.ld4(b0) : zero4;
     float xl = __shfl_up_sync(0xffffffffu, c.w, 1);
     float xr = __shfl_down_sync(0xffffffffu, c.x, 1);
@@ -457,8 +528,8 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
     if (x.fix_l) xl = x.sm.ld1(b0 - 1);
     if (x.fix_r) xr = x.sm.ld1(b0 + 4);
     auto upd = [&]() {
-      return update4(c, xl, xr, x.sm.ld4(b0 - BW), x.sm.ld4(b0 + BW), x.sm.ld4(x.rb + SM * SL),
-                     x.sm.ld4(x.rb + SP * SL), x.sm.ld4(b0 + G::PLANE), x.hd, x.om6c, x.cc);
+      return update4(c, xl, xr, x.sm.ld4(b0 - PW), x.sm.ld4(b0 + PW), x.sm.ld4(pr0 + SM * SLP),
+                     x.sm.ld4(pr0 + SP * SLP), x.sm.ld4(x.rb + S0 * SL + VOFF), x.hd, x.om6c, x.cc);
     };
     if constexpr (K == 1) {
       if (x.need[1] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
@@ -466,7 +537,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
       float* dst = x.lb + (U % 3) * G::LPLANE;
       if constexpr (STEADY) {
         if (x.need[1]) {
-          const float4 r = upd();
+          const float4 r = stored4<PT>(upd());
           x.sm.st4(dst, r);
           w[0][I0] = r;
         }
@@ -476,7 +547,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
           w[0][I0] = zero4;
         }
       } else if (p >= x.zlo && x.need[1]) {
-        const float4 r = upd();
+        const float4 r = stored4<PT>(upd());
         x.sm.st4(dst, r);
         w[0][I0] = r;
       }
@@ -497,7 +568,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
     if (x.fix_r) xr = x.sm.ld1(lp + 4);
     auto upd = [&]() {
       return update4(c, xl, xr, x.sm.ld4(lp - LW), x.sm.ld4(lp + LW), w[l - 2][I1], w[l - 2][I0],
-                     x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + G::PLANE), x.hd, x.om6c, x.cc);
+                     x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + VOFF), x.hd, x.om6c, x.cc);
     };
     if (l == K) {
       if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
@@ -505,7 +576,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
       float* dst = x.lb + (3 + 2 * (l - 2) + ((U - l + 7) & 1)) * G::LPLANE;
       if constexpr (STEADY) {
         if (x.need[l]) {
-          const float4 r = upd();
+          const float4 r = stored4<PT>(upd());
           x.sm.st4(dst, r);
           w[l - 1][I0] = r;
         }
@@ -515,7 +586,7 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
           w[l - 1][I0] = zero4;
         }
       } else if (p >= x.zlo && x.need[l]) {
-        const float4 r = upd();
+        const float4 r = stored4<PT>(upd());
         x.sm.st4(dst, r);
         w[l - 1][I0] = r;
       }
@@ -527,21 +598,21 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT>& x, Pipe<K, 
 
 // Six z-steps from j (j - j0 a multiple of 6); a partial group stops after
 // step j1.
-template <int K, int TXT, int TYT, bool STEADY>
-__device__ __forceinline__ void step_group(StepCtx<K, TXT, TYT>& x, Pipe<K, TXT, TYT>& pp, int& j, int j1,
+template <int K, int TXT, int TYT, typename PT, bool STEADY>
+__device__ __forceinline__ void step_group(StepCtx<K, TXT, TYT, PT>& x, Pipe<K, TXT, TYT, PT>& pp, int& j, int j1,
                                            float4 (&w)[K > 1 ? K - 1 : 1][3]) {
   const int jl = j1 + 1;
-  step_iteration<K, TXT, TYT, 0, STEADY>(x, pp, j, jl, w);
+  step_iteration<K, TXT, TYT, PT, 0, STEADY>(x, pp, j, jl, w);
   if (!STEADY && j + 1 > j1) { j += 1; return; }
-  step_iteration<K, TXT, TYT, 1, STEADY>(x, pp, j + 1, jl, w);
+  step_iteration<K, TXT, TYT, PT, 1, STEADY>(x, pp, j + 1, jl, w);
   if (!STEADY && j + 2 > j1) { j += 2; return; }
-  step_iteration<K, TXT, TYT, 2, STEADY>(x, pp, j + 2, jl, w);
+  step_iteration<K, TXT, TYT, PT, 2, STEADY>(x, pp, j + 2, jl, w);
   if (!STEADY && j + 3 > j1) { j += 3; return; }
-  step_iteration<K, TXT, TYT, 3, STEADY>(x, pp, j + 3, jl, w);
+  step_iteration<K, TXT, TYT, PT, 3, STEADY>(x, pp, j + 3, jl, w);
   if (!STEADY && j + 4 > j1) { j += 4; return; }
-  step_iteration<K, TXT, TYT, 4, STEADY>(x, pp, j + 4, jl, w);
+  step_iteration<K, TXT, TYT, PT, 4, STEADY>(x, pp, j + 4, jl, w);
   if (!STEADY && j + 5 > j1) { j += 5; return; }
-  step_iteration<K, TXT, TYT, 5, STEADY>(x, pp, j + 5, jl, w);
+  step_iteration<K, TXT, TYT, PT, 5, STEADY>(x, pp, j + 5, jl, w);
   j += 6;
 }
 
@@ -551,17 +622,17 @@ __device__ __forceinline__ void step_group(StepCtx<K, TXT, TYT>& x, Pipe<K, TXT,
 // a z-slab with K-plane halos: the halo planes beyond the lattice's faces);
 // the planes beyond the field read as zero (TMA fill).  Returns false (in
 // every thread) if a bounded wait expired.
-template <int K, int TXT, int TYT = TY>
+template <int K, int TXT, int TYT = TY, typename PT = float>
 __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
-                              float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
+                              PT* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
                               float one_m6c, float cc, int32_t* err, int nz = -1, int zlo = 0, int zhi = -1) {
   if (nz < 0) nz = n;
   if (zhi < 0) zhi = nz;
-  using G = Geo<K, TXT, TYT>;
+  using G = Geo<K, TXT, TYT, PT>;
   constexpr int C4 = G::C4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  StepCtx<K, TXT, TYT> x;
+  StepCtx<K, TXT, TYT, PT> x;
   x.owner = tid < G::USED;
   const int row = x.owner ? tid / C4 : 0;
   const int col = x.owner ? tid % C4 : 0;
@@ -583,7 +654,12 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.cc = cc;
   float* lev = (float*)(smem + G::LEVEL_OFF);
   x.lb = lev + row * G::LW + 4 + 4 * col;
-  x.rb = (const float*)(smem + G::RING_OFF) + row * G::BW + 4 * col;
+  if constexpr (G::PS == 4) {
+    x.rb = (const float*)(smem + G::RING_OFF) + row * G::BW + 4 * col;
+  } else {
+    x.rb = (const float*)(smem + G::RING_OFF + G::PSI_BYTES) + row * G::BW + 4 * col;
+    x.rp = (const PT*)(smem + G::RING_OFF) + row * G::BWP + G::XOFF + 4 * col;
+  }
   x.plane = (size_t)n * n;
   x.sm.set(smem, smem + (G::SMEM - 128), err);
   x.gl.set(out, out + (size_t)n * n * nz, err);
@@ -594,7 +670,7 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   x.ooff = (long long)yg * n + xg + (long long)(j0 - K + 1) * (long long)x.plane;
 
   for (int i = tid; i < G::NLEV * G::LPLANE; i += blockDim.x) lev[i] = 0.f;
-  Pipe<K, TXT, TYT> pp;
+  Pipe<K, TXT, TYT, PT> pp;
   pp.smem = smem;
   pp.mpsi = map_psi;
   pp.mv = map_v;
@@ -613,9 +689,9 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   int j = j0;
   while (j <= j1) {
     if (j >= ss && j + 5 <= se)
-      step_group<K, TXT, TYT, true>(x, pp, j, j1, w);
+      step_group<K, TXT, TYT, PT, true>(x, pp, j, j1, w);
     else
-      step_group<K, TXT, TYT, false>(x, pp, j, j1, w);
+      step_group<K, TXT, TYT, PT, false>(x, pp, j, j1, w);
     // an expired wait seen early ends the loop; the decision that counts is
     // taken below, after a barrier, the same in every thread
     if (*(volatile const int*)pp.flag) break;

@@ -42,6 +42,19 @@ for n in (8, 12, 20, 36, 44, 68, 132):
     s.init_symmetric(2, 0)
     s.evolve(60)  # autotuned: every candidate runs once
     run(s)
+# BF16 storage: the TMA stencil with BF16 psi boxes (n % 8 == 0)
+for n in (8, 16, 40, 72, 136):
+    L = 0.4 * n
+    v = wl.harmonic(n, L).astype(np.float32)
+    for depth in (1, 2, 3):
+        for tx in (64, 128):
+            for zc in (0, -1, -2, 5):
+                s = fd.Solver(fd.Lattice(n, L, fd.BF16),
+                              fd.default_options(check_every=5, tol=0.0, temporal_depth=depth, tile_x=tx, zchunk=zc))
+                s.set_potential(v)
+                s.init_symmetric(1, wl.ODD_Y)
+                s.evolve(13)
+                run(s)
 lats = [fd.Lattice(n, 0.4 * n, fd.F32) for n in (8, 12, 20, 36, 68)]
 for kw in (dict(), dict(temporal_depth=3, tile_x=64), dict(temporal_depth=2, tile_x=128),
            dict(temporal_depth=3, tile_x=64, tile_y=32), dict(temporal_depth=1, tile_x=64, tile_y=32)):

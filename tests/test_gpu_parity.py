@@ -394,26 +394,33 @@ def test_blocked_kernels_bit_identical_to_single_steps(fd, n):
         np.testing.assert_array_equal(outs[name], outs["plain"], err_msg=name)
 
 
-@pytest.mark.parametrize("n", [32, 68, 132])
-def test_bf16_direct_kernel_matches_zmarch(fd, n):
+@pytest.mark.parametrize("n", [32, 68, 136])
+def test_bf16_kernels_match_zmarch(fd, n):
     """BF16 storage: the direct four-site kernel (stencil_kernel 2), the
-    z-marching kernel (stencil_kernel 1) and the autotuner's choice give the
-    same bits after 100 steps with checks (same FP32 arithmetic, same BF16
-    rounding of each stored value)."""
+    temporally blocked TMA kernel (n % 8 == 0: BF16 psi boxes, every level
+    rounded to BF16 as a stored step is; depths 1-3, both tile widths,
+    spans and partitions), the z-marching kernel (stencil_kernel 1) and the
+    autotuner's choice give the same bits after 100 steps with checks."""
     L = 0.3 * n
     rng = np.random.default_rng(n + 1)
     v = (wl.harmonic(n, L) + rng.uniform(-0.5, 0.5, (n, n, n))).astype(np.float32)
+    variants = [("plain", dict(stencil_kernel=1)), ("direct", dict(stencil_kernel=2)), ("auto", {})]
+    if n % 8 == 0:
+        variants += [(f"k{d}t{t}z{z}", dict(temporal_depth=d, tile_x=t, zchunk=z))
+                     for d in (1, 2, 3) for t in (64, 128) for z in (0, -1, -2, 7)]
     outs = {}
-    for name, kw in (("plain", dict(stencil_kernel=1)), ("direct", dict(stencil_kernel=2)), ("auto", {})):
+    for name, kw in variants:
         s = solver(fd, n, L, fd.BF16, check_every=50, **kw)
         s.set_potential(v)
         s.init_symmetric(17, wl.ODD_Y)
         s.evolve(100)
         outs[name] = (s.get_psi(dtype=np.float32), s.last_check()["energy"])
+        if name.startswith("k"):
+            assert s.tuned_kernel()[0] == kw["tile_x"], name
         s.close()
-    for name in ("direct", "auto"):
+    for name, _ in variants[1:]:
         np.testing.assert_array_equal(outs[name][0], outs["plain"][0], err_msg=name)
-        assert outs[name][1] == outs["plain"][1]
+        assert outs[name][1] == outs["plain"][1], name
 
 
 # ------------------------------------------------------------------ evolve graph
