@@ -180,13 +180,25 @@ void choose_config(fdtd_context* c, Lat& L) {
   g_tune[key] = std::make_tuple(bd, bt, bz, bp, bdir);
 }
 
+// The last step before a check runs as the check step (update + sums of
+// its result in one pass, the sums item's partials): FP32 lattices on the
+// TMA stencil.
+bool check_step_fused(const fdtd_context* c, const Lat& L) {
+  return L.tma_ok && c->o.stencil_kernel == 0 && !L.plain;
+}
+
 // Enqueue `count` update steps of lattice L (psi[cur] -> ... ; cur follows),
-// the first of them being step t0 of the current evolve.
-void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0) {
+// the first of them being step t0 of the current evolve.  With
+// before_check, a check follows: the last step is the check step, which
+// leaves the check's partial sums in L.partials (L.sums_ready).
+void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0, bool before_check) {
   const int prec = L.d.precision;
   choose_config(c, L);
   const bool tma = (L.tma_ok || L.tma16) && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
+  const bool fuse = before_check && count > 0 && check_step_fused(c, L);
+  if (count > 0) L.sums_ready = false;
+  if (fuse) --count;
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
     const long ev = prof_begin(c);
@@ -226,6 +238,13 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
     L.cur ^= 1;
     count -= k;
     t0 += k;
+  }
+  if (fuse) {
+    launch_step_sums_tma(L.maps[0][1][L.cur], L.maps[0][1][2], (float*)L.psi[1 - L.cur], L.p, L.partials, active,
+                         c->flags + 1, c->st);
+    c->stats.launches += 1;
+    L.cur ^= 1;
+    L.sums_ready = true;
   }
 }
 
@@ -269,9 +288,18 @@ void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int ma
   c->stats.launches += 1;
 }
 
+// The partial sums of psi[cur]: those the check step left, or a sums pass.
+int check_sums(fdtd_context* c, Lat& L) {
+  if (L.sums_ready) {
+    L.sums_ready = false;
+    return tma_sums_blocks(L.d.n);
+  }
+  return launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+}
+
 // One check of Secs. III-V on psi[cur]: sums, finalize, renormalise + mask.
 void enqueue_check(fdtd_context* c, Lat& L, int check_id, int64_t t) {
-  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  int np = check_sums(c, L);
   launch_finalize(&L.state[0], L.partials, np, check_id, t, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, 0,
                   0, nullptr, L.hist, sums_per_block(L.d.precision));
   c->stats.launches += 1;
@@ -293,7 +321,7 @@ int read_state(fdtd_context* c, Lat& L) {
 
 // The check of enqueue_check in device-sequenced form (inside the graph).
 void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditionalHandle cond) {
-  int np = launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+  int np = check_sums(c, L);
   launch_finalize(&L.state[0], L.partials, np, 0, 0, L.p, L.d.v_inf, c->o.tol, c->o.tol_relative, 1, c->st, (int)ce,
                   cond, c->flags + 1, L.hist, sums_per_block(L.d.precision));
   c->stats.launches += 1;
@@ -303,11 +331,15 @@ void enqueue_check_seq(fdtd_context* c, Lat& L, int64_t ce, cudaGraphConditional
 }
 
 // Stencil launches and algorithmic bytes of one check_every-step segment.
-void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, double* bytes) {
+// (The check step, the last of a segment on a fused lattice, is not counted:
+// it is the check's sums pass as well.)
+void segment_work(fdtd_context* c, const Lat& L, int64_t ce, int64_t* launches, double* bytes, int64_t* updates) {
   const bool tma = (L.tma_ok || L.tma16) && c->o.stencil_kernel == 0 && !L.plain;
   const int depth = tma ? L.depth : 1;
-  *launches = (ce + depth - 1) / depth;
+  const int64_t steps = check_step_fused(c, L) ? ce - 1 : ce;
+  *launches = (steps + depth - 1) / depth;
   *bytes = (double)*launches * L.n3 * (2.0 * L.es + coef_bytes(L.d.precision));
+  *updates = steps * (int64_t)L.n3;
 }
 
 // Build (or reuse) the evolve graph of lattice L for its current start
@@ -360,15 +392,20 @@ bool ensure_graph(fdtd_context* c, Lat& L, int64_t ce) {
   c->st = c->cap_st;
   bool ok = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
             cudaSuccess;
+  const bool ready0 = L.sums_ready;
+  // the body starts with the sums of its start field in place: the last
+  // check step of the previous iteration, or the sums pass before the launch
+  L.sums_ready = check_step_fused(c, L);
   if (ok) {
     for (int rep = 0; rep < 2; ++rep) {
       enqueue_check_seq(c, L, ce, cond);
-      run_steps(c, L, ce, &L.state[0].active, 0);
+      run_steps(c, L, ce, &L.state[0].active, 0, true);
     }
     cudaGraph_t captured = nullptr;
     ok = cudaStreamEndCapture(c->st, &captured) == cudaSuccess && L.cur == cur0;
   }
   c->st = user_st;
+  L.sums_ready = ready0;
   L.graph_kernels = c->stats.launches - launches0;
   c->stats.launches = launches0;
   c->pending.resize(pending0);
@@ -404,13 +441,14 @@ struct EvolveRun {
 int evolve_begin(fdtd_context* c, Lat& L, int64_t max_steps, EvolveRun& r) {
   launch_state_reset(&L.state[0], 0, c->st);
   c->stats.launches += 1;
+  L.sums_ready = false;
   const int64_t ce = c->o.check_every;
   if (c->o.graphs && c->profiling) {
     // the timed sample: two segments through the stream, every stencil
     // launch between CUDA events (a graph loop body cannot hold events)
     for (int i = 0; i < 2 && r.t + ce <= max_steps; ++i) {
       enqueue_check(c, L, r.check_id++, r.t);
-      run_steps(c, L, ce, &L.state[0].active, r.t);
+      run_steps(c, L, ce, &L.state[0].active, r.t, true);
       r.t += ce;
     }
     int rc = cuda_check(c, "evolve launch");
@@ -423,6 +461,11 @@ int evolve_begin(fdtd_context* c, Lat& L, int64_t max_steps, EvolveRun& r) {
   r.pairs = (!r.done && c->o.graphs) ? std::min<int64_t>((max_steps - r.t) / (2 * ce), 1 << 28) : 0;
   r.graph = r.pairs > 0 && ensure_graph(c, L, ce);
   if (r.graph) {
+    // the graph's first check takes the sums of its start field as ready
+    if (check_step_fused(c, L) && !L.sums_ready) {
+      launch_sums_any(c, L, L.psi[L.cur], &L.state[0].active);
+      L.sums_ready = true;
+    }
     r.t_end = r.t + 2 * r.pairs * ce;
     launch_state_reset(&L.state[0], 2, c->st, r.check_id + (int)(2 * r.pairs));
     c->stats.launches += 1;
@@ -458,12 +501,13 @@ int evolve_graph_finish(fdtd_context* c, Lat& L, EvolveRun& r) {
   const LatState& hs = L.host_state;
   c->stats.launches += (int64_t)((hs.checks - r.check_id + 1) / 2) * L.graph_kernels;
   const int64_t advanced = std::max<int64_t>(0, (hs.active ? r.t_end : hs.step) - r.t);  // steps taken while active
-  int64_t seg_l;
+  int64_t seg_l, seg_u;
   double seg_b;
-  segment_work(c, L, ce, &seg_l, &seg_b);
+  segment_work(c, L, ce, &seg_l, &seg_b, &seg_u);
   c->stats.stencil_launches += advanced / ce * seg_l;
-  c->stats.stencil_site_updates += advanced * (int64_t)L.n3;
+  c->stats.stencil_site_updates += advanced / ce * seg_u;
   c->stats.stencil_bytes += (double)(advanced / ce) * seg_b;
+  L.sums_ready = check_step_fused(c, L);  // the body ends with a check step
   if (!hs.active) {
     r.done = true;
   } else {
@@ -486,7 +530,7 @@ int evolve_tail(fdtd_context* c, Lat& L, int64_t max_steps, EvolveRun& r) {
         break;
       }
       int64_t nst = std::min<int64_t>(ce, max_steps - r.t);
-      run_steps(c, L, nst, &L.state[0].active, r.t);
+      run_steps(c, L, nst, &L.state[0].active, r.t, true);
       r.t += nst;
     }
     int rc = cuda_check(c, "evolve launch");

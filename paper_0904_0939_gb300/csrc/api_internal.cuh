@@ -98,6 +98,7 @@ struct Lat {
   // (64, 128) and depth 1..3, and the sums boxes
   bool tma_ok = false;   // FP32 lattice with TMA maps (stencil, sums, batched)
   bool tma16 = false;    // BF16 lattice with TMA stencil maps (BF16 psi boxes, FP32 V boxes)
+  bool sums_ready = false;  // partials hold the sums of psi[cur] (written by the last check step)
   CUtensorMap maps[2][3][3];
   CUtensorMap sums_maps[3];
   // stencil configuration: depth, tile width, z-planes per block (0 = not chosen yet);
@@ -196,7 +197,8 @@ void with_ctype(int prec, F&& f) {
 
 // stencil configuration, steps, checks and evolves (api_evolve.cu)
 void choose_config(fdtd_context* c, Lat& L);
-void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0 = 0);
+void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, int64_t t0 = 0,
+               bool before_check = false);
 int launch_sums_any(fdtd_context* c, Lat& L, const void* psi, const int32_t* active);
 void scale_parity_any(fdtd_context* c, Lat& L, const void* in, void* out, int mask, const LatState* s, int id,
                       int out_idx, LatState* sw);

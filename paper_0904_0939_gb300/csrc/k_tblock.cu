@@ -148,6 +148,30 @@ __global__ void __launch_bounds__(Geo<K, TXT>::THREADS) k_step_slab(const __grid
   }
 }
 
+// The check step: one update step from map_psi's field into `out` and the
+// lattice sums of the result, over the lattice sums' items (grid and
+// partial index as k_sums_tma), so that the partials equal those of a
+// separate k_sums_tma on `out` bit for bit.
+__global__ void __launch_bounds__(Geo<2, kSumsTX>::THREADS) k_step_sums_tma(const __grid_constant__ CUtensorMap map_psi,
+                                                                            const __grid_constant__ CUtensorMap map_v,
+                                                                            float* __restrict__ out, int n,
+                                                                            float half_dtau, float one_m6c, float cc,
+                                                                            float a, float kfac,
+                                                                            double* __restrict__ partials,
+                                                                            const int32_t* __restrict__ active,
+                                                                            int32_t* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  if (active && *active == 0) return;
+  if (*(volatile const int32_t*)err != 0) return;
+  extern __shared__ __align__(128) char smem_raw[];
+  char* smem = aligned_smem(smem_raw);
+  const int item = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int zc = sums_zchunk(n), z0 = blockIdx.z * zc;
+  tma_step_sums_item<kSumsTX>(smem, &map_psi, &map_v, out, n, blockIdx.x * kSumsTX, blockIdx.y * TY, z0,
+                              min(z0 + zc, n), half_dtau, one_m6c, cc, a, kfac, partials + (size_t)item * 4, err);
+}
+
 // Partial sums of a z-slab's own planes [zbase, zbase + nzo) (Sec. V: each
 // process sums its own planes), cut like the lattice sums; plane zbase is
 // the lattice's plane z_first.
@@ -341,6 +365,17 @@ void launch_step_slab(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, f
 }
 
 int tma_sums_blocks(int n) { return tb::sums_items(n); }
+
+int launch_step_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, float* out, const Params& p,
+                         double* partials, const int32_t* active, int32_t* err, cudaStream_t st) {
+  using G = tb::Geo<2, tb::kSumsTX>;
+  tb::set_smem(tb::k_step_sums_tma, G::SMEM);
+  const int zc = tb::sums_zchunk(p.n);
+  dim3 grid((p.n + tb::kSumsTX - 1) / tb::kSumsTX, (p.n + tb::TY - 1) / tb::TY, (p.n + zc - 1) / zc);
+  launch_pdl(tb::k_step_sums_tma, grid, dim3(G::THREADS), G::SMEM, st, map_psi, map_v, out, p.n, p.half_dtau_f,
+             p.one_m6c_f, p.c_f, (float)p.a, (float)(1.0 / (2.0 * p.mass * p.a * p.a)), partials, active, err);
+  return (int)(grid.x * grid.y * grid.z);
+}
 int slab_sums_blocks(int n, int nzo) { return tb::sums_items_of(n, nzo); }
 
 int launch_slab_sums(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, int nzo, int zbase,

@@ -117,6 +117,12 @@ void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, fl
 void launch_step_tma(const CUtensorMap& map_psi_in, const CUtensorMap& map_v, __nv_bfloat16* out, const Params& p,
                      int depth, int tx, int zc, const int32_t* active, int32_t* err, cudaStream_t st);
 int tma_sums_blocks(int n);
+// The check step (FP32, TMA lattices): one update step psi -> out (depth-2,
+// 64-wide maps of the input field and V) and the partial sums of `out` as
+// launch_sums_tma would write them (the same partials, bit for bit).
+// Returns the number of partials.
+int launch_step_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, float* out, const Params& p,
+                         double* partials, const int32_t* active, int32_t* err, cudaStream_t st);
 int launch_sums_tma(const CUtensorMap& map_psi, const CUtensorMap& map_v, const Params& p, double* partials,
                     const int32_t* active, int32_t* err, cudaStream_t st);
 

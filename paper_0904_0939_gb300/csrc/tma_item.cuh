@@ -438,6 +438,37 @@ struct Pipe {
   }
 };
 
+// The lattice sums' contribution of four sites c (x .. x + 3) with their
+// neighbours (xl = site x - 1, xr = site x + 4) and potential: S0 += c^2,
+// SH += c (-kfac Lap c + V c), Sr += r^2 c^2, SV += V c^2 (Eq. energysum),
+// every operation rounding on its own, Kahan-compensated per accumulator.
+// The sums item and the check step's fused sums both use it, so their
+// partial sums agree bit for bit.
+__device__ __forceinline__ void sums_site4(Kahan& s0, Kahan& sh, Kahan& sr, Kahan& sv, float4 c, float xl, float xr,
+                                           float4 ym, float4 yp, float4 zm, float4 zp, float4 v, const float (&px)[4],
+                                           float py, float pz, float kfac) {
+  const float cs[4] = {c.x, c.y, c.z, c.w};
+  const float xls[4] = {xl, c.x, c.y, c.z};
+  const float xrs[4] = {c.y, c.z, c.w, xr};
+  const float yms[4] = {ym.x, ym.y, ym.z, ym.w}, yps[4] = {yp.x, yp.y, yp.z, yp.w};
+  const float zms[4] = {zm.x, zm.y, zm.z, zm.w}, zps[4] = {zp.x, zp.y, zp.z, zp.w};
+  const float vs[4] = {v.x, v.y, v.z, v.w};
+  const float r2yz = __fadd_rn(__fmul_rn(py, py), __fmul_rn(pz, pz));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float ci = cs[i];
+    // sum of neighbour differences (exact for neighbours within a factor 2)
+    const float lap = __fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(xls[i], ci), __fsub_rn(xrs[i], ci)),
+                                          __fadd_rn(__fsub_rn(yms[i], ci), __fsub_rn(yps[i], ci))),
+                                __fadd_rn(__fsub_rn(zms[i], ci), __fsub_rn(zps[i], ci)));
+    const float c2 = __fmul_rn(ci, ci);
+    s0.add(c2);
+    sh.add(__fmul_rn(ci, __fadd_rn(__fmul_rn(-kfac, lap), __fmul_rn(vs[i], ci))));
+    sr.add(__fmul_rn(__fadd_rn(__fmul_rn(px[i], px[i]), r2yz), c2));
+    sv.add(__fmul_rn(vs[i], c2));
+  }
+}
+
 // The value a BF16 field stores for each of four FP32 results (FP32 storage:
 // the results themselves), so that a temporally blocked BF16 item rounds
 // every level as a one-step kernel rounds every stored step.
@@ -471,6 +502,13 @@ struct StepCtx {
   bool need[K + 1];  // level l computes this column (without the z tests)
   float hd, om6c, cc;
   Chk sm, gl;        // shared memory of the item, the output field
+  // check step (level 1 the update, level 2 the sums of its output): the
+  // column is inside the tile, the coordinates of its sites, the sums
+  bool interior_col;
+  int n;
+  float a, kfac, py;
+  float px[4];
+  Kahan s0, sh, sr, sv;
 };
 
 // One z-step of a step item.  U = (j - j0) mod 6 makes every ring slot, the
@@ -494,7 +532,7 @@ struct StepCtx {
 // compute) or below it in z (p < 0 comes first in an item); above it
 // (p >= n, block-uniform) zeros are written.  The last level computes only
 // the planes it stores.
-template <int K, int TXT, int TYT, typename PT, int U, bool STEADY>
+template <int K, int TXT, int TYT, typename PT, int U, bool STEADY, bool SUMS = false>
 __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe<K, TXT, TYT, PT>& pp, int j, int jlast,
                                                float4 (&w)[K > 1 ? K - 1 : 1][3]) {
   using G = Geo<K, TXT, TYT, PT>;
@@ -540,6 +578,9 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe
           const float4 r = stored4<PT>(upd());
           x.sm.st4(dst, r);
           w[0][I0] = r;
+          // the check step: level 1 is the output (plane j, one after level K's)
+          if constexpr (SUMS)
+            if (x.interior_row && x.interior_col && p >= x.z0 && p < x.z1) x.gl.st4(x.out + x.ooff + x.plane, r);
         }
       } else if (p >= x.zhi) {
         if (x.need[1]) {
@@ -550,6 +591,8 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe
         const float4 r = stored4<PT>(upd());
         x.sm.st4(dst, r);
         w[0][I0] = r;
+        if constexpr (SUMS)
+          if (x.interior_row && x.interior_col && p >= x.z0 && p < x.z1) x.gl.st4(x.out + x.ooff + x.plane, r);
       }
     }
   }
@@ -571,7 +614,14 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe
                      x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + VOFF), x.hd, x.om6c, x.cc);
     };
     if (l == K) {
-      if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
+      if constexpr (SUMS) {  // the sums of level K-1's output (the update) at plane p
+        if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1)))
+          sums_site4(x.s0, x.sh, x.sr, x.sv, c, xl, xr, x.sm.ld4(lp - LW), x.sm.ld4(lp + LW), w[l - 2][I1],
+                     w[l - 2][I0], x.sm.ld4(x.rb + ((SJ - l + 1 + 2 * R) % R) * SL + VOFF), x.px, x.py,
+                     coord_f32(p, x.n, x.a), x.kfac);
+      } else {
+        if (x.need[K] && x.interior_row && (STEADY || (p >= x.z0 && p < x.z1))) x.gl.st4(x.out + x.ooff, upd());
+      }
     } else {
       float* dst = x.lb + (3 + 2 * (l - 2) + ((U - l + 7) & 1)) * G::LPLANE;
       if constexpr (STEADY) {
@@ -598,21 +648,21 @@ __device__ __forceinline__ void step_iteration(StepCtx<K, TXT, TYT, PT>& x, Pipe
 
 // Six z-steps from j (j - j0 a multiple of 6); a partial group stops after
 // step j1.
-template <int K, int TXT, int TYT, typename PT, bool STEADY>
+template <int K, int TXT, int TYT, typename PT, bool STEADY, bool SUMS = false>
 __device__ __forceinline__ void step_group(StepCtx<K, TXT, TYT, PT>& x, Pipe<K, TXT, TYT, PT>& pp, int& j, int j1,
                                            float4 (&w)[K > 1 ? K - 1 : 1][3]) {
   const int jl = j1 + 1;
-  step_iteration<K, TXT, TYT, PT, 0, STEADY>(x, pp, j, jl, w);
+  step_iteration<K, TXT, TYT, PT, 0, STEADY, SUMS>(x, pp, j, jl, w);
   if (!STEADY && j + 1 > j1) { j += 1; return; }
-  step_iteration<K, TXT, TYT, PT, 1, STEADY>(x, pp, j + 1, jl, w);
+  step_iteration<K, TXT, TYT, PT, 1, STEADY, SUMS>(x, pp, j + 1, jl, w);
   if (!STEADY && j + 2 > j1) { j += 2; return; }
-  step_iteration<K, TXT, TYT, PT, 2, STEADY>(x, pp, j + 2, jl, w);
+  step_iteration<K, TXT, TYT, PT, 2, STEADY, SUMS>(x, pp, j + 2, jl, w);
   if (!STEADY && j + 3 > j1) { j += 3; return; }
-  step_iteration<K, TXT, TYT, PT, 3, STEADY>(x, pp, j + 3, jl, w);
+  step_iteration<K, TXT, TYT, PT, 3, STEADY, SUMS>(x, pp, j + 3, jl, w);
   if (!STEADY && j + 4 > j1) { j += 4; return; }
-  step_iteration<K, TXT, TYT, PT, 4, STEADY>(x, pp, j + 4, jl, w);
+  step_iteration<K, TXT, TYT, PT, 4, STEADY, SUMS>(x, pp, j + 4, jl, w);
   if (!STEADY && j + 5 > j1) { j += 5; return; }
-  step_iteration<K, TXT, TYT, PT, 5, STEADY>(x, pp, j + 5, jl, w);
+  step_iteration<K, TXT, TYT, PT, 5, STEADY, SUMS>(x, pp, j + 5, jl, w);
   j += 6;
 }
 
@@ -705,6 +755,130 @@ __device__ bool tma_step_item(char* smem, const CUtensorMap* map_psi, const CUte
   const bool good = pp.ok(err);
   pp.finish(true);
   return good;
+}
+
+// The check step: one update step on a 64 x TY tile item, planes [z0, z1),
+// whose result is also summed (S0, SH, Sr, SV of Eq. energysum) -- the
+// depth-2 item with level 2 replaced by the sums of level 1's output.  The
+// item is one of the lattice sums' items (the same tile, z-chunk and
+// partial index), and its partial sums are bit-identical to that item's:
+// the same per-site arithmetic (sums_site4) in the same order per site
+// column, and each thread's totals moved to the thread that holds the same
+// column in the sums item before the same fixed-order block reduction.
+// Writes psi_t to out and the four totals to dst[0..3]; false if a bounded
+// wait expired.
+template <int TXT>
+__device__ bool tma_step_sums_item(char* smem, const CUtensorMap* map_psi, const CUtensorMap* map_v,
+                                   float* __restrict__ out, int n, int x0, int y0, int z0, int z1, float half_dtau,
+                                   float one_m6c, float cc, float a, float kfac, double* __restrict__ dst,
+                                   int32_t* err) {
+  constexpr int K = 2;
+  using G = Geo<K, TXT>;
+  using GS = Geo<1, TXT>;  // the sums item's layout
+  static_assert(G::C4 == GS::C4, "the sums layout differs from the step layout by whole rows");
+  constexpr int C4 = G::C4;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  StepCtx<K, TXT> x;
+  x.owner = tid < G::USED;
+  const int row = x.owner ? tid / C4 : 0;
+  const int col = x.owner ? tid % C4 : 0;
+  const int xg = x0 - HX + 4 * col;
+  const int yg = y0 - K + row;
+  const bool inside = x.owner && (xg >= 0) && (xg < n) && (yg >= 0) && (yg < n);
+  x.interior_col = (col >= HX / 4) && (col < HX / 4 + G::TX / 4);
+  x.interior_row = x.owner && (row >= K) && (row < K + TY);
+  x.fix_l = x.owner && lane == 0 && col > 0;
+  x.fix_r = x.owner && lane == 31 && col < C4 - 1;
+#pragma unroll
+  for (int l = 1; l <= K; ++l) x.need[l] = inside && (row >= l && row < G::BH - l) && (l < K || x.interior_col);
+  x.z0 = z0;
+  x.z1 = z1;
+  x.zlo = 0;
+  x.zhi = n;
+  x.hd = half_dtau;
+  x.om6c = one_m6c;
+  x.cc = cc;
+  x.n = n;
+  x.a = a;
+  x.kfac = kfac;
+  x.py = coord_f32(yg, n, a);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.px[i] = coord_f32(xg + i, n, a);
+  float* lev = (float*)(smem + G::LEVEL_OFF);
+  x.lb = lev + row * G::LW + 4 + 4 * col;
+  x.rb = (const float*)(smem + G::RING_OFF) + row * G::BW + 4 * col;
+  x.plane = (size_t)n * n;
+  x.sm.set(smem, smem + (G::SMEM - 128), err);
+  x.gl.set(out, out + (size_t)n * n * n, err);
+  const int j0 = z0 - K + 1, j1 = z1 + K - 2;
+  x.out = out;
+  x.ooff = (long long)yg * n + xg + (long long)(j0 - K + 1) * (long long)x.plane;
+
+  for (int i = tid; i < G::NLEV * G::LPLANE; i += blockDim.x) lev[i] = 0.f;
+  Pipe<K, TXT> pp;
+  pp.smem = smem;
+  pp.mpsi = map_psi;
+  pp.mv = map_v;
+  pp.x0 = x0;
+  pp.y0 = y0;
+  pp.err = err;
+  pp.begin(j0, j1 + 1, true);
+
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 w[K - 1][3];
+  w[0][0] = w[0][1] = w[0][2] = zero4;
+  const int ss = z0 + K - 1, se = min(z1 + K - 2, n - 1);
+  int j = j0;
+  while (j <= j1) {
+    if (j >= ss && j + 5 <= se)
+      step_group<K, TXT, TY, float, true, true>(x, pp, j, j1, w);
+    else
+      step_group<K, TXT, TY, float, false, true>(x, pp, j, j1, w);
+    if (*(volatile const int*)pp.flag) break;
+  }
+  pp.cta_wait((unsigned)((j - j0) & 1));
+  x.sm.flush();
+  x.gl.flush();
+  __syncthreads();
+  const bool good = pp.ok(err);
+  pp.finish(true);
+  if (!good) return false;
+  // each thread's totals to the sums item's thread of the same site column
+  // (K - 1 rows earlier: row r here is row r - 1 there), then that item's
+  // reduction over its warps
+  double* slot = (double*)(smem + G::LEVEL_OFF);  // the level planes are free now
+  constexpr int SHIFT = (K - 1) * C4;
+  for (int i = tid; i < GS::THREADS * 4; i += blockDim.x) slot[i] = 0.0;
+  __syncthreads();
+  if (tid >= SHIFT && tid - SHIFT < GS::THREADS) {
+    double* d = slot + (size_t)(tid - SHIFT) * 4;
+    d[0] = x.s0.value();
+    d[1] = x.sh.value();
+    d[2] = x.sr.value();
+    d[3] = x.sv.value();
+  }
+  __syncthreads();
+  double v4[4] = {0.0, 0.0, 0.0, 0.0};
+  if (tid < GS::THREADS)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v4[q] = slot[(size_t)tid * 4 + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], off);
+  double* red = (double*)(smem + G::RED_OFF);
+  if (lane == 0 && tid < GS::THREADS)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[(tid >> 5) * 4 + q] = v4[q];
+  __syncthreads();
+  if (tid < 4) {
+    double acc = 0.0;
+    for (int wi = 0; wi < GS::THREADS / 32; ++wi) acc += red[wi * 4 + tid];
+    dst[tid] = acc;
+  }
+  __syncthreads();
+  return true;
 }
 
 // Partition of the lattice sums: 64 x TY tile columns cut along z into
@@ -806,26 +980,7 @@ __device__ bool tma_sums_item(char* smem, const CUtensorMap* map_psi, const CUte
     if (use) {
       const float4 ym = sm.ld4(b0 + ro - BW), yp = sm.ld4(b0 + ro + BW), zm = sm.ld4(bm + ro), zp = sm.ld4(bp + ro);
       const float4 v = sm.ld4(b0 + G::PLANE + ro);
-      const float pz = coord_f32(j + zoff, n, a);
-      const float cs[4] = {c.x, c.y, c.z, c.w};
-      const float xls[4] = {xl, c.x, c.y, c.z};
-      const float xrs[4] = {c.y, c.z, c.w, xr};
-      const float yms[4] = {ym.x, ym.y, ym.z, ym.w}, yps[4] = {yp.x, yp.y, yp.z, yp.w};
-      const float zms[4] = {zm.x, zm.y, zm.z, zm.w}, zps[4] = {zp.x, zp.y, zp.z, zp.w};
-      const float vs[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float ci = cs[i];
-        // sum of neighbour differences (exact for neighbours within a factor 2)
-        const float lap = ((__fsub_rn(xls[i], ci) + __fsub_rn(xrs[i], ci)) +
-                           (__fsub_rn(yms[i], ci) + __fsub_rn(yps[i], ci))) +
-                          (__fsub_rn(zms[i], ci) + __fsub_rn(zps[i], ci));
-        const float c2 = ci * ci;
-        s0.add(c2);
-        sh.add(ci * (-kfac * lap + vs[i] * ci));
-        sr.add((px[i] * px[i] + py * py + pz * pz) * c2);
-        sv.add(vs[i] * c2);
-      }
+      sums_site4(s0, sh, sr, sv, c, xl, xr, ym, yp, zm, zp, v, px, py, coord_f32(j + zoff, n, a), kfac);
     }
     pp.end_step();
     if (!pp.ok(err)) {
