@@ -354,8 +354,9 @@ FDTD_API int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double
 FDTD_API int fdtd_get_stats(fdtd_handle h, fdtd_stats* out);
 FDTD_API int fdtd_reset_stats(fdtd_handle h);
 /* on = 1: bracket stencil launches issued through the stream with CUDA events
- * on the handle's stream (with options.graphs = 1, fdtd_evolve issues its
- * first two segments through the stream for this and the rest as a graph). */
+ * on the handle's stream, one pair around each run of consecutive launches of
+ * one temporal depth (with options.graphs = 1, fdtd_evolve issues its first
+ * two segments through the stream for this and the rest as a graph). */
 FDTD_API int fdtd_set_profiling(fdtd_handle h, int on);
 
 /* Allocation-free observables of a caller-held field (no counterpart in

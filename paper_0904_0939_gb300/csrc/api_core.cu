@@ -224,18 +224,18 @@ void prof_end(fdtd_context* c) {
   cudaEventRecord(c->ev[c->ev_used + 1], c->st);
   c->ev_used += 2;
 }
-// Credit the pending stencil launches that started before step `cutoff`
-// (call after a stream synchronisation).
+// Credit the pending runs of stencil launches that started before step
+// `cutoff` (call after a stream synchronisation).
 void flush_pending(fdtd_context* c, int64_t cutoff) {
   for (const auto& p : c->pending) {
     if (p.t_start >= cutoff) continue;
-    c->stats.stencil_launches += 1;
+    c->stats.stencil_launches += p.launches;
     c->stats.stencil_site_updates += p.updates;
     c->stats.stencil_bytes += p.bytes;
     float ms = 0.f;
     if (p.ev >= 0 && cudaEventElapsedTime(&ms, c->ev[p.ev], c->ev[p.ev + 1]) == cudaSuccess) {
       c->stats.stencil_ms += ms;
-      c->stats.stencil_timed_launches += 1;
+      c->stats.stencil_timed_launches += p.launches;
     }
   }
   c->pending.clear();

@@ -199,9 +199,25 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
   const bool fuse = before_check && count > 0 && check_step_fused(c, L);
   if (count > 0) L.sums_ready = false;
   if (fuse) --count;
+  // the launches go to the profiling record in runs of one depth: one pair
+  // of events around each run (an event between two launches would cost
+  // the second its early launch), credited per launch
+  fdtd_context::Pending run{};
+  int run_k = 0;
+  auto close_run = [&]() {
+    if (!run.launches) return;
+    prof_end(c);
+    c->pending.push_back(run);
+    run = fdtd_context::Pending{};
+  };
   while (count > 0) {
     int k = (int)std::min<int64_t>(count, depth);
-    const long ev = prof_begin(c);
+    if (run.launches && k != run_k) close_run();
+    if (!run.launches) {
+      run.ev = prof_begin(c);
+      run.t_start = t0;
+      run_k = k;
+    }
     if (is_complex(prec)) {
       with_ctype(prec, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
@@ -231,14 +247,16 @@ void run_steps(fdtd_context* c, Lat& L, int64_t count, const int32_t* active, in
       launch_step_f32<__nv_bfloat16>((const __nv_bfloat16*)L.psi[L.cur], (__nv_bfloat16*)L.psi[1 - L.cur],
                                      (const float*)L.v, L.p, active, c->st);
     }
-    prof_end(c);
     c->stats.launches += 1;
     // algorithmic bytes: psi read + psi write + V (FP64: A and cB; complex: A and cB pairs) read once per launch
-    c->pending.push_back({t0, (int64_t)L.n3 * k, (double)L.n3 * (2.0 * L.es + coef_bytes(prec)), ev});
+    run.launches += 1;
+    run.updates += (int64_t)L.n3 * k;
+    run.bytes += (double)L.n3 * (2.0 * L.es + coef_bytes(prec));
     L.cur ^= 1;
     count -= k;
     t0 += k;
   }
+  close_run();
   if (fuse) {
     launch_step_sums_tma(L.maps[0][1][L.cur], L.maps[0][1][2], (float*)L.psi[1 - L.cur], L.p, L.partials, active,
                          c->flags + 1, c->st);

@@ -149,10 +149,11 @@ struct fdtd_context {
   cudaEvent_t ev_in = nullptr;    // orders the lattices' graph loops after the handle's stream
   // stencil launches not yet credited to the stats: a launch enqueued past
   // the check at which its lattice converged runs as a no-op and is dropped
-  struct Pending {
+  struct Pending {  // a run of consecutive stencil launches of one depth
     int64_t t_start, updates;
     double bytes;
-    long ev;  // index of its start event, or -1
+    long ev;  // index of the run's start event, or -1
+    int64_t launches;
   };
   std::vector<Pending> pending;
 };
