@@ -117,25 +117,32 @@ def c3_potentials(resident: bool, device):
     return out
 
 
-def c3_step(fd, pots, seed, keep_last=False, graphs=1):
+def c3_step(fd, pots, seed, keep_last=False, graphs=1, streams=None):
     """One pass of the chain: one handle per level, random start on the
-    first, transfer into the next.  Returns totals: site updates, kernel
-    launches, the 512^3 level's stencil time / algorithmic bytes / updates,
-    and per-level results."""
+    first, transfer into the next.  Every level's handle is created and its
+    V enqueued (fdtd_set_potential_async) before the first level runs, each
+    handle on its own stream when `streams` are given, so that the later
+    levels' potentials upload while the first levels compute.  Returns
+    totals: site updates, kernel launches, the 512^3 level's stencil time /
+    algorithmic bytes / updates, and per-level results."""
     import torch
 
     prec = {"bf16": fd.BF16, "f32": fd.F32}
     tot = {"updates": 0, "launches": 0, "fine_ms": 0.0, "fine_bytes": 0.0, "fine_updates": 0, "fine_launches": 0,
            "fine_timed": 0, "results": {}, "config": None, "last": None}
+    solvers = []
+    for i, ((n, kind, tol), v) in enumerate(zip(C3_PLAN, pots)):
+        s = fd.Solver(fd.Lattice(n, C3_LENGTH, prec[kind]),
+                      fd.default_options(check_every=100, tol=tol, tol_relative=1, graphs=graphs),
+                      stream=streams[i] if streams else None)
+        s.set_profiling(n == C3_PLAN[-1][0])
+        s.set_potential(v, wait=False)
+        solvers.append(s)
     prev = None
-    for (n, kind, tol), v in zip(C3_PLAN, pots):
+    for (n, kind, tol), s in zip(C3_PLAN, solvers):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        s = fd.Solver(fd.Lattice(n, C3_LENGTH, prec[kind]), fd.default_options(check_every=100, tol=tol,
-                                                                               tol_relative=1, graphs=graphs))
+        ev0.record(s.stream)
         fine = n == C3_PLAN[-1][0]
-        s.set_profiling(fine)
-        s.set_potential(v)
         if prev is None:
             s.init_symmetric(seed, 0)
         else:
@@ -151,7 +158,7 @@ def c3_step(fd, pots, seed, keep_last=False, graphs=1):
             tot["fine_timed"] += st["stencil_timed_launches"]
             tot["config"] = s.tuned_config() + s.tuned_kernel()
         o = s.last_check()
-        ev1.record()
+        ev1.record(s.stream)
         ev1.synchronize()
         tot["updates"] += n**3 * o["steps"]
         tot["results"][f"{n}_{kind}"] = {"E": o["energy"], "r2": o["r2"], "steps": o["steps"],
@@ -820,9 +827,10 @@ def main():
     pots_dev = c3_potentials(True, dev)
     pots_host = c3_potentials(False, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    level_streams = [torch.cuda.Stream(dev) for _ in C3_PLAN]
 
     for _ in range(max(3, args.warmup)):
-        c3_step(fd, pots_dev, seed, graphs=args.graphs)
+        c3_step(fd, pots_dev, seed, graphs=args.graphs, streams=level_streams)
     torch.cuda.synchronize()
 
     def barrier():
@@ -844,8 +852,10 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         torch.cuda.nvtx.range_push("timed_step")  # lets a profiler select the timed steps' launches
-        tot = c3_step(fd, pots_dev, seed, graphs=args.graphs)
+        tot = c3_step(fd, pots_dev, seed, graphs=args.graphs, streams=level_streams)
         torch.cuda.nvtx.range_pop()
+        for st in level_streams:  # the levels ran on their own streams: e1 follows all of them
+            torch.cuda.current_stream(dev).wait_stream(st)
         e1.record()
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
@@ -865,7 +875,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_upd += c3_step(fd, pots_host, seed, graphs=args.graphs)["updates"]
+        e2e_upd += c3_step(fd, pots_host, seed, graphs=args.graphs, streams=level_streams)["updates"]
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
 

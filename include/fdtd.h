@@ -226,6 +226,19 @@ FDTD_API int fdtd_last_error(fdtd_handle h, char* buf, size_t n);
  * FDTD_ERR_NONFINITE for NaN/Inf and FDTD_ERR_UNSTABLE_DT where
  * 1 + dtau V/2 <= 0 (the update would divide by zero or flip sign). */
 FDTD_API int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind);
+/* fdtd_set_potential without waiting: the copy (or conversion) of V and its
+ * checks are enqueued on the handle's stream and the call returns; argument
+ * errors are reported at once.  The caller keeps v valid and unchanged until
+ * the handle's stream has passed the copy (for host memory, page-locked
+ * memory makes the copy asynchronous; from pageable memory the CUDA runtime
+ * may copy before returning).  The next call of the handle that uses V
+ * (fdtd_evolve, fdtd_observables, fdtd_upsample into it, fdtd_backward,
+ * fdtd_project_out, fdtd_combine, fdtd_tuned_config/kernel) or a
+ * fdtd_set_potential first waits for the stream and reports the checks'
+ * result (FDTD_ERR_NONFINITE / FDTD_ERR_UNSTABLE_DT as above; with several
+ * potentials pending, every one of them is then unset).  A handle on its own
+ * stream can so upload one level's potential while another handle computes. */
+FDTD_API int fdtd_set_potential_async(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind);
 
 /* Random initial wavefunction (Sec. III) followed by the symmetry mask
  * (Sec. IV).  Site value = draw number lat_id * 2^42 + n (uniform) or

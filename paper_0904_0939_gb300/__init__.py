@@ -80,7 +80,7 @@ class Stats(ctypes.Structure):
 
 
 EXPORTED = ["fdtd_default_options", "fdtd_workspace_size", "fdtd_create", "fdtd_destroy", "fdtd_last_error",
-            "fdtd_set_potential", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
+            "fdtd_set_potential", "fdtd_set_potential_async", "fdtd_init_symmetric", "fdtd_set_psi", "fdtd_get_psi", "fdtd_evolve",
             "fdtd_last_check", "fdtd_observables", "fdtd_upsample", "fdtd_backward", "fdtd_get_stats",
             "fdtd_reset_stats", "fdtd_set_profiling", "fdtd_observables_noalloc", "fdtd_tuned_config",
             "fdtd_tuned_kernel",
@@ -104,6 +104,7 @@ def _load():
         "fdtd_create": [P(LatticeDesc), i32, P(Options), vp, ctypes.c_size_t, vp, P(vp)],
         "fdtd_destroy": [vp],
         "fdtd_set_potential": [vp, i32, vp, i32, i32],
+        "fdtd_set_potential_async": [vp, i32, vp, i32, i32],
         "fdtd_init_symmetric": [vp, i32, u64, i32, i32],
         "fdtd_set_psi": [vp, i32, vp, i32, i32, i32],
         "fdtd_get_psi": [vp, i32, vp, i32, i32],
@@ -233,11 +234,13 @@ class Solver:
                                    ctypes.c_void_p(self.workspace.data_ptr()), size.value,
                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.handle = h
+        self._in_flight = []  # buffers of potentials enqueued without waiting
 
     def close(self):
         if getattr(self, "handle", None):
-            lib.fdtd_destroy(self.handle)
+            lib.fdtd_destroy(self.handle)  # waits for the stream
             self.handle = None
+            self._in_flight = []
 
     def __del__(self):
         try:
@@ -261,10 +264,19 @@ class Solver:
         return arr
 
     # --- calls ---------------------------------------------------------------
-    def set_potential(self, v, lat: int = 0):
+    def set_potential(self, v, lat: int = 0, wait: bool = True):
+        """Load V.  wait=False enqueues the copy and its checks on the
+        handle's stream and returns (fdtd_set_potential_async): v is kept
+        referenced until the next call that waits for the stream, which
+        also reports the checks (host tensors should be pinned)."""
         ptr, code, mem, keep = _buffer(self._sized(v, lat, "set_potential"))
         with self._ctx():
-            _check(lib.fdtd_set_potential(self.handle, lat, ptr, code, mem), self.handle)
+            if wait:
+                _check(lib.fdtd_set_potential(self.handle, lat, ptr, code, mem), self.handle)
+                self._in_flight.clear()
+            else:
+                _check(lib.fdtd_set_potential_async(self.handle, lat, ptr, code, mem), self.handle)
+                self._in_flight.append((v, keep))
 
     def init_symmetric(self, seed: int, mask: int = 0, lat: int = 0, dist: int = DIST_UNIFORM):
         with self._ctx():
@@ -293,6 +305,7 @@ class Solver:
         done = ctypes.c_int64()
         with self._ctx():
             rc = _check(lib.fdtd_evolve(self.handle, max_steps, ctypes.byref(done)), self.handle, allow_soft=True)
+        self._in_flight.clear()  # the call waited for the stream
         return done.value, rc == OK
 
     def last_check(self, lat: int = 0) -> dict:
@@ -305,11 +318,13 @@ class Solver:
         o = Obs()
         with self._ctx():
             _check(lib.fdtd_observables(self.handle, lat, ctypes.byref(o)), self.handle)
+        self._in_flight.clear()
         return o.to_dict()
 
     def upsample_from(self, src: "Solver", lat_src: int = 0, lat: int = 0):
         with self._ctx():
             _check(lib.fdtd_upsample(src.handle, lat_src, self.handle, lat), self.handle)
+        self._in_flight.clear()
 
     def backward(self, T: int, w_e: float = 1.0, w_r: float = 0.0, lat: int = 0, out=None):
         """dL/dV for L = w_e E + w_r <r^2> after T steps; returns (gV, obs)."""
@@ -320,6 +335,7 @@ class Solver:
         o = Obs()
         with self._ctx():
             _check(lib.fdtd_backward(self.handle, lat, T, w_e, w_r, ptr, code, mem, ctypes.byref(o)), self.handle)
+        self._in_flight.clear()
         return out, o.to_dict()
 
     # --- snapshots (Sec. III) and combinations (Sec. VI) -----------------------
@@ -336,6 +352,7 @@ class Solver:
         arr = (ctypes.c_int * max(1, len(slots)))(*slots)
         with self._ctx():
             _check(lib.fdtd_project_out(self.handle, lat, arr, len(slots)), self.handle)
+        self._in_flight.clear()
 
     def combine(self, slots, weights, lat: int = 0):
         """psi <- sum_k weights[k] * slot_k, renormalised."""
@@ -343,6 +360,7 @@ class Solver:
         w = (ctypes.c_double * len(weights))(*weights)
         with self._ctx():
             _check(lib.fdtd_combine(self.handle, lat, a, w, len(slots)), self.handle)
+        self._in_flight.clear()
 
     def bounds_violations(self) -> int:
         """Out-of-allocation accesses counted by a bounds-checking build."""
@@ -379,6 +397,7 @@ class Solver:
         d, z = ctypes.c_int(), ctypes.c_int()
         with self._ctx():
             _check(lib.fdtd_tuned_config(self.handle, lat, ctypes.byref(d), ctypes.byref(z)), self.handle)
+        self._in_flight.clear()
         return d.value, z.value
 
     def tuned_kernel(self, lat: int = 0) -> tuple[int, int]:
@@ -387,6 +406,7 @@ class Solver:
         t, r = ctypes.c_int(), ctypes.c_int()
         with self._ctx():
             _check(lib.fdtd_tuned_kernel(self.handle, lat, ctypes.byref(t), ctypes.byref(r)), self.handle)
+        self._in_flight.clear()
         return t.value, r.value
 
     def stats(self) -> dict:

@@ -24,6 +24,7 @@ int fdtd_backward(fdtd_handle h, int lat, int64_t T, double w_e, double w_r, voi
   if (L.d.precision == FDTD_BF16) return fail(h, FDTD_ERR_INVALID_ARG, "backward: not available for BF16 storage");
   if (!L.psi0 || T > L.bw_T)
     return fail(h, FDTD_ERR_WORKSPACE, "backward: T exceeds options.backward_steps given at create");
+  if ((rc = resolve_potentials(h))) return rc;
   if (!L.has_v || !L.has_psi0) return fail(h, FDTD_ERR_STATE, "backward: set_potential and init/set_psi first");
   const int64_t ce = h->o.check_every;
   const int K = L.bw_K;

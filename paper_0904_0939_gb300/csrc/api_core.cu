@@ -503,7 +503,14 @@ int fdtd_last_error(fdtd_handle h, char* buf, size_t n) {
   return (int)std::min<size_t>(m.size(), 0x7fffffff);
 }
 
-int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
+}  // extern "C"
+
+namespace fdtd {
+namespace api {
+namespace {
+// Enqueue V's conversion (or copy) and its checks on the handle's stream;
+// the check bits accumulate in flags[0] until resolve_potentials reads them.
+int enqueue_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
   int rc = lat_check(h, lat);
   if (rc) return rc;
   const bool cplx_in = dtype == FDTD_C64 || dtype == FDTD_C32;
@@ -513,7 +520,11 @@ int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem
   Lat& L = h->lats[lat];
   if (cplx_in && !is_complex(L.d.precision))
     return fail(h, FDTD_ERR_INVALID_ARG, "set_potential: a complex potential needs a complex lattice (FDTD_C64/C32)");
-  cudaMemsetAsync(h->flags, 0, sizeof(int32_t), h->st);
+  bool pending = false;
+  for (const Lat& o : h->lats) pending = pending || o.v_pending;
+  if (!pending) cudaMemsetAsync(h->flags, 0, sizeof(int32_t), h->st);
+  L.has_v = false;
+  L.v_pending = true;
   if (is_complex(L.d.precision)) {
     // V, A and cB of a complex lattice (real input: V_I = 0)
     const bool in64 = dtype == FDTD_F64 || dtype == FDTD_C64;
@@ -565,15 +576,41 @@ int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem
       conv(h->staging, cnt, off);
     }
   }
+  return cuda_check(h, "set_potential");
+}
+}  // namespace
+
+int resolve_potentials(fdtd_context* c) {
+  bool pending = false;
+  for (const Lat& o : c->lats) pending = pending || o.v_pending;
+  if (!pending) return FDTD_OK;
   int32_t flags = 0;
-  cudaMemcpyAsync(&flags, h->flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-  cudaError_t e = cudaStreamSynchronize(h->st);
-  if (e != cudaSuccess) return fail(h, FDTD_ERR_CUDA, std::string("set_potential: ") + cudaGetErrorString(e));
-  if ((rc = cuda_check(h, "set_potential"))) return rc;
-  if (flags & 1) return fail(h, FDTD_ERR_NONFINITE, "set_potential: NaN or Inf in V");
-  if (flags & 2) return fail(h, FDTD_ERR_UNSTABLE_DT, "set_potential: 1 + dtau Re V / 2 <= 0 at some site");
-  L.has_v = true;
+  cudaMemcpyAsync(&flags, c->flags, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  for (Lat& o : c->lats) {
+    if (!o.v_pending) continue;
+    o.v_pending = false;
+    o.has_v = e == cudaSuccess && (flags & 3) == 0;
+  }
+  if (e != cudaSuccess) return fail(c, FDTD_ERR_CUDA, std::string("set_potential: ") + cudaGetErrorString(e));
+  if (flags & 1) return fail(c, FDTD_ERR_NONFINITE, "set_potential: NaN or Inf in V");
+  if (flags & 2) return fail(c, FDTD_ERR_UNSTABLE_DT, "set_potential: 1 + dtau Re V / 2 <= 0 at some site");
   return FDTD_OK;
+}
+
+}  // namespace api
+}  // namespace fdtd
+
+extern "C" {
+
+int fdtd_set_potential(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
+  int rc = fdtd::api::enqueue_potential(h, lat, v, dtype, mem_kind);
+  if (rc) return rc;
+  return fdtd::api::resolve_potentials(h);
+}
+
+int fdtd_set_potential_async(fdtd_handle h, int lat, const void* v, int dtype, int mem_kind) {
+  return fdtd::api::enqueue_potential(h, lat, v, dtype, mem_kind);
 }
 
 int fdtd_init_symmetric(fdtd_handle h, int lat, uint64_t seed, int parity_mask, int dist) {
@@ -693,6 +730,7 @@ int fdtd_observables(fdtd_handle h, int lat, fdtd_obs* out) {
   if (rc) return rc;
   if (!out) return fail(h, FDTD_ERR_INVALID_ARG, "observables: null output");
   Lat& L = h->lats[lat];
+  if ((rc = resolve_potentials(h))) return rc;
   if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "observables: set_potential and init/set_psi first");
   int np = launch_sums_any(h, L, L.psi[L.cur], nullptr);
   launch_state_reset(&L.state[1], 0, h->st);
@@ -723,6 +761,7 @@ int fdtd_upsample(fdtd_handle src, int lat_src, fdtd_handle dst, int lat_dst) {
     return fail(dst, FDTD_ERR_SHAPE, "upsample: need n_dst = 2 n_src and equal box lengths");
   if (!S.has_psi) return fail(dst, FDTD_ERR_STATE, "upsample: source has no wavefunction");
   if (S.p.periodic != D.p.periodic) return fail(dst, FDTD_ERR_INVALID_ARG, "upsample: boundaries differ");
+  if ((rc = resolve_potentials(dst))) return rc;
   if (!D.has_v) return fail(dst, FDTD_ERR_STATE, "upsample: set the destination potential first");
   if (is_complex(S.d.precision) != is_complex(D.d.precision))
     return fail(dst, FDTD_ERR_INVALID_ARG, "upsample: both lattices complex or both real");
@@ -781,6 +820,7 @@ int fdtd_tuned_config(fdtd_handle h, int lat, int* depth, int* zchunk) {
     *zchunk = -1;
     return FDTD_OK;
   }
+  if ((rc = resolve_potentials(h))) return rc;
   if (L.has_v && L.has_psi) choose_config(h, L);
   *depth = L.depth;
   *zchunk = L.plain ? 0 : L.zc;
@@ -800,6 +840,7 @@ int fdtd_tuned_kernel(fdtd_handle h, int lat, int* tile_x, int* tile_y) {
     }
     return FDTD_OK;
   }
+  if ((rc = resolve_potentials(h))) return rc;
   if (L.has_v && L.has_psi) choose_config(h, L);
   if ((L.tma_ok || L.tma16) && h->o.stencil_kernel == 0 && !L.plain && L.depth > 0) {
     int bw = 0, bh = 0;

@@ -777,9 +777,10 @@ int fdtd_evolve(fdtd_handle h, int64_t max_steps, int64_t* steps_done) {
   Range r("fdtd_evolve");
   if (!h) return FDTD_ERR_INVALID_ARG;
   if (max_steps < 0) return fail(h, FDTD_ERR_INVALID_ARG, "evolve: max_steps < 0");
+  int rc = resolve_potentials(h);
+  if (rc) return rc;
   for (auto& L : h->lats)
     if (!L.has_v || !L.has_psi) return fail(h, FDTD_ERR_STATE, "evolve: set_potential and init/set_psi first");
-  int rc = FDTD_OK;
   if (h->o.batched) {
     rc = evolve_batched(h, max_steps);
   } else {

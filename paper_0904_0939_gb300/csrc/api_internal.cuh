@@ -73,6 +73,7 @@ struct Lat {
   double* hist = nullptr;       // check history ring of the evolve (kHistCap records)
   int mask = 0;
   bool has_v = false, has_psi = false, has_psi0 = false;
+  bool v_pending = false;  // V enqueued by fdtd_set_potential_async, its checks not yet read
   // backward storage
   void* psi0 = nullptr;
   int64_t bw_T = 0;
@@ -121,6 +122,11 @@ struct Lat {
 
 void release_graph(Lat& L, int b);
 void release_graph(Lat& L);
+// Read the checks of every potential enqueued without waiting
+// (fdtd_set_potential_async) on handle c: one stream synchronisation; the
+// lattices become usable (has_v) or the error is returned.  No-op when none
+// is pending.
+int resolve_potentials(fdtd_context* c);
 
 }  // namespace api
 }  // namespace fdtd

@@ -212,6 +212,7 @@ int fdtd_project_out(fdtd_handle h, int lat, const int* slots, int count) {
   Lat& L = h->lats[lat];
   if (is_complex(L.d.precision))
     return fail(h, FDTD_ERR_INVALID_ARG, "project_out: not available for complex lattices");
+  if ((rc = resolve_potentials(h))) return rc;
   if (!L.has_psi || !L.has_v) return fail(h, FDTD_ERR_STATE, "project_out: set_potential and a wavefunction first");
   for (int k = 0; k < count; ++k)
     if ((rc = snap_check(h, lat, slots[k]))) return rc;
@@ -235,6 +236,7 @@ int fdtd_combine(fdtd_handle h, int lat, const int* slots, const double* weights
   Lat& L = h->lats[lat];
   if (is_complex(L.d.precision))
     return fail(h, FDTD_ERR_INVALID_ARG, "combine: not available for complex lattices");
+  if ((rc = resolve_potentials(h))) return rc;
   if (!L.has_v) return fail(h, FDTD_ERR_STATE, "combine: set_potential first");
   for (int k = 0; k < count; ++k) {
     if ((rc = snap_check(h, lat, slots[k]))) return rc;
