@@ -31,13 +31,15 @@ def potential(n, L):
     return (wl.harmonic(n, L) + 0.3 * np.cos(wl.radius2(n, L))).astype(np.float32)
 
 
-@pytest.mark.parametrize("prec", ["F32", "BF16", "F64"])
+@pytest.mark.parametrize("prec", ["F32", "BF16", "F64", "C64", "C32"])
 @pytest.mark.parametrize("where", ["pinned", "device", "numpy"])
 def test_async_equals_blocking(fd, prec, where):
     import torch
 
     n, L = 40, 12.0
     v = potential(n, L)
+    if prec in ("C64", "C32"):  # a complex potential: an absorbing imaginary part
+        v = (v - 0.05j * wl.radius2(n, L)).astype(np.complex64)
     src = {"pinned": lambda: torch.from_numpy(v.copy()).pin_memory(),
            "device": lambda: torch.from_numpy(v).cuda(), "numpy": lambda: v.copy()}[where]
     out = []
