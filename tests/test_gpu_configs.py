@@ -138,6 +138,64 @@ def test_anisotropic_512_sampled_sites(fd, orc):
         assert got[z, y, x] == pytest.approx(want, rel=2e-5, abs=2e-5 * peak)
 
 
+def test_largest_lattice_2048_sampled_sites(fd, orc):
+    """n = 2048, the largest lattice the library accepts: 8.6e9 sites, so
+    every linear index past plane 512 is above 2^31, and 34 GB per field.
+    FP32 in the tuned TMA configuration, V = r^2/2 built in FP32 on the
+    device, sampled sites (near the first and the last planes, rows and
+    columns) after 6 steps against the oracle on each site's cone of
+    dependence, as at 512^3."""
+    import torch
+
+    if torch.cuda.get_device_properties(0).total_memory < 240 * 2**30:
+        pytest.skip("needs about 210 GB of device memory")
+    n, L, steps = 2048, 64.0, 6
+    a = L / n
+    r = steps + 1
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(3)
+    sites = [tuple(int(c) for c in rng.integers(8, n - 8, size=3)) for _ in range(10)]
+    sites += [(2039, 2039, 2039), (2040, 8, 2031), (9, 2035, 8), (1024, 1023, 2040), (513, 1, 1)]
+    ax2 = torch.as_tensor(wl.axis(n, L), dtype=torch.float32, device=dev) ** 2
+    v = 0.5 * ((ax2[None, None, :] + ax2[None, :, None]) + ax2[:, None, None])
+    s = fd.Solver(fd.Lattice(n, L, fd.F32), fd.default_options(check_every=1000, tol=0.0))
+    try:
+        s.set_potential(v)
+
+        w = 2 * r + 1
+        corner = [[min(max(c - r, 0), n - w) for c in site] for site in sites]
+
+        def boxes(t):
+            # a (2r+1)^3 box around each site's cone of dependence, moved
+            # inside the lattice at its faces: a box face on a lattice face
+            # is the Dirichlet wall (the oracle's zero padding), any other
+            # face is at least r > steps sites from the site
+            return [t[lo[0]:lo[0] + w, lo[1]:lo[1] + w, lo[2]:lo[2] + w].double().cpu().numpy() for lo in corner]
+
+        vs = boxes(v)
+        del v
+        torch.cuda.empty_cache()
+        s.init_symmetric(23, 0)
+        buf = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        s.get_psi(out=buf)
+        subs = boxes(buf)
+        s0 = sum(float(torch.sum(buf[z0:z0 + 128].double() ** 2)) for z0 in range(0, n, 128))
+        s.evolve(steps)
+        sT = s.last_check()["norm"] / a**3
+        s.get_psi(out=buf)
+        got = [float(buf[z, y, x]) for (z, y, x) in sites]
+        peak = float(buf.abs().max())
+        scale = 1.0 / math.sqrt(s0 * a**3) / math.sqrt(sT * a**3)
+        for site, lo, g, sub, vsub in zip(sites, corner, got, subs, vs):
+            cz, cy, cx = (c - o for c, o in zip(site, lo))
+            want = scale * orc.steps(sub, vsub, a, a * a / 4, steps)[cz, cy, cx]
+            assert g == pytest.approx(want, rel=2e-5, abs=2e-5 * peak)
+        del buf
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
+
+
 def test_batch_subset_matches_separate_runs(fd):
     """Eight lattices of the 64-lattice batch (sizes 48..160, oscillator or
     soft Coulomb, four sectors) in one persistent launch vs one by one from
